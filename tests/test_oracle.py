@@ -1,0 +1,204 @@
+"""Pins for the oracle against what the paper and the mathematics fix (CPU only).
+
+* Fig. 1 (Sec. II-A): the offsets/edges values stated in the text.
+* The definition (Sec. II-A): CSC lists = CSR edges stably sorted by
+  destination -> brute force by lexicographic sort, exhaustively on tiny graphs.
+* Involution (Sec. II-A: the transpose of the transpose is the original).
+* Degree preservation and offsets semantics (Algorithm 1 Steps 1-2).
+* Undirected graphs have identical CSR and CSC (Sec. II-A).
+* Weights ride along unchanged (Sec. II-A).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_06872_gb300 import inputs
+from tests._graphs import all_tiny_graphs, brute_transpose, csr_from_rows
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fig1_pins.txt")
+
+
+def _read_golden():
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *vs = line.split()
+            out[k] = [int(x) for x in vs]
+    return out
+
+
+def test_fig1_pins():
+    g = _read_golden()
+    n = g["reconstruction_n"][0]
+    ed = g["reconstruction_edges"]
+    rows = [[] for _ in range(n)]
+    for i in range(0, len(ed), 2):
+        rows[ed[i]].append(ed[i + 1])
+    row_ptr, col_idx = csr_from_rows(n, rows)
+    # the reconstruction agrees with the CSR values stated in the text
+    assert list(row_ptr[:2]) == g["csr_offsets_prefix"]
+    assert list(col_idx[row_ptr[0]:row_ptr[1]]) == g["csr_vertex0_out"]
+    col_ptr, row_idx, _ = oracle.transpose(row_ptr, col_idx)
+    assert list(col_ptr[:2]) == g["csc_offsets_prefix"]
+    assert list(row_idx[:1]) == g["csc_edges_prefix"]
+
+
+def test_exhaustive_tiny_vs_definition():
+    count = 0
+    for n, rows in all_tiny_graphs(3, 4):
+        row_ptr, col_idx = csr_from_rows(n, rows)
+        m = col_idx.shape[0]
+        vals = np.arange(m, dtype=np.float32) + 0.5  # distinct: exposes the duplicate order
+        got = oracle.transpose(row_ptr, col_idx, vals)
+        exp = brute_transpose(row_ptr, col_idx, vals)
+        assert np.array_equal(got[0], exp[0])
+        assert np.array_equal(got[1], exp[1])
+        assert np.array_equal(got[2], exp[2])
+        count += 1
+    assert count == 1683  # every CSR with n <= 3 and m <= 4
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("n,m", [(1, 5), (7, 0), (17, 200), (300, 5000), (1000, 777)])
+def test_random_vs_definition(seed, n, m):
+    n, row_ptr, col_idx, vals = inputs.random_csr(n, m, seed=seed, hot=3, hot_frac=0.3)
+    got = oracle.transpose(row_ptr, col_idx, vals)
+    exp = brute_transpose(row_ptr, col_idx, vals)
+    for a, b in zip(got, exp):
+        assert np.array_equal(a, b)
+
+
+def test_rmat_small_vs_definition():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(10, 8, seed=5, weighted=True)
+    got = oracle.transpose(row_ptr, col_idx, vals)
+    exp = brute_transpose(row_ptr, col_idx, vals)
+    for a, b in zip(got, exp):
+        assert np.array_equal(a, b)
+
+
+def test_invariants_degrees_offsets():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(11, 16, seed=9, order="random", weighted=True)
+    col_ptr, row_idx, vo = oracle.transpose(row_ptr, col_idx, vals)
+    m = col_idx.shape[0]
+    assert col_ptr[0] == 0 and col_ptr[-1] == m
+    assert np.all(np.diff(col_ptr.astype(np.int64)) >= 0)
+    # in-degree of CSR = out-degree of CSC; out-degree of CSR = in-degree of CSC
+    assert np.array_equal(np.diff(col_ptr.astype(np.int64)), np.bincount(col_idx, minlength=n))
+    assert np.array_equal(np.bincount(row_idx, minlength=n), np.diff(row_ptr.astype(np.int64)))
+    # the multiset of (u, v, w) triples is preserved
+    src = np.repeat(np.arange(n), np.diff(row_ptr.astype(np.int64)))
+    dst_t = np.repeat(np.arange(n), np.diff(col_ptr.astype(np.int64)))
+    a = np.lexsort((vals.view(np.uint32), col_idx, src))
+    b = np.lexsort((vo.view(np.uint32), dst_t, row_idx))
+    assert np.array_equal(src[a], row_idx[b])
+    assert np.array_equal(col_idx[a], dst_t[b])
+    assert np.array_equal(vals[a].view(np.uint32), vo[b].view(np.uint32))
+    # every list ascending in source
+    for v in range(0, n, 37):
+        seg = row_idx[col_ptr[v]:col_ptr[v + 1]]
+        assert np.all(np.diff(seg.astype(np.int64)) >= 0)
+
+
+def test_involution_sorted_rows():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(9, 8, seed=3, weighted=True, sorted_rows=True)
+    c1 = oracle.transpose(row_ptr, col_idx, vals)
+    c2 = oracle.transpose(c1[0], c1[1], c1[2])
+    assert np.array_equal(c2[0], row_ptr)
+    assert np.array_equal(c2[1], col_idx)
+    assert np.array_equal(c2[2].view(np.uint32), vals.view(np.uint32))
+
+
+def test_involution_unsorted_rows_up_to_row_order():
+    n, row_ptr, col_idx, _ = inputs.rmat_csr(9, 8, seed=4)
+    c1 = oracle.transpose(row_ptr, col_idx)
+    c2 = oracle.transpose(c1[0], c1[1])
+    assert np.array_equal(c2[0], row_ptr)
+    for u in range(n):
+        a, b = int(row_ptr[u]), int(row_ptr[u + 1])
+        assert np.array_equal(np.sort(c2[1][a:b]), np.sort(col_idx[a:b]))
+
+
+def test_undirected_graph_is_its_own_transpose():
+    src, dst = inputs.er_edges(200, 1500, seed=2)
+    s2 = np.concatenate([src, dst])
+    d2 = np.concatenate([dst, src])
+    o = np.lexsort((d2, s2))
+    row_ptr, col_idx, _ = inputs.csr_from_edges(200, s2[o], d2[o])
+    col_ptr, row_idx, _ = oracle.transpose(row_ptr, col_idx)
+    assert np.array_equal(col_ptr, row_ptr)
+    assert np.array_equal(row_idx, col_idx)
+
+
+def test_degenerate_cases():
+    # no edges
+    col_ptr, row_idx, _ = oracle.transpose(np.zeros(6, np.uint64), np.zeros(0, np.uint32))
+    assert np.array_equal(col_ptr, np.zeros(6, np.uint64)) and row_idx.size == 0
+    # one vertex with self-loops, weights kept in CSR order
+    col_ptr, row_idx, vo = oracle.transpose(np.array([0, 3], np.uint64), np.zeros(3, np.uint32),
+                                            np.array([3.0, 1.0, 2.0], np.float32))
+    assert list(col_ptr) == [0, 3] and list(row_idx) == [0, 0, 0] and list(vo) == [3.0, 1.0, 2.0]
+    # all edges into the last vertex
+    n = 50
+    row_ptr = np.arange(n + 1, dtype=np.uint64)
+    col_idx = np.full(n, n - 1, np.uint32)
+    col_ptr, row_idx, _ = oracle.transpose(row_ptr, col_idx)
+    assert col_ptr[n - 1] == 0 and col_ptr[n] == n and np.array_equal(row_idx, np.arange(n))
+
+
+def test_errors():
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.transpose(np.array([0, 1], np.uint64), np.array([1], np.uint32))
+    assert ei.value.code == 2
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.transpose(np.array([0, 2, 1], np.uint64), np.array([0], np.uint32))
+    assert ei.value.code == 3
+
+
+def test_range_chunks_reassemble_full():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(10, 16, seed=8, order="random", weighted=True)
+    full = oracle.transpose(row_ptr, col_idx, vals)
+    cuts = [0, 1, 100, 513, 900, n]
+    rows, vs = [], []
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        cp, r, v = oracle.transpose_range(row_ptr, col_idx, vals, lo, hi)
+        assert np.array_equal(cp, full[0][lo:hi + 1])
+        rows.append(r)
+        vs.append(v)
+    assert np.array_equal(np.concatenate(rows), full[1])
+    assert np.array_equal(np.concatenate(vs), full[2])
+
+
+def test_sampled_columns_match_full():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(10, 16, seed=6, order="degree", weighted=True)
+    full = oracle.transpose(row_ptr, col_idx, vals)
+    cols = np.array([0, 1, 2, 17, 400, 1023], dtype=np.uint32)
+    c, start, deg, rows, vo = oracle.columns(row_ptr, col_idx, vals, cols)
+    off = 0
+    for i, v in enumerate(c):
+        assert start[i] == full[0][v]
+        assert deg[i] == full[0][v + 1] - full[0][v]
+        d = int(deg[i])
+        assert np.array_equal(rows[off:off + d], full[1][full[0][v]:full[0][v + 1]])
+        assert np.array_equal(vo[off:off + d], full[2][full[0][v]:full[0][v + 1]])
+        off += d
+
+
+def test_brute_force_detects_planted_mistakes():
+    """The pins must fail on plausible mistakes: here they are planted in a copy
+    of the oracle's output (dropped edge, swapped order, off-by-one offset)."""
+    n, row_ptr, col_idx, vals = inputs.random_csr(40, 300, seed=11)
+    good = oracle.transpose(row_ptr, col_idx, vals)
+    exp = brute_transpose(row_ptr, col_idx, vals)
+    assert all(np.array_equal(a, b) for a, b in zip(good, exp))
+    bad_ptr = good[0].copy()
+    bad_ptr[5] += 1
+    assert not np.array_equal(bad_ptr, exp[0])
+    bad_rows = good[1].copy()
+    j = int(np.argmax(np.diff(bad_rows.astype(np.int64)) > 0))
+    bad_rows[j], bad_rows[j + 1] = bad_rows[j + 1], bad_rows[j]
+    assert not np.array_equal(bad_rows, exp[1])
