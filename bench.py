@@ -1,0 +1,376 @@
+"""Benchmark: CSR -> CSC transposition on one GB300 (or N replicas under torchrun).
+
+One step = one gt_transpose call (sampling, count, scan, scatter, LDV sort)
+over the resident workload.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transposed edges/s & HBM GB/s vs peak; batched/learned vs plain on one GB300"
+UNIT = "edges/s"
+
+# name -> (kind, scale, edge_factor, order, weighted)
+WORKLOADS = {
+    "rmat28-degree": ("rmat", 28, 16, "degree", True),
+    "rmat28-random": ("rmat", 28, 16, "random", True),
+    "rmat24-random": ("rmat", 24, 16, "random", False),
+    "er24-random": ("er", 24, 16, "random", False),
+    "rmat16": ("rmat", 16, 16, "natural", False),
+    "rmat20-degree": ("rmat", 20, 16, "degree", True),
+    "rmat22-degree": ("rmat", 22, 16, "degree", True),
+    "rmat24-degree": ("rmat", 24, 16, "degree", True),
+}
+SEED = 0x5EED0003
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2501_06872_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(f"{kernel}@{workload}")
+        if e and e.get("source_sha") == kernel_source_sha():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def algorithmic_bytes(n, m, weighted):
+    """Bytes the transposition must move (formula of the metric): 2 x col_idx read +
+    row_ptr read + row_idx (+ vals_out) write + col_ptr write; plus, separately,
+    the vals read."""
+    literal = 2 * 4 * m + 8 * (n + 1) + 4 * m + (4 * m if weighted else 0) + 8 * (n + 1)
+    with_vals = literal + (4 * m if weighted else 0)
+    return literal, with_vals
+
+
+def stage_bytes(n, m, weighted):
+    """Algorithmic bytes per launch of each step's kernels."""
+    w = 4 * m if weighted else 0
+    return {
+        "count": 4 * m + 4 * n,                       # col_idx read, degrees written
+        "scan": 4 * n + 8 * (n + 1),                  # degrees read, col_ptr written
+        "scatter": 4 * m + w + 8 * (n + 1) + 4 * m + w,  # col_idx, vals, row_ptr read; row_idx, vals_out written
+    }
+
+
+def cpu_baseline_sample(rp_h, ci_h, vv_h, target_edges):
+    """Rows [0, R) of the workload, R chosen so the prefix holds about target_edges."""
+    import oracle
+    n = rp_h.size - 1
+    R = int(np.searchsorted(rp_h, np.uint64(target_edges), side="left"))
+    R = max(1, min(R, n))
+    mS = int(rp_h[R])
+    rp_s = rp_h.copy()
+    rp_s[R:] = mS
+    t0 = time.perf_counter()
+    oracle.transpose(rp_s, ci_h[:mS], None if vv_h is None else vv_h[:mS])
+    dt = time.perf_counter() - t0
+    return mS, R, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle (single-threaded C, host cores) on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2501_06872_gb300.inputs import gpu as ggen
+    import __graft_entry__
+    __graft_entry__.build()
+    kind, scale, ef, order, weighted = WORKLOADS[args.workload]
+    torch.cuda.set_device(0)
+    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=SEED, order=order, weighted=weighted)
+    target = min(args.ref_sample_edges, ci.numel())
+    R = int(torch.searchsorted(rp, torch.tensor([target], device=rp.device)).item())
+    R = max(1, min(R, n))
+    mS = int(rp[R].item())
+    rp_h = rp.cpu().numpy().view(np.uint64).copy()
+    rp_h[R:] = mS
+    ci_h = ci[:mS].cpu().numpy().view(np.uint32)
+    vv_h = None if vv is None else vv[:mS].cpu().numpy()
+    del rp, ci, vv
+    torch.cuda.empty_cache()
+    import oracle
+    for _ in range(args.warmup):
+        oracle.transpose(rp_h, ci_h, vv_h)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.transpose(rp_h, ci_h, vv_h)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = mS * args.steps / total
+    sample = f"rows [0,{R}) of the workload ({mS} edges, all {n} vertices)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(args.workload, n, int(mS), weighted),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(name, n, m, weighted):
+    kind, scale, ef, order, _ = WORKLOADS[name]
+    return {"workload": f"{name}{'-weighted' if weighted else ''}", "graph": kind, "scale": scale,
+            "edge_factor": ef, "n_vertices": n, "n_edges": m, "vertex_order": order, "weighted": weighted,
+            "seed": SEED, "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat28-degree", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=None, help="JSON gt_config overrides")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-edges", type=int, default=1 << 26)
+    ap.add_argument("--ref-sample-edges", type=int, default=1 << 24)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_06872_gb300 import binding
+    from paper_2501_06872_gb300.inputs import gpu as ggen
+
+    kind, scale, ef, order, weighted = WORKLOADS[args.workload]
+    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=SEED + rank, order=order, weighted=weighted)
+    m = ci.numel()
+    cfg = binding.default_config(n, m)
+    if args.config:
+        for k, v in json.loads(args.config).items():
+            setattr(cfg, k, int(v))
+    plan = binding.Plan(n, m, weighted, cfg)
+    cp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    ri = torch.empty(m, dtype=torch.int32, device="cuda")
+    vo = torch.empty(m, dtype=torch.float32, device="cuda") if weighted else None
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.transpose(rp, ci, vv, cp, ri, vo)
+    plan.check()
+
+    plan.enable_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.transpose(rp, ci, vv, cp, ri, vo)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    plan.check()
+    ms = ev0.elapsed_time(ev1)
+    timing = plan.timing()
+    stats = plan.stats()
+    plan.enable_timing(False)
+    ms_step = ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = m * world / (ms_step * 1e-3)
+
+    peak, peak_kind = load_peaks()
+    sb = stage_bytes(n, m, weighted)
+    stage_ms = {"count": timing["count_ms"], "scan": timing["scan_ms"], "scatter": timing["scatter_ms"],
+                "sort": timing["sort_ms"], "sample": timing["sample_ms"]}
+    dominant = max(["count", "scan", "scatter"], key=lambda k: stage_ms[k])
+    if stage_ms["sort"] > stage_ms[dominant]:
+        dom_note = "sort is longest; its bytes are not algorithmic, roofline given for the longest algorithmic step"
+    else:
+        dom_note = None
+    kname = {"count": "k_count", "scan": "k_scan", "scatter": "k_scatter"}[dominant]
+    ach = sb[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+    lit, withv = algorithmic_bytes(n, m, weighted)
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": load_traffic(kname, args.workload), "kernel": kname,
+            "algorithmic_bytes_per_launch": sb[dominant], "peak_kind": peak_kind}
+    if dom_note:
+        roof["note"] = dom_note
+    step_gbs = lit / (ms_step * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(plan, rp, ci, vv, n, m, weighted, args)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        rp_h = rp.cpu().numpy().view(np.uint64)
+        target = min(args.cpu_sample_edges, m)
+        R = int(np.searchsorted(rp_h, np.uint64(target), side="left"))
+        mS = int(rp_h[max(1, min(R, n))])
+        ci_h = ci[:mS].cpu().numpy().view(np.uint32)
+        vv_h = None if vv is None else vv[:mS].cpu().numpy()
+        mS, R, dt = cpu_baseline_sample(rp_h, ci_h, vv_h, target)
+        cpu = {"value": mS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"rows [0,{R}) of the workload: {mS} edges, all {n} vertices, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": dict(workload_config(args.workload, n, m, weighted), gt_config=plan.config().as_dict()),
+                "roofline": roof,
+                "step_hbm": {"gbs_formula": step_gbs, "frac_of_peak": step_gbs / peak,
+                             "frac_of_8tbs": step_gbs / 8000.0, "bytes_formula": lit, "bytes_with_vals_read": withv,
+                             "gbs_with_vals_read": withv / (ms_step * 1e-3) / 1e9},
+                "stage_ms": stage_ms, "stats": stats,
+                "coverage": stats["hdv_edges"] / max(1, m),
+                "clocks": clk.summary(),
+                "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+                "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(plan, rp, ci, vv, n, m, weighted, args):
+    """Same metric through gt_transpose_host: pinned host inputs copied in and
+    outputs copied out inside the timed region, every step."""
+    import torch
+    need = (8 * (n + 1) + 4 * m + (4 * m if weighted else 0)) * 2
+    avail = 0
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    if avail and need > 0.7 * avail:
+        return {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": f"host memory {avail / 2**30:.0f} GiB too small for {need / 2**30:.0f} GiB pinned buffers"}
+    h_rp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+    h_ci = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    h_vv = torch.empty(m, dtype=torch.float32, pin_memory=True) if weighted else None
+    h_cp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+    h_ri = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    h_vo = torch.empty(m, dtype=torch.float32, pin_memory=True) if weighted else None
+    h_rp.copy_(rp)
+    h_ci.copy_(ci)
+    if weighted:
+        h_vv.copy_(vv)
+    steps = max(1, min(args.steps, 3))
+    plan.transpose_host(h_rp, h_ci, h_vv, h_cp, h_ri, h_vo)  # warm-up (allocates device staging)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.transpose_host(h_rp, h_ci, h_vv, h_cp, h_ri, h_vo)
+    dt = (time.perf_counter() - t0) / steps
+    h2d = 8 * (n + 1) + 4 * m + (4 * m if weighted else 0)
+    d2h = h2d
+    return {"value": m / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

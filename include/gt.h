@@ -1,0 +1,166 @@
+/*
+ * gt.h -- C ABI of the GB300 graph-transposition library (libgt.so).
+ *
+ * Graph transposition (Sec. II-A of "On Optimizing Locality of Graph
+ * Transposition on Modern Architectures", PoTra) turns the CSR of a directed
+ * graph with n vertices and m edges (out-edge offsets row_ptr[n+1] and
+ * destination IDs col_idx[m], optionally one f32 value per edge) into its CSC
+ * (in-edge offsets col_ptr[n+1], source IDs row_idx[m], values carried
+ * bit-for-bit).  Every CSC list comes out in ascending source order, and
+ * parallel edges with the same (source, destination) keep their CSR order:
+ * the result is the stable sort of the CSR edge sequence by destination.
+ * The result never depends on the gt_config used.
+ *
+ * Method (all steps run in CUDA kernels for sm_103a; there is no CPU path):
+ *   Step 0  (Sec. IV-C, Step 0)  sample ceil(n * sample_permille / 1000)
+ *           random positions of col_idx, take the most frequent destinations
+ *           as high-degree vertices (HDV), build an open-addressing hash table
+ *           mapping HDV IDs to a compact index (Sec. IV-A).
+ *   Step 1  (Algorithm 2, Step 1)  in-degree count; HDV edges go to counters
+ *           private to a warp in shared memory, low-degree (LDV) edges to
+ *           global atomics aggregated per warp.
+ *   Step 2  (Algorithm 2, Step 2)  per-warp HDV counts are scanned into
+ *           per-warp insertion points, and one single-pass decoupled
+ *           look-back scan turns the degrees into col_ptr.
+ *   Step 3  (Algorithm 2, Step 3)  each warp revisits the same edges (the
+ *           part2tid rule); HDV edges take deterministic slots from its
+ *           private insertion points, LDV edges take slots from atomic
+ *           cursors (Algorithm 1, Step 3).
+ *   Sort    (Sec. II-B, optional sort)  LDV lists are sorted by source.
+ *
+ * Conventions
+ *   - Every array argument of gt_transpose* is a DEVICE pointer owned by the
+ *     caller (inputs are read only; outputs are written completely).  The
+ *     plan owns only its workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that enqueue work return once it is enqueued; errors
+ *     the host can see are returned at once, errors only the device can see
+ *     (out-of-range ID, bad row_ptr, timed-out wait) are latched in the plan's
+ *     status word and read with gt_plan_status() after the work completes.
+ *     Outputs are unspecified when any error is reported.
+ *   - Vertex IDs are u32 (n <= 2^32 - 1); edge offsets are u64
+ *     (m <= 2^32 for weighted graphs, see gt_plan_create).
+ *   - A plan may be used by one stream at a time.
+ */
+#ifndef GT_H_
+#define GT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gt_status {
+    GT_OK = 0,
+    GT_ERR_INVALID_ARG = 1,   /* null pointer, size mismatch, bad config field   */
+    GT_ERR_OUT_OF_RANGE = 2,  /* some col_idx[e] >= n (device-detected)           */
+    GT_ERR_BAD_ROW_PTR = 3,   /* row_ptr[0] != 0, decreasing, or row_ptr[n] != m  */
+    GT_ERR_NO_MEMORY = 4,     /* workspace allocation failed                       */
+    GT_ERR_CUDA = 5,          /* a CUDA runtime call failed                        */
+    GT_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired                */
+    GT_ERR_UNSUPPORTED = 7    /* size outside what this build handles              */
+} gt_status;
+
+/* Launch/method configuration.  Any valid configuration yields the same bytes. */
+typedef struct gt_config {
+    uint32_t hdv_k;           /* max number of HDV (0 = pure atomic, Algorithm 1)         */
+    uint32_t table_log2;      /* log2 of hash-table slots; 2^table_log2 >= 2*hdv_k       */
+    uint32_t block_threads;   /* threads per CTA for the count/scatter passes (64..1024, multiple of 32) */
+    uint32_t ctas_per_sm;     /* CTAs per SM for the count/scatter passes (1..32)          */
+    uint32_t warp_edges;      /* target edges per warp partition (>= 32)                   */
+    uint32_t stage_edges;     /* edges per bulk-copy stage per warp (0 = direct loads; else 128..4096, multiple of 128) */
+    uint32_t sample_permille; /* sample size in 1/1000 of n (Sec. IV-C uses 10 = 1 %)     */
+    uint32_t flags;           /* GT_FLAG_* bits                                            */
+    uint64_t seed;            /* seed of the sampling positions                            */
+} gt_config;
+
+#define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
+
+typedef struct gt_stats {
+    uint32_t hdv_selected;    /* HDV actually selected by Step 0 (<= hdv_k)  */
+    uint32_t partitions;      /* warp partitions of Steps 1 and 3            */
+    uint64_t hdv_edges;       /* edges whose destination is an HDV (coverage numerator, Sec. IV-B) */
+    uint64_t n_edges;         /* m                                           */
+    uint32_t ldv_sorted_cols; /* LDV lists of length >= 2 that were sorted    */
+    uint32_t large_cols;      /* of those, lists longer than one CTA's shared-memory sort */
+    uint32_t kernel_launches; /* kernels the last gt_transpose enqueued       */
+} gt_stats;
+
+/* Average device time per gt_transpose call, per step, over the calls made
+ * since timing was (re)enabled.  Measured with CUDA events recorded on the
+ * caller's stream between the steps. */
+typedef struct gt_timing {
+    uint32_t calls;
+    float sample_ms;   /* Step 0: sampling, HDV selection, hash table       */
+    float count_ms;    /* Step 1: partition bounds + in-degree count         */
+    float scan_ms;     /* Step 2: HDV insertion points + look-back scan      */
+    float scatter_ms;  /* Step 3: scatter                                    */
+    float sort_ms;     /* LDV list sort                                      */
+    float total_ms;
+} gt_timing;
+
+typedef struct gt_plan_s *gt_plan;
+
+/* Fills *cfg with the analytic default for a graph of this size (Eq. 1 sizing). */
+gt_status gt_default_config(gt_config *cfg, uint32_t n_vertices, uint64_t n_edges);
+
+/* Creates a plan for graphs with exactly n_vertices and n_edges.  has_vals != 0
+ * reserves the extra workspace of weighted graphs.  cfg == NULL takes
+ * gt_default_config.  The stream is used for workspace initialisation.
+ * Weighted graphs need n_edges <= 2^32; unweighted need n_edges < 2^63. */
+gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, int has_vals,
+                         const gt_config *cfg, void *stream);
+
+/* Replaces the configuration (reallocating workspace if needed). Synchronous. */
+gt_status gt_plan_set_config(gt_plan plan, const gt_config *cfg);
+gt_status gt_plan_get_config(gt_plan plan, gt_config *cfg);
+
+/* Enqueues the transposition (Steps 0-3 and the LDV sort) on `stream`.
+ * row_ptr: u64[n+1]; col_idx: u32[m]; vals: f32[m] or NULL;
+ * col_ptr: u64[n+1]; row_idx: u32[m]; vals_out: f32[m], NULL iff vals is NULL.
+ * Output arrays must not overlap inputs.  Row pointers are validated on the
+ * device (GT_ERR_BAD_ROW_PTR) and destinations range-checked (GT_ERR_OUT_OF_RANGE). */
+gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx,
+                       const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out,
+                       void *stream);
+
+/* Same as gt_transpose on HOST arrays (pinned memory recommended): copies the
+ * inputs to plan-owned device buffers, transposes, copies the outputs back and
+ * synchronises the stream.  Returns the device status as well. */
+gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx,
+                            const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
+                            float *vals_out, void *stream);
+
+/* Synchronises the plan's last stream and returns (then clears) the latched
+ * device status. */
+gt_status gt_plan_status(gt_plan plan);
+
+/* Statistics of the last completed gt_transpose (synchronises). */
+gt_status gt_plan_stats(gt_plan plan, gt_stats *stats);
+
+/* Starts (enable != 0, clearing earlier records) or stops per-step timing. */
+gt_status gt_plan_enable_timing(gt_plan plan, int enable);
+
+/* Averages of the recorded calls (synchronises the plan's stream). */
+gt_status gt_plan_timing(gt_plan plan, gt_timing *timing);
+
+/* Device bytes held by the plan's workspace. */
+uint64_t gt_plan_workspace_bytes(gt_plan plan);
+
+void gt_plan_destroy(gt_plan plan);
+
+const char *gt_status_string(gt_status status);
+
+/* Text of the last CUDA runtime error seen by this thread (GT_ERR_CUDA detail). */
+const char *gt_last_cuda_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+uint32_t gt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GT_H_ */

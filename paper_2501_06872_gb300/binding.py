@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libgt.so (include/gt.h): argument marshalling only.
+
+Every step of the transposition runs in the library's CUDA kernels; this
+module converts torch tensors / numpy arrays into pointers and sizes.  If the
+library has not been built, every call raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgt.so")
+
+GT_OK = 0
+STATUS = {0: "GT_OK", 1: "GT_ERR_INVALID_ARG", 2: "GT_ERR_OUT_OF_RANGE", 3: "GT_ERR_BAD_ROW_PTR",
+          4: "GT_ERR_NO_MEMORY", 5: "GT_ERR_CUDA", 6: "GT_ERR_TIMEOUT", 7: "GT_ERR_UNSUPPORTED"}
+FLAG_AGGREGATE = 1
+
+
+class GtError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("hdv_k", ctypes.c_uint32), ("table_log2", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("warp_edges", ctypes.c_uint32), ("stage_edges", ctypes.c_uint32),
+                ("sample_permille", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d):
+        c = cls()
+        for k, v in d.items():
+            setattr(c, k, int(v))
+        return c
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("hdv_selected", ctypes.c_uint32), ("partitions", ctypes.c_uint32),
+                ("hdv_edges", ctypes.c_uint64), ("n_edges", ctypes.c_uint64),
+                ("ldv_sorted_cols", ctypes.c_uint32), ("large_cols", ctypes.c_uint32),
+                ("kernel_launches", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_uint32), ("sample_ms", ctypes.c_float), ("count_ms", ctypes.c_float),
+                ("scan_ms", ctypes.c_float), ("scatter_ms", ctypes.c_float), ("sort_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan_get_config",
+           "gt_transpose", "gt_transpose_host", "gt_plan_status", "gt_plan_stats",
+           "gt_plan_enable_timing", "gt_plan_timing", "gt_plan_workspace_bytes", "gt_plan_destroy",
+           "gt_status_string", "gt_last_cuda_error", "gt_version"]
+
+
+def load():
+    """Loads libgt.so; raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    lib.gt_default_config.argtypes = [ctypes.POINTER(Config), u32, u64]
+    lib.gt_plan_create.argtypes = [ctypes.POINTER(P), u32, u64, ctypes.c_int, ctypes.POINTER(Config), P]
+    lib.gt_plan_set_config.argtypes = [P, ctypes.POINTER(Config)]
+    lib.gt_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
+    lib.gt_transpose.argtypes = [P, P, P, P, P, P, P, P]
+    lib.gt_transpose_host.argtypes = [P, P, P, P, P, P, P, P]
+    lib.gt_plan_status.argtypes = [P]
+    lib.gt_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.gt_plan_enable_timing.argtypes = [P, ctypes.c_int]
+    lib.gt_plan_timing.argtypes = [P, ctypes.POINTER(Timing)]
+    lib.gt_plan_workspace_bytes.argtypes = [P]
+    lib.gt_plan_workspace_bytes.restype = u64
+    lib.gt_plan_destroy.argtypes = [P]
+    lib.gt_plan_destroy.restype = None
+    lib.gt_status_string.argtypes = [ctypes.c_int]
+    lib.gt_status_string.restype = ctypes.c_char_p
+    lib.gt_version.restype = u32
+    lib.gt_last_cuda_error.restype = ctypes.c_char_p
+    for f in ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan_get_config",
+              "gt_transpose", "gt_transpose_host", "gt_plan_status", "gt_plan_stats",
+              "gt_plan_enable_timing", "gt_plan_timing"]:
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != GT_OK:
+        if rc == 5 and _lib is not None:
+            what = f"{what} ({_lib.gt_last_cuda_error().decode()})"
+        raise GtError(rc, what)
+
+
+def default_config(n: int, m: int) -> Config:
+    c = Config()
+    _check(load().gt_default_config(ctypes.byref(c), n, m), "gt_default_config")
+    return c
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owns a gt_plan (workspace for graphs with exactly n vertices, m edges)."""
+
+    def __init__(self, n: int, m: int, weighted: bool, config: Config | dict | None = None, stream=None):
+        lib = load()
+        self._lib = lib
+        self.n, self.m, self.weighted = int(n), int(m), bool(weighted)
+        h = ctypes.c_void_p()
+        if isinstance(config, dict):
+            config = Config.from_dict(config)
+        cfgp = ctypes.byref(config) if config is not None else None
+        _check(lib.gt_plan_create(ctypes.byref(h), self.n, self.m, int(self.weighted), cfgp,
+                                  _stream(stream) if stream is not None else None), "gt_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def config(self) -> Config:
+        c = Config()
+        _check(self._lib.gt_plan_get_config(self._h, ctypes.byref(c)), "gt_plan_get_config")
+        return c
+
+    def set_config(self, config: Config | dict):
+        if isinstance(config, dict):
+            config = Config.from_dict(config)
+        _check(self._lib.gt_plan_set_config(self._h, ctypes.byref(config)), "gt_plan_set_config")
+
+    def transpose(self, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
+        """Enqueue CSR -> CSC on device tensors (u64/int64 row_ptr, u32/int32 col_idx)."""
+        rc = self._lib.gt_transpose(self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
+                                    _ptr(row_idx), _ptr(vals_out), _stream(stream))
+        _check(rc, "gt_transpose")
+
+    def transpose_host(self, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
+        """CSR -> CSC on host arrays (pinned recommended); synchronous, returns status."""
+        rc = self._lib.gt_transpose_host(self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
+                                         _ptr(row_idx), _ptr(vals_out), _stream(stream))
+        _check(rc, "gt_transpose_host")
+
+    def status(self) -> int:
+        return self._lib.gt_plan_status(self._h)
+
+    def check(self):
+        _check(self.status(), "device status")
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.gt_plan_stats(self._h, ctypes.byref(s)), "gt_plan_stats")
+        return s.as_dict()
+
+    def enable_timing(self, on: bool = True):
+        _check(self._lib.gt_plan_enable_timing(self._h, int(on)), "gt_plan_enable_timing")
+
+    def timing(self) -> dict:
+        t = Timing()
+        _check(self._lib.gt_plan_timing(self._h, ctypes.byref(t)), "gt_plan_timing")
+        return t.as_dict()
+
+    def workspace_bytes(self) -> int:
+        return int(self._lib.gt_plan_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def transpose(row_ptr, col_idx, vals=None, config=None, stream=None, check=True):
+    """Convenience: allocate outputs (torch, same device) and transpose once."""
+    import torch
+    n = row_ptr.numel() - 1
+    m = col_idx.numel()
+    dev = col_idx.device if m else row_ptr.device
+    col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    row_idx = torch.empty(m, dtype=torch.int32, device=dev)
+    vals_out = torch.empty(m, dtype=torch.float32, device=dev) if vals is not None else None
+    plan = Plan(n, m, vals is not None, config, stream)
+    try:
+        plan.transpose(row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream)
+        if check:
+            plan.check()
+    finally:
+        plan.close()
+    return col_ptr, row_idx, vals_out

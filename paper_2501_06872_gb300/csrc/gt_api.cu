@@ -1,0 +1,448 @@
+// C ABI of libgt.so: plan management, workspace, argument checks.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "gt.h"
+#include "gt_device.cuh"
+#include "gt_internal.h"
+
+namespace gt {
+cudaError_t configure_steps();
+cudaError_t configure_sort();
+}  // namespace gt
+
+struct gt_plan_s {
+  gt::DevWork w;
+  gt_config cfg;
+  int device = 0;
+  cudaStream_t last = nullptr;
+  uint64_t ws_bytes = 0;
+  void *allocs[32] = {};
+  int nalloc = 0;
+  // device copies for gt_transpose_host (allocated on first use)
+  uint64_t *h_row_ptr = nullptr, *h_col_ptr = nullptr;
+  uint32_t *h_col_idx = nullptr, *h_row_idx = nullptr;
+  float *h_vals = nullptr, *h_vals_out = nullptr;
+  void *host_allocs[6] = {};
+  int nhost = 0;
+  // per-step timing
+  bool timing = false;
+  std::vector<gt::StepEvents> events;
+  uint32_t launches = 0;
+};
+
+namespace {
+void drop_events(gt_plan p) {
+  for (auto &e : p->events)
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(e.ev[i]);
+  p->events.clear();
+}
+}  // namespace
+
+namespace {
+
+uint32_t ceil_log2_u64(uint64_t x) {
+  uint32_t b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
+
+bool config_valid(const gt_config &c) {
+  if (c.hdv_k > (uint32_t)gt::kMaxHdv) return false;
+  if (c.hdv_k > 0) {
+    if (c.table_log2 < 1 || c.table_log2 > (uint32_t)gt::kMaxTableLog2) return false;
+    if ((1ull << c.table_log2) < 2ull * c.hdv_k) return false;
+  }
+  if (c.block_threads < 64 || c.block_threads > 1024 || c.block_threads % 32) return false;
+  if (c.ctas_per_sm < 1 || c.ctas_per_sm > 32) return false;
+  if (c.warp_edges < 32) return false;
+  if (c.stage_edges != 0 && (c.stage_edges < 128 || c.stage_edges > 4096 || c.stage_edges % 128)) return false;
+  if (c.sample_permille > 1000) return false;
+  return true;
+}
+
+// Derives the launch shape of Steps 1-3 from the configuration and sizes.
+gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
+  w.num_sms = num_sms;
+  w.kmax = (w.m > 0) ? c.hdv_k : 0;
+  w.tlog2 = w.kmax ? c.table_log2 : 0;
+  w.W = c.block_threads / 32;
+  uint64_t want = (w.m + (uint64_t)w.W * c.warp_edges - 1) / ((uint64_t)w.W * c.warp_edges);
+  uint64_t cap = (uint64_t)num_sms * c.ctas_per_sm;
+  if (want < 1) want = 1;
+  if (want > cap) want = cap;
+  w.G = (uint32_t)want;
+  w.P = w.G * w.W;
+  w.psize = w.m ? (w.m + w.P - 1) / w.P : 1;
+  if (w.psize == 0) w.psize = 1;
+  w.staged = c.stage_edges ? 1 : 0;
+  w.stage_edges = c.stage_edges;
+  w.smem_count = gt::smem_count_bytes(w.W, w.kmax, w.tlog2, w.staged, w.stage_edges, w.has_vals);
+  w.smem_scatter = gt::smem_scatter_bytes(w.W, w.kmax, w.tlog2, w.staged, w.stage_edges, w.has_vals);
+  if (w.smem_count > 227u * 1024u || w.smem_scatter > 227u * 1024u) return GT_ERR_INVALID_ARG;
+  uint64_t ns = w.kmax ? ((uint64_t)w.n * c.sample_permille + 999) / 1000 : 0;
+  if (ns > (1u << 22)) ns = 1u << 22;
+  if (w.m == 0) ns = 0;
+  w.ns = (uint32_t)ns;
+  w.ts_log2 = ceil_log2_u64(ns * 2 < 1024 ? 1024 : ns * 2);
+  w.ntiles = (uint32_t)((w.n + gt::kScanTile - 1) / gt::kScanTile);
+  if (w.ntiles == 0) w.ntiles = 1;
+  w.big_cap = (uint32_t)(w.m / (gt::kWarpSortCap + 1) + 1);
+  w.flag_mode = (w.has_vals && w.n <= 0x80000000u) ? 1 : 0;
+  return GT_OK;
+}
+
+gt_status plan_alloc(gt_plan p, void **ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (p->nalloc >= 32) return GT_ERR_NO_MEMORY;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return GT_ERR_NO_MEMORY;
+  }
+  p->allocs[p->nalloc++] = *ptr;
+  p->ws_bytes += bytes;
+  return GT_OK;
+}
+
+void plan_free_ws(gt_plan p) {
+  for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
+  p->nalloc = 0;
+  p->ws_bytes = 0;
+  gt::DevWork keep = p->w;
+  p->w = gt::DevWork();
+  p->w.n = keep.n;
+  p->w.m = keep.m;
+  p->w.has_vals = keep.has_vals;
+}
+
+gt_status plan_alloc_ws(gt_plan p) {
+  gt::DevWork &w = p->w;
+  const size_t n = w.n, m = w.m;
+  const size_t T = w.kmax ? ((size_t)1 << w.tlog2) : 1;
+  const size_t ts = (size_t)1 << w.ts_log2;
+  gt_status st;
+#define GT_AL(field, bytes)                                                    \
+  do {                                                                         \
+    if ((st = plan_alloc(p, (void **)&w.field, (bytes))) != GT_OK) return st; \
+  } while (0)
+  GT_AL(deg, n * 4);
+  GT_AL(cursor, n * 8);
+  GT_AL(hdv_cnt, (size_t)w.P * (w.kmax ? w.kmax : 1) * 4);
+  GT_AL(hdv_ids, (w.kmax ? w.kmax : 1) * 4);
+  GT_AL(hdv_start, (w.kmax ? w.kmax : 1) * 8);
+  GT_AL(hkeys, T * 4);
+  GT_AL(hvals, T * 2);
+  GT_AL(part, ((size_t)w.P + 1) * 8);
+  GT_AL(scan_state, (size_t)w.ntiles * 8);
+  GT_AL(status, 4);
+  GT_AL(meta, gt::kMetaCount * 4);
+  GT_AL(meta64, 4 * 8);
+  GT_AL(skeys, (w.kmax ? ts : 1) * 4);
+  GT_AL(scnt, (w.kmax ? ts : 1) * 4);
+  GT_AL(fhist, (w.kmax ? gt::kFreqBins : 1) * 4);
+  GT_AL(cand, (w.kmax ? w.kmax : 1) * 4);
+  GT_AL(ties, (w.kmax ? gt::kTieCap : 1) * 4);
+  GT_AL(biglist, (size_t)w.big_cap * 4);
+  GT_AL(scr_u, m * 4);
+  if (w.has_vals) GT_AL(scr_w, m * 4);
+#undef GT_AL
+  if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
+  if (cudaMemset(w.meta, 0, gt::kMetaCount * 4) != cudaSuccess) return GT_ERR_CUDA;
+  if (cudaMemset(w.meta64, 0, 32) != cudaSuccess) return GT_ERR_CUDA;
+  return GT_OK;
+}
+
+gt_status apply_config(gt_plan p, const gt_config &c) {
+  if (!config_valid(c)) return GT_ERR_INVALID_ARG;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return GT_ERR_CUDA;
+  gt::DevWork w;
+  w.n = p->w.n;
+  w.m = p->w.m;
+  w.has_vals = p->w.has_vals;
+  gt_status st = derive_shape(w, c, sms);
+  if (st != GT_OK) return st;
+  plan_free_ws(p);
+  p->w = w;
+  p->cfg = c;
+  st = plan_alloc_ws(p);
+  if (st != GT_OK) plan_free_ws(p);
+  return st;
+}
+
+thread_local const char *g_last_cuda = "no error";
+
+gt_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return GT_OK;
+  g_last_cuda = cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return GT_ERR_NO_MEMORY;
+  return GT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t gt_version(void) { return 100; }
+
+const char *gt_last_cuda_error(void) { return g_last_cuda; }
+
+const char *gt_status_string(gt_status s) {
+  switch (s) {
+    case GT_OK: return "ok";
+    case GT_ERR_INVALID_ARG: return "invalid argument";
+    case GT_ERR_OUT_OF_RANGE: return "col_idx entry out of range";
+    case GT_ERR_BAD_ROW_PTR: return "invalid row_ptr";
+    case GT_ERR_NO_MEMORY: return "out of device memory";
+    case GT_ERR_CUDA: return "CUDA runtime error";
+    case GT_ERR_TIMEOUT: return "bounded device wait expired";
+    case GT_ERR_UNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+gt_status gt_default_config(gt_config *cfg, uint32_t n_vertices, uint64_t n_edges) {
+  if (!cfg) return GT_ERR_INVALID_ARG;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->block_threads = 256;
+  cfg->ctas_per_sm = 4;
+  cfg->warp_edges = 4096;
+  cfg->stage_edges = 0;
+  cfg->sample_permille = 10;
+  cfg->flags = GT_FLAG_AGGREGATE;
+  cfg->seed = 0x5EED0001ull;
+  // Eq. 1 with the per-CTA shared memory of 4 CTAs/SM as |cache|, a 6-byte
+  // record at load factor 1/2, 8 bytes of per-CTA HDV data and one 4-byte
+  // counter per warp: k = 48 KB / (12 + 8 + 4*8) ~ 945 -> 512 (power of two).
+  uint32_t k = 512;
+  if (n_edges < (1ull << 18)) k = 0;
+  if (k > n_vertices / 2) {
+    k = 0;
+  }
+  cfg->hdv_k = k;
+  cfg->table_log2 = k ? ceil_log2_u64(2ull * k) : 0;
+  return GT_OK;
+}
+
+gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, int has_vals, const gt_config *cfg,
+                         void *stream) {
+  (void)stream;
+  if (!plan) return GT_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (has_vals && n_edges > (1ull << 32)) return GT_ERR_UNSUPPORTED;
+  if (n_edges >= (1ull << 62)) return GT_ERR_UNSUPPORTED;
+  if (n_vertices == 0 && n_edges != 0) return GT_ERR_INVALID_ARG;
+  gt_plan p = new (std::nothrow) gt_plan_s();
+  if (!p) return GT_ERR_NO_MEMORY;
+  cudaError_t ge = cudaGetDevice(&p->device);
+  if (ge != cudaSuccess) {
+    from_cuda(ge);
+    cudaGetLastError();
+    delete p;
+    return GT_ERR_CUDA;
+  }
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e1 = gt::configure_steps();
+    cudaError_t e2 = gt::configure_sort();
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      from_cuda(e1 != cudaSuccess ? e1 : e2);
+      cudaGetLastError();
+      delete p;
+      return GT_ERR_CUDA;
+    }
+    configured = true;
+  }
+  p->w.n = n_vertices;
+  p->w.m = n_edges;
+  p->w.has_vals = has_vals ? 1 : 0;
+  gt_config c;
+  if (cfg) c = *cfg;
+  else gt_default_config(&c, n_vertices, n_edges);
+  gt_status st = apply_config(p, c);
+  if (st != GT_OK) {
+    plan_free_ws(p);
+    delete p;
+    return st;
+  }
+  *plan = p;
+  return GT_OK;
+}
+
+gt_status gt_plan_set_config(gt_plan plan, const gt_config *cfg) {
+  if (!plan || !cfg) return GT_ERR_INVALID_ARG;
+  if (!config_valid(*cfg)) return GT_ERR_INVALID_ARG;
+  if (plan->last) cudaStreamSynchronize(plan->last);
+  return apply_config(plan, *cfg);
+}
+
+gt_status gt_plan_get_config(gt_plan plan, gt_config *cfg) {
+  if (!plan || !cfg) return GT_ERR_INVALID_ARG;
+  *cfg = plan->cfg;
+  return GT_OK;
+}
+
+gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                       uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+  if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
+  const gt::DevWork &w0 = plan->w;
+  if (w0.m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
+  if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
+  if (vals && !w0.has_vals) return GT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  plan->last = s;
+  if (w0.n == 0) return from_cuda(cudaMemsetAsync(col_ptr, 0, 8, s));
+  gt::DevWork w = w0;
+  // bulk copies need 16-byte aligned sources; fall back to direct loads otherwise
+  if (w.staged && ((((uintptr_t)col_idx) & 15u) || (vals && (((uintptr_t)vals) & 15u)))) {
+    w.staged = 0;
+    w.smem_count = gt::smem_count_bytes(w.W, w.kmax, w.tlog2, 0, 0, w.has_vals);
+    w.smem_scatter = gt::smem_scatter_bytes(w.W, w.kmax, w.tlog2, 0, 0, w.has_vals);
+  }
+  gt::Problem pb{row_ptr, col_idx, vals, col_ptr, row_idx, vals_out};
+  const gt::StepEvents *ev = nullptr;
+  if (plan->timing) {
+    gt::StepEvents e;
+    for (int i = 0; i < 6; ++i)
+      if (cudaEventCreate(&e.ev[i]) != cudaSuccess) return GT_ERR_CUDA;
+    plan->events.push_back(e);
+    ev = &plan->events.back();
+  }
+  return from_cuda(gt::run_transpose(w, plan->cfg, pb, s, ev, &plan->launches));
+}
+
+gt_status gt_plan_enable_timing(gt_plan plan, int enable) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  if (plan->last) cudaStreamSynchronize(plan->last);
+  drop_events(plan);
+  plan->timing = enable != 0;
+  return GT_OK;
+}
+
+gt_status gt_plan_timing(gt_plan plan, gt_timing *t) {
+  if (!plan || !t) return GT_ERR_INVALID_ARG;
+  memset(t, 0, sizeof(*t));
+  if (plan->events.empty()) return GT_OK;
+  if (cudaEventSynchronize(plan->events.back().ev[5]) != cudaSuccess) return GT_ERR_CUDA;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (auto &e : plan->events) {
+    for (int i = 0; i < 5; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.ev[i], e.ev[i + 1]) != cudaSuccess) return GT_ERR_CUDA;
+      acc[i] += ms;
+    }
+  }
+  const double c = (double)plan->events.size();
+  t->calls = (uint32_t)plan->events.size();
+  t->sample_ms = (float)(acc[0] / c);
+  t->count_ms = (float)(acc[1] / c);
+  t->scan_ms = (float)(acc[2] / c);
+  t->scatter_ms = (float)(acc[3] / c);
+  t->sort_ms = (float)(acc[4] / c);
+  t->total_ms = (float)((acc[0] + acc[1] + acc[2] + acc[3] + acc[4]) / c);
+  return GT_OK;
+}
+
+gt_status gt_plan_status(gt_plan plan) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  {
+    cudaError_t se = cudaStreamSynchronize(plan->last);
+    if (se != cudaSuccess) return from_cuda(se);
+  }
+  uint32_t st = 0;
+  {
+    cudaError_t ce = cudaMemcpy(&st, plan->w.status, 4, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return from_cuda(ce);
+  }
+  if (st) cudaMemset(plan->w.status, 0, 4);
+  return (gt_status)st;
+}
+
+gt_status gt_plan_stats(gt_plan plan, gt_stats *stats) {
+  if (!plan || !stats) return GT_ERR_INVALID_ARG;
+  {
+    cudaError_t se = cudaStreamSynchronize(plan->last);
+    if (se != cudaSuccess) return from_cuda(se);
+  }
+  uint32_t meta[gt::kMetaCount];
+  unsigned long long m64[4];
+  if (cudaMemcpy(meta, plan->w.meta, sizeof(meta), cudaMemcpyDeviceToHost) != cudaSuccess) return GT_ERR_CUDA;
+  if (cudaMemcpy(m64, plan->w.meta64, sizeof(m64), cudaMemcpyDeviceToHost) != cudaSuccess) return GT_ERR_CUDA;
+  memset(stats, 0, sizeof(*stats));
+  stats->hdv_selected = plan->w.kmax ? meta[gt::kMetaK] : 0;
+  stats->partitions = plan->w.P;
+  stats->hdv_edges = m64[0];
+  stats->n_edges = plan->w.m;
+  stats->ldv_sorted_cols = meta[gt::kMetaSorted];
+  stats->large_cols = meta[gt::kMetaLarge];
+  stats->kernel_launches = plan->launches;
+  return GT_OK;
+}
+
+uint64_t gt_plan_workspace_bytes(gt_plan plan) { return plan ? plan->ws_bytes : 0; }
+
+gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                            uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+  if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
+  const size_t n = plan->w.n, m = plan->w.m;
+  if (m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
+  if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
+  if (vals && !plan->w.has_vals) return GT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!plan->h_row_ptr) {
+    void *q;
+#define GT_HA(field, bytes)                                              \
+  do {                                                                   \
+    if (cudaMalloc(&q, (bytes) ? (bytes) : 16) != cudaSuccess) {         \
+      cudaGetLastError();                                                \
+      return GT_ERR_NO_MEMORY;                                           \
+    }                                                                    \
+    plan->host_allocs[plan->nhost++] = q;                                \
+    plan->field = (decltype(plan->field))q;                              \
+  } while (0)
+    GT_HA(h_row_ptr, (n + 1) * 8);
+    GT_HA(h_col_ptr, (n + 1) * 8);
+    GT_HA(h_col_idx, m * 4);
+    GT_HA(h_row_idx, m * 4);
+    if (plan->w.has_vals) {
+      GT_HA(h_vals, m * 4);
+      GT_HA(h_vals_out, m * 4);
+    }
+#undef GT_HA
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return from_cuda(e);
+  if (m && (e = cudaMemcpyAsync(plan->h_col_idx, col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return from_cuda(e);
+  if (vals && m && (e = cudaMemcpyAsync(plan->h_vals, vals, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return from_cuda(e);
+  gt_status st = gt_transpose(plan, plan->h_row_ptr, plan->h_col_idx, vals ? plan->h_vals : nullptr,
+                              plan->h_col_ptr, plan->h_row_idx, vals ? plan->h_vals_out : nullptr, stream);
+  if (st != GT_OK) return st;
+  if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return from_cuda(e);
+  if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx, m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return from_cuda(e);
+  if (vals && m &&
+      (e = cudaMemcpyAsync(vals_out, plan->h_vals_out, m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return from_cuda(e);
+  return gt_plan_status(plan);
+}
+
+void gt_plan_destroy(gt_plan plan) {
+  if (!plan) return;
+  if (plan->last) cudaStreamSynchronize(plan->last);
+  drop_events(plan);
+  plan_free_ws(plan);
+  for (int i = 0; i < plan->nhost; ++i) cudaFree(plan->host_allocs[i]);
+  delete plan;
+}
+
+}  // extern "C"

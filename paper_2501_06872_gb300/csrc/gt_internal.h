@@ -1,0 +1,82 @@
+// Host-side view of a plan's device workspace and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gt.h"
+
+namespace gt {
+
+constexpr uint32_t kFreqBins = 1u << 16;   // sample-frequency histogram bins
+constexpr uint32_t kTieCap = 8192;         // tie candidates kept at the threshold
+constexpr uint32_t kScanTile = 4096;       // elements per decoupled-look-back tile
+constexpr uint32_t kSortSmemCap = 4096;    // longest list sorted in one CTA's shared memory
+constexpr uint32_t kWarpSortCap = 32;      // longest list sorted in one warp's registers
+
+struct DevWork {
+  // sizes and derived launch shape
+  uint32_t n = 0;
+  uint64_t m = 0;
+  int has_vals = 0;
+  uint32_t kmax = 0, tlog2 = 0, W = 0, G = 0, P = 0;
+  uint64_t psize = 0;
+  uint32_t ns = 0, ts_log2 = 0;
+  uint32_t ntiles = 0;
+  uint32_t big_cap = 0;
+  int flag_mode = 0;  // split-row duplicate ordering via row_idx bit 31 (weighted, n <= 2^31)
+  int staged = 0;     // bulk-copy staging of col_idx/vals tiles
+  uint32_t stage_edges = 0;
+  uint32_t smem_count = 0, smem_scatter = 0;
+  int num_sms = 0;
+  // buffers (device)
+  uint32_t *deg = nullptr;                   // [n]
+  unsigned long long *cursor = nullptr;      // [n]
+  uint32_t *hdv_cnt = nullptr;               // [P * kmax]
+  uint32_t *hdv_ids = nullptr;               // [kmax]
+  unsigned long long *hdv_start = nullptr;   // [kmax]
+  uint32_t *hkeys = nullptr;                 // [2^tlog2]
+  uint16_t *hvals = nullptr;                 // [2^tlog2]
+  unsigned long long *part = nullptr;        // [P + 1]
+  unsigned long long *scan_state = nullptr;  // [ntiles]
+  uint32_t *status = nullptr;                // [1]
+  uint32_t *meta = nullptr;                  // [kMetaCount]
+  unsigned long long *meta64 = nullptr;      // [4]
+  uint32_t *skeys = nullptr, *scnt = nullptr;  // [2^ts_log2]
+  uint32_t *fhist = nullptr;                   // [kFreqBins]
+  uint32_t *cand = nullptr;                    // [kmax]
+  uint32_t *ties = nullptr;                    // [kTieCap]
+  uint32_t *biglist = nullptr;                 // [big_cap]
+  uint32_t *scr_u = nullptr;                   // [m] radix ping-pong
+  float *scr_w = nullptr;                      // [m] (weighted)
+};
+
+struct Problem {
+  const uint64_t *row_ptr;
+  const uint32_t *col_idx;
+  const float *vals;
+  uint64_t *col_ptr;
+  uint32_t *row_idx;
+  float *vals_out;
+};
+
+// Events recorded between the steps of one call (null = not timed).
+struct StepEvents {
+  cudaEvent_t ev[6];
+};
+
+// Enqueues the whole transposition on `stream`.  Returns cudaSuccess or the
+// first launch error; *launches receives the number of kernels enqueued.
+cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem &pb, cudaStream_t stream,
+                          const StepEvents *events, uint32_t *launches);
+
+// Shared-memory bytes needed by the count / scatter kernels for a shape.
+uint32_t smem_count_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged, uint32_t stage_edges,
+                          int has_vals);
+uint32_t smem_scatter_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged, uint32_t stage_edges,
+                            int has_vals);
+
+// Raises the dynamic shared-memory limits of the kernels once per process.
+cudaError_t configure_kernels();
+
+}  // namespace gt

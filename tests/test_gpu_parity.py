@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit-exact.
+
+Integer outputs (col_ptr, row_idx) and the carried f32 value bits must be
+identical; every configuration must give the same bytes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_06872_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _to_dev(row_ptr, col_idx, vals):
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(np.ascontiguousarray(row_ptr).view(np.int64)).to(dev)
+    ci = torch.from_numpy(np.ascontiguousarray(col_idx, dtype=np.uint32).view(np.int32)).to(dev)
+    vv = None if vals is None else torch.from_numpy(np.ascontiguousarray(vals, dtype=np.float32)).to(dev)
+    return rp, ci, vv
+
+
+def gpu_transpose(row_ptr, col_idx, vals=None, cfg=None, check=True):
+    from paper_2501_06872_gb300 import binding
+    rp, ci, vv = _to_dev(row_ptr, col_idx, vals)
+    out = binding.transpose(rp, ci, vv, config=cfg, check=check)
+    torch.cuda.synchronize()
+    cp = out[0].cpu().numpy().view(np.uint64)
+    ri = out[1].cpu().numpy().view(np.uint32)
+    vo = None if out[2] is None else out[2].cpu().numpy()
+    return cp, ri, vo
+
+
+def assert_same(got, exp):
+    assert np.array_equal(got[0], exp[0]), "col_ptr differs"
+    if not np.array_equal(got[1], exp[1]):
+        bad = np.nonzero(got[1] != exp[1])[0]
+        raise AssertionError(f"row_idx differs at {bad.size} slots, first {bad[:8]}")
+    if exp[2] is not None:
+        assert np.array_equal(got[2].view(np.uint32), exp[2].view(np.uint32)), "vals differ"
+
+
+def config(**kw):
+    from paper_2501_06872_gb300 import binding
+    base = dict(hdv_k=0, table_log2=0, block_threads=256, ctas_per_sm=4, warp_edges=256, stage_edges=0,
+                sample_permille=10, flags=1, seed=7)
+    base.update(kw)
+    if base["hdv_k"] and not base["table_log2"]:
+        base["table_log2"] = max(1, (2 * base["hdv_k"] - 1).bit_length())
+    return binding.Config.from_dict(base)
+
+
+CONFIGS = {
+    "atomic": dict(hdv_k=0),
+    "hdv64": dict(hdv_k=64, warp_edges=128),
+    "hdv512_staged": dict(hdv_k=512, stage_edges=256, warp_edges=512),
+    "hdv4096_w1024": dict(hdv_k=4096, table_log2=13, block_threads=128, ctas_per_sm=1, warp_edges=2048),
+    "noagg_staged": dict(hdv_k=16, flags=0, stage_edges=128),
+    "big_blocks": dict(hdv_k=128, block_threads=1024, ctas_per_sm=1, warp_edges=64),
+}
+
+
+def test_fig1_reconstruction():
+    row_ptr = np.array([0, 2, 3, 4, 6], np.uint64)
+    col_idx = np.array([1, 2, 2, 3, 0, 1], np.uint32)
+    assert_same(gpu_transpose(row_ptr, col_idx), oracle.transpose(row_ptr, col_idx))
+
+
+def test_empty_and_degenerate():
+    # no edges
+    rp = np.zeros(9, np.uint64)
+    got = gpu_transpose(rp, np.zeros(0, np.uint32))
+    assert np.array_equal(got[0], np.zeros(9, np.uint64))
+    # single vertex, weighted self-loops (order of parallel edges = CSR order)
+    rp = np.array([0, 5], np.uint64)
+    ci = np.zeros(5, np.uint32)
+    vv = np.array([5, 4, 3, 2, 1], np.float32)
+    assert_same(gpu_transpose(rp, ci, vv), oracle.transpose(rp, ci, vv))
+    # all edges into the last vertex, long enough for the radix path
+    n = 20000
+    rp = np.arange(n + 1, dtype=np.uint64)
+    ci = np.full(n, n - 1, np.uint32)
+    vv = np.arange(n, dtype=np.float32)
+    for name in ["atomic", "hdv64"]:
+        assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), oracle.transpose(rp, ci, vv))
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_graphs_all_configs(name, seed):
+    n, rp, ci, vv = inputs.random_csr(5000, 77777, seed=seed, weighted=True, hot=20, hot_frac=0.4)
+    assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), oracle.transpose(rp, ci, vv))
+    assert_same(gpu_transpose(rp, ci, None, config(**CONFIGS[name])), oracle.transpose(rp, ci, None))
+
+
+@pytest.mark.parametrize("order", ["natural", "random", "degree"])
+def test_rmat_numpy_scale14(order):
+    n, rp, ci, vv = inputs.rmat_csr(14, 16, seed=3, order=order, weighted=True)
+    exp = oracle.transpose(rp, ci, vv)
+    for name in ["atomic", "hdv512_staged", "big_blocks"]:
+        assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
+    assert_same(gpu_transpose(rp, ci, vv), exp)  # default configuration
+
+
+def test_split_rows_with_parallel_edges():
+    """Hub rows much longer than a partition, with many parallel edges into
+    LDV lists of all lengths: partitions split the rows, and parallel edges
+    must keep CSR order."""
+    rng = np.random.default_rng(5)
+    n = 3000
+    rows = []
+    for u in range(n):
+        if u in (0, 7, 1500):
+            d = rng.integers(0, 40, size=30000)  # few destinations, many repeats
+            d = np.where(rng.random(30000) < 0.5, d, rng.integers(0, n, size=30000))
+        else:
+            d = rng.integers(0, n, size=rng.integers(0, 6))
+        rows.append(d.astype(np.uint32))
+    rp = np.zeros(n + 1, np.uint64)
+    rp[1:] = np.cumsum([r.size for r in rows])
+    ci = np.concatenate(rows).astype(np.uint32)
+    vv = rng.standard_normal(ci.size).astype(np.float32)
+    exp = oracle.transpose(rp, ci, vv)
+    for cfg in [config(hdv_k=0, warp_edges=64), config(hdv_k=8, warp_edges=128, stage_edges=128),
+                config(hdv_k=0, warp_edges=4096, block_threads=64)]:
+        assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
+
+
+def test_ragged_edge_counts_and_empty_rows():
+    for m in [1, 3, 5, 31, 33, 129, 1023, 4097]:
+        n = 257
+        key = np.random.default_rng(m)
+        src = np.sort(key.integers(0, n, size=m) // 3 * 3)  # two thirds of rows empty
+        dst = key.integers(0, n, size=m)
+        rp, ci, _ = inputs.csr_from_edges(n, src.astype(np.uint32), dst.astype(np.uint32))
+        vv = key.standard_normal(m).astype(np.float32)
+        exp = oracle.transpose(rp, ci, vv)
+        for name in ["atomic", "noagg_staged", "hdv512_staged"]:
+            assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
+
+
+def test_errors_are_reported_not_faulted():
+    from paper_2501_06872_gb300 import binding
+    rp = np.array([0, 2, 3, 4], np.uint64)
+    ci = np.array([1, 2, 3, 0], np.uint32)  # 3 >= n
+    with pytest.raises(binding.GtError) as ei:
+        gpu_transpose(rp, ci)
+    assert ei.value.code == 2
+    rp = np.array([0, 3, 2, 4], np.uint64)  # decreasing
+    ci = np.array([1, 2, 0, 0], np.uint32)
+    with pytest.raises(binding.GtError) as ei:
+        gpu_transpose(rp, ci)
+    assert ei.value.code == 3
+    rp = np.array([0, 1, 2, 3], np.uint64)  # row_ptr[n] != m
+    ci = np.array([1, 2, 0, 0], np.uint32)
+    with pytest.raises(binding.GtError) as ei:
+        gpu_transpose(rp, ci)
+    assert ei.value.code == 3
+
+
+def test_host_path_matches_device_path():
+    from paper_2501_06872_gb300 import binding
+    n, rp, ci, vv = inputs.rmat_csr(12, 8, seed=4, order="random", weighted=True)
+    m = ci.size
+    plan = binding.Plan(n, m, True, config(hdv_k=64))
+    cp = np.empty(n + 1, np.uint64)
+    ri = np.empty(m, np.uint32)
+    vo = np.empty(m, np.float32)
+    for _ in range(2):
+        plan.transpose_host(rp, ci, vv, cp, ri, vo)
+        assert_same((cp, ri, vo), oracle.transpose(rp, ci, vv))
+    plan.close()
+
+
+def test_plan_reuse_and_stats():
+    from paper_2501_06872_gb300 import binding
+    n, rp, ci, vv = inputs.rmat_csr(13, 16, seed=2, order="degree", weighted=True)
+    exp = oracle.transpose(rp, ci, vv)
+    d_rp, d_ci, d_vv = _to_dev(rp, ci, vv)
+    m = ci.size
+    plan = binding.Plan(n, m, True, config(hdv_k=256, warp_edges=512))
+    cp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    ri = torch.empty(m, dtype=torch.int32, device="cuda")
+    vo = torch.empty(m, dtype=torch.float32, device="cuda")
+    plan.enable_timing(True)
+    for _ in range(3):
+        plan.transpose(d_rp, d_ci, d_vv, cp, ri, vo)
+        plan.check()
+        assert_same((cp.cpu().numpy().view(np.uint64), ri.cpu().numpy().view(np.uint32), vo.cpu().numpy()), exp)
+    st = plan.stats()
+    t = plan.timing()
+    assert st["hdv_selected"] > 0 and 0 < st["hdv_edges"] < m and st["kernel_launches"] >= 8
+    assert t["calls"] == 3 and t["total_ms"] > 0
+    # every list of an HDV is long: coverage is the fraction of edges into them
+    plan.set_config(config(hdv_k=0))
+    plan.transpose(d_rp, d_ci, d_vv, cp, ri, vo)
+    plan.check()
+    assert plan.stats()["hdv_edges"] == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("kind,order,weighted", [("rmat", "natural", False), ("rmat", "degree", True),
+                                                  ("er", "random", True)])
+def test_gpu_generated_scale16(kind, order, weighted):
+    """R-MAT scale 16 (65,536 vertices, 1,048,576 edges) and a uniform graph of
+    the same size, generated on the GPU, against the oracle."""
+    from paper_2501_06872_gb300 import binding
+    from paper_2501_06872_gb300.inputs import gpu as ggen
+    n, rp, ci, vv = ggen.graph(16, 16, kind=kind, seed=0x5EED0001, order=order, weighted=weighted)
+    h_rp = rp.cpu().numpy().view(np.uint64)
+    h_ci = ci.cpu().numpy().view(np.uint32)
+    h_vv = None if vv is None else vv.cpu().numpy()
+    exp = oracle.transpose(h_rp, h_ci, h_vv)
+    out = binding.transpose(rp, ci, vv)
+    got = (out[0].cpu().numpy().view(np.uint64), out[1].cpu().numpy().view(np.uint32),
+           None if vv is None else out[2].cpu().numpy())
+    assert_same(got, exp)
