@@ -133,6 +133,23 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
                             const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
                             float *vals_out, void *stream);
 
+/* Allocation-free variant of gt_transpose (no counterpart in the paper).
+ * For callers that must not allocate device memory on the call path, e.g. a
+ * host program whose pool already owns all device memory, or a latency-
+ * critical loop that cannot take the synchronisation cudaMalloc/cudaFree may
+ * cause.  The caller passes device inputs/outputs exactly as for
+ * gt_transpose; the workspace comes from a fixed 64 MiB array that every GPU
+ * loading this library holds until the process exits.  Graphs whose
+ * workspace does not fit (roughly 12 bytes per vertex plus 4 bytes per edge,
+ * 8 with values) return GT_ERR_UNSUPPORTED.  Runs the pure-atomic
+ * configuration, synchronises `stream`, and returns the device status.  All
+ * calls share the array: calls that overlap on the GPU race.  The first call
+ * on a device performs a one-time set-up (looks up the array's address, sets
+ * kernel limits) and should come before any stream capture on that device. */
+gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
+                               const uint32_t *col_idx, const float *vals, uint64_t *col_ptr,
+                               uint32_t *row_idx, float *vals_out, void *stream);
+
 /* Synchronises the plan's last stream and returns (then clears) the latched
  * device status. */
 gt_status gt_plan_status(gt_plan plan);

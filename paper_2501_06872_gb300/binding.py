@@ -66,7 +66,7 @@ _lib = None
 EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan_get_config",
            "gt_transpose", "gt_transpose_host", "gt_plan_status", "gt_plan_stats",
            "gt_plan_enable_timing", "gt_plan_timing", "gt_plan_workspace_bytes", "gt_plan_destroy",
-           "gt_status_string", "gt_last_cuda_error", "gt_version"]
+           "gt_status_string", "gt_last_cuda_error", "gt_version", "gt_transpose_noalloc"]
 
 
 def load():
@@ -87,6 +87,8 @@ def load():
     lib.gt_transpose_host.argtypes = [P, P, P, P, P, P, P, P]
     lib.gt_plan_status.argtypes = [P]
     lib.gt_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.gt_transpose_noalloc.argtypes = [u32, u64, P, P, P, P, P, P, P]
+    lib.gt_transpose_noalloc.restype = ctypes.c_int
     lib.gt_plan_enable_timing.argtypes = [P, ctypes.c_int]
     lib.gt_plan_timing.argtypes = [P, ctypes.POINTER(Timing)]
     lib.gt_plan_workspace_bytes.argtypes = [P]
@@ -208,6 +210,16 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def transpose_noalloc(row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
+    """gt_transpose_noalloc on caller-owned device tensors (no device allocation
+    inside the call; synchronous).  Raises GtError on any non-OK status."""
+    n = row_ptr.numel() - 1
+    m = col_idx.numel()
+    rc = load().gt_transpose_noalloc(n, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
+                                     _ptr(row_idx), _ptr(vals_out), _stream(stream))
+    _check(rc, "gt_transpose_noalloc")
 
 
 def transpose(row_ptr, col_idx, vals=None, config=None, stream=None, check=True):
