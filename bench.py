@@ -34,6 +34,9 @@ WORKLOADS = {
     "rmat20-degree": ("rmat", 20, 16, "degree", True),
     "rmat22-degree": ("rmat", 22, 16, "degree", True),
     "rmat24-degree": ("rmat", 24, 16, "degree", True),
+    "rmat25-degree": ("rmat", 25, 16, "degree", True),
+    "rmat26-degree": ("rmat", 26, 16, "degree", True),
+    "rmat27-degree": ("rmat", 27, 16, "degree", True),
 }
 SEED = 0x5EED0003
 

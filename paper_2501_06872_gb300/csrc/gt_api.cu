@@ -92,7 +92,7 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   w.ts_log2 = ceil_log2_u64(ns * 2 < 1024 ? 1024 : ns * 2);
   w.ntiles = (uint32_t)((w.n + gt::kScanTile - 1) / gt::kScanTile);
   if (w.ntiles == 0) w.ntiles = 1;
-  w.big_cap = (uint32_t)(w.m / (gt::kWarpSortCap + 1) + 1);
+  w.big_cap = (uint32_t)gt::worklist_entries(w.m);
   w.flag_mode = (w.has_vals && w.n <= 0x80000000u) ? 1 : 0;
   return GT_OK;
 }
@@ -149,8 +149,7 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(cand, (w.kmax ? w.kmax : 1) * 4);
   GT_AL(ties, (w.kmax ? gt::kTieCap : 1) * 4);
   GT_AL(biglist, (size_t)w.big_cap * 4);
-  GT_AL(scr_u, m * 4);
-  if (w.has_vals) GT_AL(scr_w, m * 4);
+  GT_AL(scratch, m * (w.has_vals ? 8 : 4));
 #undef GT_AL
   if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
   if (cudaMemset(w.meta, 0, gt::kMetaCount * 4) != cudaSuccess) return GT_ERR_CUDA;
@@ -380,7 +379,7 @@ gt_status gt_plan_stats(gt_plan plan, gt_stats *stats) {
   stats->hdv_edges = m64[0];
   stats->n_edges = plan->w.m;
   stats->ldv_sorted_cols = meta[gt::kMetaSorted];
-  stats->large_cols = meta[gt::kMetaLarge];
+  stats->large_cols = meta[gt::kMetaLargeN];
   stats->kernel_launches = plan->launches;
   return GT_OK;
 }

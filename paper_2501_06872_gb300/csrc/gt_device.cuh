@@ -26,6 +26,10 @@ enum MetaIdx : int {
   kMetaSorted = 7,   // LDV lists of length >= 2 that were sorted
   kMetaLarge = 8,    // of those, handled by the radix path
   kMetaScanTicket = 9,
+  kMetaMid = 10,         // lists for the warp sort
+  kMetaMidTicket = 11,
+  kMetaLargeN = 12,      // lists for the radix sort
+  kMetaLargeTicket = 13,
   kMetaCount = 16
 };
 

@@ -11,8 +11,14 @@ namespace gt {
 constexpr uint32_t kFreqBins = 1u << 16;   // sample-frequency histogram bins
 constexpr uint32_t kTieCap = 8192;         // tie candidates kept at the threshold
 constexpr uint32_t kScanTile = 4096;       // elements per decoupled-look-back tile
-constexpr uint32_t kSortSmemCap = 4096;    // longest list sorted in one CTA's shared memory
+constexpr uint32_t kSortSmemCap = 2048;    // longest list sorted in one CTA's shared memory
+constexpr uint32_t kMidCap = 256;          // longest list sorted in one warp's shared-memory slice
 constexpr uint32_t kWarpSortCap = 32;      // longest list sorted in one warp's registers
+
+// Entries of the sort worklists (mid | big | large regions) for m edges.
+inline uint64_t worklist_entries(uint64_t m) {
+  return m / (kWarpSortCap + 1) + m / (kMidCap + 1) + m / (kSortSmemCap + 1) + 3;
+}
 
 struct DevWork {
   // sizes and derived launch shape
@@ -47,8 +53,10 @@ struct DevWork {
   uint32_t *cand = nullptr;                    // [kmax]
   uint32_t *ties = nullptr;                    // [kTieCap]
   uint32_t *biglist = nullptr;                 // [big_cap]
-  uint32_t *scr_u = nullptr;                   // [m] radix ping-pong
-  float *scr_w = nullptr;                      // [m] (weighted)
+  // [m] entries: weighted graphs keep LDV entries here as u64 (value bits << 32 |
+  // source, bit 31 of the source tagging split rows) until the LDV sort moves them
+  // to the outputs; both kinds reuse it as the radix sort's second buffer.
+  void *scratch = nullptr;
 };
 
 struct Problem {

@@ -120,7 +120,7 @@ extern "C" gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges,
   w.ns = 0;
   w.ts_log2 = 10;
   w.ntiles = (uint32_t)((n_vertices + gt::kScanTile - 1) / gt::kScanTile);
-  w.big_cap = (uint32_t)(n_edges / (gt::kWarpSortCap + 1) + 1);
+  w.big_cap = (uint32_t)gt::worklist_entries(n_edges);
   w.flag_mode = (w.has_vals && n_vertices <= 0x80000000u) ? 1 : 0;
 
   // carve the workspace out of the static array
@@ -150,8 +150,7 @@ extern "C" gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges,
   w.cand = (uint32_t *)take(16);
   w.ties = (uint32_t *)take(16);
   w.biglist = (uint32_t *)take((size_t)w.big_cap * 4);
-  w.scr_u = (uint32_t *)take(m * 4);
-  w.scr_w = vals ? (float *)take(m * 4) : nullptr;
+  w.scratch = take(m * (vals ? 8 : 4));
   if (off > kNoAllocBytes) return GT_ERR_UNSUPPORTED;  // graph too large for the fixed scratch
 
   gt::Problem pb{row_ptr, col_idx, vals, col_ptr, row_idx, vals_out};

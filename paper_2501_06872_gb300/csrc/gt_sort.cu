@@ -2,12 +2,21 @@
 // every LDV list of the CSC is ordered by source.  HDV lists are skipped:
 // their slots were assigned in edge order, which is already source order.
 //
-// Ties (parallel edges u->v) keep CSR order.  LDV slots of one warp were
-// assigned in edge order, so a sort that is stable with respect to the
-// current slot order is enough, except for rows shared by two partitions
-// ("split rows"), whose entries carry a tag (bit 31 of row_idx) and their
-// position inside the row (in the value slot); those are ordered by that
+// Ties (parallel edges u->v) keep CSR order.  The LDV slots one warp takes in
+// a list increase along its edges, so a sort that is stable with respect to
+// the slot order is enough -- except for rows shared by two partitions
+// ("split rows"), whose entries carry a tag (bit 31 of the source) and their
+// position inside the row in place of the value; those are ordered by that
 // position and their values are re-read from the input.
+//
+// Data flow.  Weighted graphs: the scatter left every LDV entry in the packed
+// scratch array (u64: value bits << 32 | source); this pass sorts each list
+// and writes row_idx / vals_out.  Unweighted graphs: the scatter wrote
+// row_idx directly and lists are sorted in place.
+//
+// List classes (by length L): 1 copy; 2..32 one warp, registers; 33..256
+// one warp, its own shared-memory slice; 257..2048 one CTA, shared memory
+// (all bitonic on a unique key); > 2048 stable LSD radix through scratch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,72 +29,72 @@ struct SortArgs {
   uint32_t n;
   const uint64_t *col_ptr;
   const uint64_t *row_ptr;
-  const float *vals;  // input values (for tagged entries)
+  const float *vals;  // input values (tagged entries re-read theirs)
   uint32_t *row_idx;
   float *vals_out;
+  unsigned long long *ldv64;  // weighted: packed LDV entries [m]
+  uint32_t *scr32;            // unweighted: radix second buffer [m]
   const uint32_t *hkeys;
   const uint16_t *hvals;
   uint32_t tlog2, kmax;
   uint32_t *meta;
-  uint32_t *biglist;
-  uint32_t big_cap;
+  uint32_t *midlist, *biglist, *largelist;
+  uint32_t mid_cap, big_cap, large_cap;
   uint32_t *status;
   int flag_mode;
-  uint32_t *scr_u;
-  float *scr_w;
   uint32_t key_bits;  // bits of a vertex ID (ceil(log2 n))
 };
 
-// ---------------------------------------------------------------------------
-// Element encoding for the comparison sorts.
-//   weighted:   key = (u << 32) | (tagged ? pos_in_row : index_in_list), payload = value bits or pos
-//   unweighted: key = u  (equal keys are indistinguishable)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void finish_entry(const SortArgs &a, uint64_t key, uint32_t pay, uint32_t tag,
-                                             uint64_t slot) {
-  uint32_t u = (uint32_t)(key >> 32);
+struct WarpSync {
+  __device__ void operator()() const { __syncwarp(); }
+};
+struct CtaSync {
+  __device__ void operator()() const { __syncthreads(); }
+};
+
+__device__ __forceinline__ uint32_t umask_of(const SortArgs &a) { return a.flag_mode ? ~kSplitFlag : 0xFFFFFFFFu; }
+
+// Writes one finished weighted entry (packed) to the outputs.
+__device__ __forceinline__ void emit_packed(const SortArgs &a, uint64_t slot, unsigned long long ent) {
+  uint32_t u = (uint32_t)ent;
+  uint32_t wb = (uint32_t)(ent >> 32);
+  if (a.flag_mode && (u & kSplitFlag)) {
+    u &= ~kSplitFlag;
+    wb = __float_as_uint(a.vals[a.row_ptr[u] + wb]);
+  }
   a.row_idx[slot] = u;
-  uint32_t wb = pay;
-  if (tag) wb = __float_as_uint(a.vals[a.row_ptr[u] + pay]);
   a.vals_out[slot] = __uint_as_float(wb);
 }
 
-// Warp bitonic sort of 32 (key, pay, tag) triples held one per lane, ascending.
-__device__ __forceinline__ void warp_bitonic(uint64_t &key, uint32_t &pay, uint32_t &tag, uint32_t lane) {
+// Unique ordering key of a weighted entry at list index i.
+__device__ __forceinline__ unsigned long long packed_key(const SortArgs &a, unsigned long long ent, uint32_t i) {
+  const uint32_t u = (uint32_t)ent;
+  const bool tag = a.flag_mode && (u & kSplitFlag);
+  return ((unsigned long long)(u & umask_of(a)) << 32) | (tag ? (uint32_t)(ent >> 32) : i);
+}
+
+template <typename K, typename P>
+__device__ __forceinline__ void warp_bitonic32(K &key, P &pay, uint32_t lane) {
 #pragma unroll
   for (uint32_t k = 2; k <= 32; k <<= 1) {
 #pragma unroll
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      uint64_t ok = __shfl_xor_sync(kFull, key, j);
-      uint32_t op = __shfl_xor_sync(kFull, pay, j);
-      uint32_t ot = __shfl_xor_sync(kFull, tag, j);
+      K ok = __shfl_xor_sync(kFull, key, j);
+      P op = __shfl_xor_sync(kFull, pay, j);
       bool up = (lane & k) == 0;
       bool lower = (lane & j) == 0;
-      bool take = (lower == up) ? (ok < key) : (ok > key);
-      if (take) {
+      if ((lower == up) ? (ok < key) : (ok > key)) {
         key = ok;
         pay = op;
-        tag = ot;
       }
     }
   }
 }
 
-__device__ __forceinline__ void warp_bitonic_u32(uint32_t &key, uint32_t lane) {
-#pragma unroll
-  for (uint32_t k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      uint32_t ok = __shfl_xor_sync(kFull, key, j);
-      bool up = (lane & k) == 0;
-      bool lower = (lane & j) == 0;
-      if ((lower == up) ? (ok < key) : (ok > key)) key = ok;
-    }
-  }
-}
-
-// Small lists: one warp per group of 32 consecutive destinations.  Lists of
-// length 2..32 are sorted in registers; longer LDV lists go to the big list.
+// ---------------------------------------------------------------------------
+// Lists of length <= 32 (and length-1 copies); longer lists go to worklists.
+// One warp per group of 32 consecutive destinations.
+// ---------------------------------------------------------------------------
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_sort_small(SortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -108,21 +117,31 @@ __global__ void __launch_bounds__(256) k_sort_small(SortArgs a) {
   for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < ngroups; g += warps_total) {
     const uint32_t v = g * 32 + lane;
     uint64_t c0 = 0, c1 = 0;
-    bool need = false;
+    bool ldv = false;
     if (v < a.n) {
       c0 = a.col_ptr[v];
       c1 = a.col_ptr[v + 1];
-      need = c1 - c0 >= 2;
-      if (need && K && hdv_lookup(keys, hv, a.tlog2, v) >= 0) need = false;
+      ldv = c1 > c0 && !(K && hdv_lookup(keys, hv, a.tlog2, v) >= 0);
     }
     const uint64_t len = c1 - c0;
-    const bool big = need && len > kWarpSortCap;
-    if (big) {
-      uint32_t i = atomicAdd(&a.meta[kMetaBig], 1u);
-      if (i < a.big_cap) a.biglist[i] = v;
-      else set_status(a.status, GT_ERR_UNSUPPORTED);
+    if (VALS && ldv && len == 1) emit_packed(a, c0, a.ldv64[c0]);
+    const bool need = ldv && len >= 2;
+    if (need && len > kWarpSortCap) {
+      if (len <= kMidCap) {
+        uint32_t i = atomicAdd(&a.meta[kMetaMid], 1u);
+        if (i < a.mid_cap) a.midlist[i] = v;
+        else set_status(a.status, GT_ERR_UNSUPPORTED);
+      } else if (len <= kSortSmemCap) {
+        uint32_t i = atomicAdd(&a.meta[kMetaBig], 1u);
+        if (i < a.big_cap) a.biglist[i] = v;
+        else set_status(a.status, GT_ERR_UNSUPPORTED);
+      } else {
+        uint32_t i = atomicAdd(&a.meta[kMetaLargeN], 1u);
+        if (i < a.large_cap) a.largelist[i] = v;
+        else set_status(a.status, GT_ERR_UNSUPPORTED);
+      }
     }
-    uint32_t todo = __ballot_sync(kFull, need && !big);
+    uint32_t todo = __ballot_sync(kFull, need && len <= kWarpSortCap);
     sorted_local += __popc(__ballot_sync(kFull, need));
     while (todo) {
       const uint32_t j = __ffs(todo) - 1;
@@ -131,214 +150,110 @@ __global__ void __launch_bounds__(256) k_sort_small(SortArgs a) {
       const uint32_t L = (uint32_t)__shfl_sync(kFull, len, j);
       const bool act = lane < L;
       if (VALS) {
-        uint64_t key = ~0ull;
-        uint32_t pay = 0, tag = 0;
-        if (act) {
-          uint32_t u = a.row_idx[s0 + lane];
-          pay = __float_as_uint(a.vals_out[s0 + lane]);
-          tag = (a.flag_mode && (u & kSplitFlag)) ? 1u : 0u;
-          if (tag) u &= ~kSplitFlag;
-          key = ((uint64_t)u << 32) | (tag ? pay : lane);
-        }
-        warp_bitonic(key, pay, tag, lane);
-        if (act) finish_entry(a, key, pay, tag, s0 + lane);
+        unsigned long long ent = act ? a.ldv64[s0 + lane] : 0ull;
+        unsigned long long key = act ? packed_key(a, ent, lane) : ~0ull;
+        warp_bitonic32(key, ent, lane);
+        if (act) emit_packed(a, s0 + lane, ent);
       } else {
         uint32_t key = act ? a.row_idx[s0 + lane] : 0xFFFFFFFFu;
-        warp_bitonic_u32(key, lane);
+        uint32_t dummy = 0;
+        warp_bitonic32(key, dummy, lane);
         if (act) a.row_idx[s0 + lane] = key;
       }
     }
   }
-  // every lane holds the same warp-wide count
   if (lane == 0 && sorted_local) atomicAdd(&a.meta[kMetaSorted], sorted_local);
 }
 
 // ---------------------------------------------------------------------------
-// Big lists: one CTA per list.  Up to kSortSmemCap entries are sorted in
-// shared memory (bitonic on the composite key); longer lists use a stable
-// LSD radix sort on the source ID through the plan's scratch arrays.
+// Bitonic network in shared memory over cap (power of two) elements.
 // ---------------------------------------------------------------------------
-constexpr int kBigThreads = 1024;
-
-template <bool VALS>
-__device__ void smem_sort_list(const SortArgs &a, uint64_t s0, uint32_t L, unsigned char *smem) {
-  uint32_t cap = 1;
-  while (cap < L) cap <<= 1;
-  if (VALS) {
-    uint64_t *k = (uint64_t *)smem;
-    uint32_t *p = (uint32_t *)(k + kSortSmemCap);
-    uint8_t *t = (uint8_t *)(p + kSortSmemCap);
-    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
-      uint64_t key = ~0ull;
-      uint32_t pay = 0, tag = 0;
-      if (i < L) {
-        uint32_t u = a.row_idx[s0 + i];
-        pay = __float_as_uint(a.vals_out[s0 + i]);
-        tag = (a.flag_mode && (u & kSplitFlag)) ? 1u : 0u;
-        if (tag) u &= ~kSplitFlag;
-        key = ((uint64_t)u << 32) | (tag ? pay : i);
-      }
-      k[i] = key;
-      p[i] = pay;
-      t[i] = (uint8_t)tag;
-    }
-    __syncthreads();
-    for (uint32_t kk = 2; kk <= cap; kk <<= 1) {
-      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
-          uint32_t q = i ^ j;
-          if (q > i) {
-            bool up = (i & kk) == 0;
-            uint64_t x = k[i], y = k[q];
-            if ((x > y) == up) {
-              k[i] = y;
-              k[q] = x;
-              uint32_t tp = p[i];
-              p[i] = p[q];
-              p[q] = tp;
-              uint8_t tt = t[i];
-              t[i] = t[q];
-              t[q] = tt;
-            }
+template <bool VALS, typename Sync>
+__device__ __forceinline__ void smem_bitonic(unsigned long long *key, unsigned long long *pay, uint32_t *key32,
+                                             uint32_t cap, uint32_t tid, uint32_t nthreads, Sync sync) {
+  for (uint32_t k = 2; k <= cap; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = tid; i < cap / 2; i += nthreads) {
+        const uint32_t lo = 2 * j * (i / j) + (i % j);
+        const uint32_t hi = lo + j;
+        const bool up = (lo & k) == 0;
+        if (VALS) {
+          unsigned long long ka = key[lo], kb = key[hi];
+          if ((ka > kb) == up) {
+            key[lo] = kb;
+            key[hi] = ka;
+            unsigned long long t = pay[lo];
+            pay[lo] = pay[hi];
+            pay[hi] = t;
+          }
+        } else {
+          uint32_t ka = key32[lo], kb = key32[hi];
+          if ((ka > kb) == up) {
+            key32[lo] = kb;
+            key32[hi] = ka;
           }
         }
-        __syncthreads();
       }
+      sync();
     }
-    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) finish_entry(a, k[i], p[i], t[i], s0 + i);
-  } else {
-    uint32_t *k = (uint32_t *)smem;
-    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) k[i] = (i < L) ? a.row_idx[s0 + i] : 0xFFFFFFFFu;
-    __syncthreads();
-    for (uint32_t kk = 2; kk <= cap; kk <<= 1) {
-      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
-          uint32_t q = i ^ j;
-          if (q > i) {
-            bool up = (i & kk) == 0;
-            uint32_t x = k[i], y = k[q];
-            if ((x > y) == up) {
-              k[i] = y;
-              k[q] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) a.row_idx[s0 + i] = k[i];
   }
-  __syncthreads();
 }
 
-// One stable counting pass on digit (key >> shift) & (2^dbits - 1) of the
-// (tag-masked) source ID, src -> dst, by the whole CTA in input order.
+constexpr int kWarpThreads = 256;
+constexpr int kCtaThreads = 512;
+constexpr int kRadixThreads = 1024;
+
+// 33..kMidCap: one warp per list in its own shared-memory slice.
 template <bool VALS>
-__device__ void radix_pass(const uint32_t *su, const float *sw, uint32_t *du, float *dw, uint32_t L, uint32_t shift,
-                           uint32_t dbits, uint32_t kmask, unsigned char *smem) {
-  const uint32_t nb = 1u << dbits;
-  uint32_t *base = (uint32_t *)smem;   // [nb]
-  uint32_t *wc = base + 256;            // [nb][32]
+__global__ void __launch_bounds__(kWarpThreads) k_sort_warp(SortArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (cta_status_set(a.status)) return;
   const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) base[i] = 0;
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) atomicAdd(&base[((su[i] & kmask) >> shift) & (nb - 1)], 1u);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (uint32_t d = 0; d < nb; ++d) {
-      uint32_t c = base[d];
-      base[d] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  for (uint32_t c = 0; c < L; c += blockDim.x) {
-    const uint32_t i = c + threadIdx.x;
-    const bool act = i < L;
-    uint32_t u = act ? su[i] : 0u;
-    float wv = (VALS && act) ? sw[i] : 0.f;
-    uint32_t d = act ? (((u & kmask) >> shift) & (nb - 1)) : nb;
-    for (uint32_t dd = lane; dd < nb; dd += 32) wc[dd * 32 + w] = 0;
-    __syncthreads();
-    uint32_t mm = __match_any_sync(kFull, d);
-    uint32_t rank = __popc(mm & lanemask_lt());
-    if (act && rank == 0) wc[d * 32 + w] = __popc(mm);
-    __syncthreads();
-    // exclusive scan over warps for every digit: warp w handles digits w, w+32, ...
-    for (uint32_t dd = w; dd < nb; dd += 32) {
-      uint32_t x = wc[dd * 32 + lane];
-      uint32_t inc = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= (uint32_t)o) inc += y;
+  const size_t per = VALS ? 16u : 4u;
+  unsigned char *mine = smem + (size_t)w * kMidCap * per;
+  unsigned long long *key = (unsigned long long *)mine;
+  unsigned long long *pay = key + kMidCap;
+  uint32_t *key32 = (uint32_t *)mine;
+  const uint32_t nmid = min(a.meta[kMetaMid], a.mid_cap);
+  while (true) {
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(&a.meta[kMetaMidTicket], 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= nmid) break;
+    const uint32_t v = a.midlist[it];
+    const uint64_t s0 = a.col_ptr[v];
+    const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
+    uint32_t cap = 64;
+    while (cap < L) cap <<= 1;
+    for (uint32_t i = lane; i < cap; i += 32) {
+      if (VALS) {
+        unsigned long long ent = i < L ? a.ldv64[s0 + i] : 0ull;
+        key[i] = i < L ? packed_key(a, ent, i) : ~0ull;
+        pay[i] = ent;
+      } else {
+        key32[i] = i < L ? a.row_idx[s0 + i] : 0xFFFFFFFFu;
       }
-      const uint32_t b0 = base[dd];
-      wc[dd * 32 + lane] = b0 + inc - x;
-      __syncwarp();
-      if (lane == 31) base[dd] = b0 + inc;
     }
-    __syncthreads();
-    if (act) {
-      uint32_t pos = wc[d * 32 + w] + rank;
-      du[pos] = u;
-      if (VALS) dw[pos] = wv;
+    __syncwarp();
+    smem_bitonic<VALS>(key, pay, key32, cap, lane, 32, WarpSync{});
+    for (uint32_t i = lane; i < L; i += 32) {
+      if (VALS) emit_packed(a, s0 + i, pay[i]);
+      else a.row_idx[s0 + i] = key32[i];
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
+// kMidCap+1..kSortSmemCap: one CTA per list in shared memory.
 template <bool VALS>
-__device__ void radix_sort_list(const SortArgs &a, uint64_t s0, uint32_t L, unsigned char *smem) {
-  const uint32_t bits = a.key_bits;
-  const uint32_t passes = bits <= 16 ? 2u : 4u;
-  const uint32_t dbits = (bits + passes - 1) / passes;
-  const uint32_t kmask = a.flag_mode ? ~kSplitFlag : 0xFFFFFFFFu;
-  uint32_t *ou = a.row_idx + s0;
-  float *ow = VALS ? a.vals_out + s0 : nullptr;
-  uint32_t *xu = a.scr_u + s0;
-  float *xw = VALS ? a.scr_w + s0 : nullptr;
-  for (uint32_t ps = 0; ps < passes; ++ps) {
-    const uint32_t shift = ps * dbits;
-    if ((ps & 1u) == 0) radix_pass<VALS>(ou, ow, xu, xw, L, shift, dbits, kmask, smem);
-    else radix_pass<VALS>(xu, xw, ou, ow, L, shift, dbits, kmask, smem);
-  }
-  if (VALS && a.flag_mode) {
-    // tagged runs: order by position in row, then re-read the values
-    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-      uint32_t u = ou[i];
-      if (!(u & kSplitFlag)) continue;
-      if (i > 0 && ou[i - 1] == u) continue;  // not the first of its run
-      uint32_t j = i + 1;
-      while (j < L && ou[j] == u) ++j;
-      // insertion sort of positions in [i, j)
-      for (uint32_t x = i + 1; x < j; ++x) {
-        uint32_t t = __float_as_uint(ow[x]);
-        uint32_t y = x;
-        while (y > i && __float_as_uint(ow[y - 1]) > t) {
-          ow[y] = ow[y - 1];
-          --y;
-        }
-        ow[y] = __uint_as_float(t);
-      }
-      const uint32_t uu = u & ~kSplitFlag;
-      const uint64_t rs = a.row_ptr[uu];
-      for (uint32_t x = i; x < j; ++x) ow[x] = a.vals[rs + __float_as_uint(ow[x])];
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) ou[i] &= ~kSplitFlag;
-  }
-  __syncthreads();
-}
-
-template <bool VALS>
-__global__ void __launch_bounds__(kBigThreads) k_sort_big(SortArgs a) {
+__global__ void __launch_bounds__(kCtaThreads) k_sort_cta(SortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (cta_status_set(a.status)) return;
   __shared__ uint32_t s_item;
+  unsigned long long *key = (unsigned long long *)smem;
+  unsigned long long *pay = key + kSortSmemCap;
+  uint32_t *key32 = (uint32_t *)smem;
   const uint32_t nbig = min(a.meta[kMetaBig], a.big_cap);
-  uint32_t large_local = 0;
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaTicket], 1u);
     __syncthreads();
@@ -348,24 +263,200 @@ __global__ void __launch_bounds__(kBigThreads) k_sort_big(SortArgs a) {
     const uint32_t v = a.biglist[it];
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
-    if (L <= kSortSmemCap) {
-      smem_sort_list<VALS>(a, s0, L, smem);
-    } else {
-      radix_sort_list<VALS>(a, s0, L, smem);
-      ++large_local;
+    uint32_t cap = 512;
+    while (cap < L) cap <<= 1;
+    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+      if (VALS) {
+        unsigned long long ent = i < L ? a.ldv64[s0 + i] : 0ull;
+        key[i] = i < L ? packed_key(a, ent, i) : ~0ull;
+        pay[i] = ent;
+      } else {
+        key32[i] = i < L ? a.row_idx[s0 + i] : 0xFFFFFFFFu;
+      }
     }
+    __syncthreads();
+    smem_bitonic<VALS>(key, pay, key32, cap, threadIdx.x, blockDim.x, CtaSync{});
+    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
+      if (VALS) emit_packed(a, s0 + i, pay[i]);
+      else a.row_idx[s0 + i] = key32[i];
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 0 && large_local) atomicAdd(&a.meta[kMetaLarge], large_local);
 }
 
-static size_t big_smem_bytes() {
-  size_t bitonic = (size_t)kSortSmemCap * (8 + 4 + 1);
-  size_t radix = (256 + 256 * 32) * 4;
-  return bitonic > radix ? bitonic : radix;
+// ---------------------------------------------------------------------------
+// > kSortSmemCap: stable LSD radix sort on the (tag-masked) source ID, one
+// CTA per list.  The list is cut into 32 contiguous warp ranges; per pass
+// every warp scatters its range in order from per-(digit, warp) offsets and
+// counts the next pass's digits per destination warp range as it writes.
+// Buffers are SoA views (u[], w[]); weighted lists start in the packed
+// scratch (AoS) and alternate between the outputs and the same scratch
+// region viewed as SoA.
+// ---------------------------------------------------------------------------
+struct Buf {
+  uint32_t *u;
+  uint32_t *w;                 // null for unweighted
+  unsigned long long *packed;  // non-null: AoS source (first pass only)
+  __device__ uint32_t getu(uint32_t i) const { return packed ? (uint32_t)packed[i] : u[i]; }
+  __device__ uint32_t getw(uint32_t i) const { return packed ? (uint32_t)(packed[i] >> 32) : (w ? w[i] : 0u); }
+};
+
+template <bool VALS>
+__global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (cta_status_set(a.status)) return;
+  __shared__ uint32_t s_item;
+  const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t umask = umask_of(a);
+  const uint32_t nlarge = min(a.meta[kMetaLargeN], a.large_cap);
+  const uint32_t bits = a.key_bits ? a.key_bits : 1u;
+  const uint32_t passes = (bits + 7) / 8;
+  const uint32_t dbits = (bits + passes - 1) / passes;
+  const uint32_t nb = 1u << dbits;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaLargeTicket], 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    __syncthreads();
+    if (it >= nlarge) break;
+    const uint32_t v = a.largelist[it];
+    const uint64_t s0 = a.col_ptr[v];
+    const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
+    const uint32_t chunk = (L + 31) / 32;
+    uint32_t *hist = (uint32_t *)smem;  // [256][32]
+    uint32_t *next = hist + 256 * 32;   // [256][32]
+    Buf out{a.row_idx + s0, VALS ? (uint32_t *)(a.vals_out + s0) : nullptr, nullptr};
+    Buf scr;
+    Buf src;
+    if (VALS) {
+      uint32_t *base32 = (uint32_t *)(a.ldv64 + s0);  // the list's 8L scratch bytes as u[L], w[L]
+      scr = Buf{base32, base32 + L, nullptr};
+      src = Buf{nullptr, nullptr, a.ldv64 + s0};
+    } else {
+      scr = Buf{a.scr32 + s0, nullptr, nullptr};
+      src = out;
+    }
+    // first pass's per-warp counts
+    for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    {
+      const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
+      for (uint32_t i = r0 + lane; i < r1; i += 32) atomicAdd(&hist[(src.getu(i) & umask & (nb - 1)) * 32 + w], 1u);
+    }
+    __syncthreads();
+    Buf dst = VALS ? out : scr;
+    for (uint32_t ps = 0; ps < passes; ++ps) {
+      const uint32_t shift = ps * dbits;
+      // exclusive scan over (digit, warp), digit-major: per-digit prefix over
+      // warps, per-digit totals, prefix over digits, then combine
+      for (uint32_t d = w; d < nb; d += 32) {
+        uint32_t x = hist[d * 32 + lane];
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t y = __shfl_up_sync(kFull, inc, o);
+          if (lane >= (uint32_t)o) inc += y;
+        }
+        hist[d * 32 + lane] = inc - x;
+        if (lane == 31) next[d] = inc;  // digit total (next[] is cleared below)
+      }
+      __syncthreads();
+      if (w == 0) {
+        uint32_t run = 0;
+        for (uint32_t d0 = 0; d0 < nb; d0 += 32) {
+          uint32_t t = (d0 + lane < nb) ? next[d0 + lane] : 0u;
+          uint32_t inc = t;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+          }
+          if (d0 + lane < nb) next[d0 + lane] = run + inc - t;
+          run += __shfl_sync(kFull, inc, 31);
+        }
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < nb * 32; i += blockDim.x) hist[i] += next[i >> 5];
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) next[i] = 0;
+      __syncthreads();
+      const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
+      const uint32_t nshift = shift + dbits;
+      const bool more = ps + 1 < passes;
+      for (uint32_t c = r0; c < r1; c += 32) {
+        const uint32_t i = c + lane;
+        const bool act = i < r1;
+        const uint32_t u = act ? src.getu(i) : 0u;
+        const uint32_t wv = (VALS && act) ? src.getw(i) : 0u;
+        const uint32_t d = act ? (((u & umask) >> shift) & (nb - 1)) : nb;
+        const uint32_t mm = __match_any_sync(kFull, d);
+        const uint32_t rank = __popc(mm & lanemask_lt());
+        uint32_t base = 0;
+        if (act) base = hist[d * 32 + w];
+        __syncwarp();
+        if (act && rank == 0) hist[d * 32 + w] = base + __popc(mm);
+        __syncwarp();
+        if (act) {
+          const uint32_t pos = base + rank;
+          dst.u[pos] = u;
+          if (VALS) dst.w[pos] = wv;
+          if (more) atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * 32 + min(pos / chunk, 31u)], 1u);
+        }
+      }
+      __syncthreads();
+      uint32_t *t = hist;
+      hist = next;
+      next = t;
+      src = dst;
+      dst = (dst.u == out.u) ? scr : out;
+    }
+    // src holds the sorted list (SoA): order tagged runs by position, then
+    // write the outputs (in place when src is the output buffer)
+    if (VALS && a.flag_mode) {
+      for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
+        const uint32_t u = src.u[i];
+        if (!(u & kSplitFlag)) continue;
+        if (i > 0 && src.u[i - 1] == u) continue;  // not the first of its run
+        uint32_t j = i + 1;
+        while (j < L && src.u[j] == u) ++j;
+        for (uint32_t x = i + 1; x < j; ++x) {
+          const uint32_t tpos = src.w[x];
+          uint32_t y = x;
+          while (y > i && src.w[y - 1] > tpos) {
+            src.w[y] = src.w[y - 1];
+            --y;
+          }
+          src.w[y] = tpos;
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
+      uint32_t u = src.u[i];
+      if (VALS) {
+        uint32_t wb = src.w[i];
+        if (a.flag_mode && (u & kSplitFlag)) {
+          u &= ~kSplitFlag;
+          wb = __float_as_uint(a.vals[a.row_ptr[u] + wb]);
+        }
+        a.row_idx[s0 + i] = u;
+        a.vals_out[s0 + i] = __uint_as_float(wb);
+      } else if (src.u != out.u) {
+        a.row_idx[s0 + i] = u;
+      }
+    }
+    __syncthreads();
+  }
 }
+
+static size_t warp_smem_bytes(bool vals) { return (size_t)(kWarpThreads / 32) * kMidCap * (vals ? 16 : 4); }
+static size_t cta_smem_bytes(bool vals) { return (size_t)kSortSmemCap * (vals ? 16 : 4); }
+static size_t radix_smem_bytes() { return (size_t)2 * 256 * 32 * 4; }
 
 cudaError_t configure_sort() {
-  cudaError_t e[4] = {allow_max_dynamic_smem(k_sort_big<true>), allow_max_dynamic_smem(k_sort_big<false>),
+  cudaError_t e[8] = {allow_max_dynamic_smem(k_sort_warp<true>),  allow_max_dynamic_smem(k_sort_warp<false>),
+                      allow_max_dynamic_smem(k_sort_cta<true>),   allow_max_dynamic_smem(k_sort_cta<false>),
+                      allow_max_dynamic_smem(k_sort_radix<true>), allow_max_dynamic_smem(k_sort_radix<false>),
                       allow_max_dynamic_smem(k_sort_small<true>), allow_max_dynamic_smem(k_sort_small<false>)};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
@@ -376,8 +467,30 @@ cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &p
   (void)cfg;
   uint32_t bits = 0;
   while (bits < 32 && (w.n - 1) >> bits) ++bits;
-  SortArgs sa{w.n,     pb.col_ptr, pb.row_ptr, pb.vals,      pb.row_idx, pb.vals_out, w.hkeys, w.hvals, w.tlog2,
-              w.kmax,  w.meta,     w.biglist,  w.big_cap,    w.status,   w.flag_mode, w.scr_u, w.scr_w, bits};
+  SortArgs sa;
+  sa.n = w.n;
+  sa.col_ptr = pb.col_ptr;
+  sa.row_ptr = pb.row_ptr;
+  sa.vals = pb.vals;
+  sa.row_idx = pb.row_idx;
+  sa.vals_out = pb.vals_out;
+  sa.ldv64 = (unsigned long long *)w.scratch;
+  sa.scr32 = (uint32_t *)w.scratch;
+  sa.hkeys = w.hkeys;
+  sa.hvals = w.hvals;
+  sa.tlog2 = w.tlog2;
+  sa.kmax = w.kmax;
+  sa.meta = w.meta;
+  sa.status = w.status;
+  sa.flag_mode = w.flag_mode;
+  sa.key_bits = bits;
+  // worklist regions inside biglist: mid | big | large
+  sa.mid_cap = (uint32_t)(w.m / (kWarpSortCap + 1) + 1);
+  sa.big_cap = (uint32_t)(w.m / (kMidCap + 1) + 1);
+  sa.large_cap = (uint32_t)(w.m / (kSortSmemCap + 1) + 1);
+  sa.midlist = w.biglist;
+  sa.biglist = w.biglist + sa.mid_cap;
+  sa.largelist = sa.biglist + sa.big_cap;
   const bool vals = pb.vals != nullptr;
   const size_t ssm = w.kmax ? (size_t)(1u << w.tlog2) * 6 + 16 : 0;
   const uint32_t groups = (w.n + 31) / 32;
@@ -387,9 +500,15 @@ cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &p
   if (g == 0) g = 1;
   if (vals) k_sort_small<true><<<g, 256, ssm, s>>>(sa);
   else k_sort_small<false><<<g, 256, ssm, s>>>(sa);
-  const uint32_t gb = (uint32_t)w.num_sms * 2u;
-  if (vals) k_sort_big<true><<<gb, kBigThreads, big_smem_bytes(), s>>>(sa);
-  else k_sort_big<false><<<gb, kBigThreads, big_smem_bytes(), s>>>(sa);
+  const uint32_t gw = (uint32_t)w.num_sms * 4u;
+  if (vals) k_sort_warp<true><<<gw, kWarpThreads, warp_smem_bytes(true), s>>>(sa);
+  else k_sort_warp<false><<<gw, kWarpThreads, warp_smem_bytes(false), s>>>(sa);
+  const uint32_t gc = (uint32_t)w.num_sms * 4u;
+  if (vals) k_sort_cta<true><<<gc, kCtaThreads, cta_smem_bytes(true), s>>>(sa);
+  else k_sort_cta<false><<<gc, kCtaThreads, cta_smem_bytes(false), s>>>(sa);
+  const uint32_t gr = (uint32_t)w.num_sms * 2u;
+  if (vals) k_sort_radix<true><<<gr, kRadixThreads, radix_smem_bytes(), s>>>(sa);
+  else k_sort_radix<false><<<gr, kRadixThreads, radix_smem_bytes(), s>>>(sa);
   return cudaGetLastError();
 }
 

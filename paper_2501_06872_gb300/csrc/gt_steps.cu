@@ -634,6 +634,7 @@ struct ScatterArgs {
   const uint64_t *col_ptr;
   uint32_t *row_idx;
   float *vals_out;
+  unsigned long long *ldv64;  // weighted: LDV entries go here (one 8-byte store)
   uint32_t *status;
   int flag_mode;
   uint32_t stage_edges;
@@ -787,20 +788,37 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
           wbits = (uint32_t)(e - (my_u == row_first ? rs_first : rs_last));
         }
       }
-      a.row_idx[slot] = uu;
-      if (VALS) a.vals_out[slot] = __uint_as_float(wbits);
+      if (VALS && ldv) {
+        a.ldv64[slot] = ((unsigned long long)wbits << 32) | uu;
+      } else {
+        a.row_idx[slot] = uu;
+        if (VALS) a.vals_out[slot] = __uint_as_float(wbits);
+      }
     }
     asm volatile("" ::: "memory");
   };
 
   if (!STAGED) {
+    // the next chunk's loads are in flight while this chunk waits on its atomics
+    uint64_t e = e0 + lane;
+    bool act = e < e1;
+    uint32_t v = act ? __ldcs(a.col_idx + e) : kEmptyKey;
+    float wv = (VALS && act) ? __ldcs(a.vals + e) : 0.f;
 #pragma unroll 1
     for (uint64_t c = e0; c < e1; c += 32) {
-      uint64_t e = c + lane;
-      bool act = e < e1;
-      uint32_t v = act ? __ldcs(a.col_idx + e) : kEmptyKey;
-      float wv = (VALS && act) ? __ldcs(a.vals + e) : 0.f;
+      const uint64_t en = c + 32 + lane;
+      const bool actn = en < e1;
+      uint32_t vn = kEmptyKey;
+      float wn = 0.f;
+      if (actn) {
+        vn = __ldcs(a.col_idx + en);
+        if (VALS) wn = __ldcs(a.vals + en);
+      }
       step(e, act, v, wv);
+      e = en;
+      act = actn;
+      v = vn;
+      wv = wn;
     }
   } else {
     const uint32_t S = a.stage_edges;
@@ -1001,7 +1019,8 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // Step 3
   ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n,         w.m,       w.part,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
-                 pb.col_ptr, pb.row_idx, pb.vals_out, w.status, w.flag_mode, w.stage_edges};
+                 pb.col_ptr, pb.row_idx, pb.vals_out, (unsigned long long *)w.scratch, w.status, w.flag_mode,
+                 w.stage_edges};
   const bool vals = pb.vals != nullptr;
 #define GT_SC(H, V, ST) k_scatter<H, V, ST><<<w.G, threads, w.smem_scatter, s>>>(sa)
   if (hdv) {
@@ -1028,7 +1047,7 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
 
   // LDV sort
   err = launch_sort(w, cfg, pb, s);
-  nl += 2;
+  nl += 4;
   mark(5);
   if (launches) *launches = nl;
   return err;

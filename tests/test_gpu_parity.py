@@ -136,6 +136,23 @@ def test_split_rows_with_parallel_edges():
         assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
 
 
+def test_split_hub_rows_into_radix_lists():
+    """Two hub rows of 120,000 edges into 10 destinations each (lists > 8192
+    entries take the radix path) split across many partitions, weighted."""
+    rng = np.random.default_rng(9)
+    n = 500
+    rows = [rng.integers(0, 10, size=120000) if u in (3, 250) else rng.integers(0, n, size=rng.integers(0, 4))
+            for u in range(n)]
+    rp = np.zeros(n + 1, np.uint64)
+    rp[1:] = np.cumsum([r.size for r in rows])
+    ci = np.concatenate(rows).astype(np.uint32)
+    vv = rng.standard_normal(ci.size).astype(np.float32)
+    exp = oracle.transpose(rp, ci, vv)
+    for cfg in [config(hdv_k=0, warp_edges=256), config(hdv_k=4, warp_edges=512, stage_edges=256)]:
+        assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
+    assert_same(gpu_transpose(rp, ci, None, config(hdv_k=0, warp_edges=256)), oracle.transpose(rp, ci, None))
+
+
 def test_ragged_edge_counts_and_empty_rows():
     for m in [1, 3, 5, 31, 33, 129, 1023, 4097]:
         n = 257
