@@ -143,6 +143,21 @@ def stage_bytes(n, m, weighted):
     }
 
 
+def radix_passes(n):
+    bits = max(1, (n - 1).bit_length())
+    return (bits + 7) // 8
+
+
+def radix_down_bytes_per_edge(weighted, passes):
+    """Average algorithmic bytes per edge of one downsweep launch: the first
+    reads col_idx (+vals) and writes key, source (+value); later passes read
+    and write key, source (+value)."""
+    w = 4 if weighted else 0
+    first = (4 + w) + (8 + w)
+    later = 2 * (8 + w)
+    return (first + later * (passes - 1)) / passes
+
+
 def cpu_baseline_sample(rp_h, ci_h, vv_h, target_edges):
     """Rows [0, R) of the workload, R chosen so the prefix holds about target_edges."""
     import oracle
@@ -283,22 +298,24 @@ def main():
     value = m * world / (ms_step * 1e-3)
 
     peak, peak_kind = load_peaks()
-    sb = stage_bytes(n, m, weighted)
+    method = plan.config().method
     stage_ms = {"count": timing["count_ms"], "scan": timing["scan_ms"], "scatter": timing["scatter_ms"],
                 "sort": timing["sort_ms"], "sample": timing["sample_ms"]}
-    dominant = max(["count", "scan", "scatter"], key=lambda k: stage_ms[k])
-    if stage_ms["sort"] > stage_ms[dominant]:
-        dom_note = "sort is longest; its bytes are not algorithmic, roofline given for the longest algorithmic step"
+    if method == 1:
+        kname = "k_radix_down"
+        passes = radix_passes(n)
+        per_edge = radix_down_bytes_per_edge(weighted, passes)
+        dom_bytes = int(per_edge * m + 8 * (n + 1) / passes)
     else:
-        dom_note = None
-    kname = {"count": "k_count", "scan": "k_scan", "scatter": "k_scatter"}[dominant]
-    ach = sb[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+        kname = "k_scatter"
+        dom_bytes = stage_bytes(n, m, weighted)["scatter"]
+    dom_ms = timing["dominant_ms"]
+    ach = dom_bytes / (dom_ms * 1e-3) / 1e9
     lit, withv = algorithmic_bytes(n, m, weighted)
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": load_traffic(kname, args.workload), "kernel": kname,
-            "algorithmic_bytes_per_launch": sb[dominant], "peak_kind": peak_kind}
-    if dom_note:
-        roof["note"] = dom_note
+            "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": dom_ms,
+            "launches_timed": timing["dominant_launches"], "peak_kind": peak_kind}
     step_gbs = lit / (ms_step * 1e-3) / 1e9
 
     e2e = None
@@ -326,7 +343,7 @@ def main():
                 "step_hbm": {"gbs_formula": step_gbs, "frac_of_peak": step_gbs / peak,
                              "frac_of_8tbs": step_gbs / 8000.0, "bytes_formula": lit, "bytes_with_vals_read": withv,
                              "gbs_with_vals_read": withv / (ms_step * 1e-3) / 1e9},
-                "stage_ms": stage_ms, "stats": stats,
+                "stage_ms": stage_ms, "method": "radix" if method == 1 else "hlh", "stats": stats,
                 "coverage": stats["hdv_edges"] / max(1, m),
                 "clocks": clk.summary(),
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps,

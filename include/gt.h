@@ -27,6 +27,8 @@
  *           private insertion points, LDV edges take slots from atomic
  *           cursors (Algorithm 1, Step 3).
  *   Sort    (Sec. II-B, optional sort)  LDV lists are sorted by source.
+ * A second method (GT_METHOD_RADIX) computes the same bytes as a stable LSD
+ * radix sort by destination; gt_config.method selects it.
  *
  * Conventions
  *   - Every array argument of gt_transpose* is a DEVICE pointer owned by the
@@ -73,10 +75,20 @@ typedef struct gt_config {
     uint32_t stage_edges;     /* edges per bulk-copy stage per warp (0 = direct loads; else 128..4096, multiple of 128) */
     uint32_t sample_permille; /* sample size in 1/1000 of n (Sec. IV-C uses 10 = 1 %)     */
     uint32_t flags;           /* GT_FLAG_* bits                                            */
+    uint32_t method;          /* GT_METHOD_*                                               */
+    uint32_t reserved;        /* must be 0                                                 */
     uint64_t seed;            /* seed of the sampling positions                            */
 } gt_config;
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
+
+/* GT_METHOD_HLH: PoTra's hash-based LDV-HDV method (Algorithm 2; hdv_k = 0 is
+ *   Atomic GT, Algorithm 1) with the LDV list sort.
+ * GT_METHOD_RADIX: stable LSD radix sort of the CSR edge sequence by
+ *   destination (8-bit digits); streams the data once per digit, independent
+ *   of vertex order.  Uses 12-16 bytes per edge of extra workspace. */
+#define GT_METHOD_HLH 0u
+#define GT_METHOD_RADIX 1u
 
 typedef struct gt_stats {
     uint32_t hdv_selected;    /* HDV actually selected by Step 0 (<= hdv_k)  */
@@ -98,7 +110,11 @@ typedef struct gt_timing {
     float scan_ms;     /* Step 2: HDV insertion points + look-back scan      */
     float scatter_ms;  /* Step 3: scatter                                    */
     float sort_ms;     /* LDV list sort                                      */
-    float total_ms;
+    float total_ms;    /* GT_METHOD_RADIX: count_ms holds the digit passes and
+                          degree runs, scan_ms the scan, the rest are 0      */
+    float dominant_ms; /* average duration of one launch of the dominant
+                          kernel: the scatter (HLH) or a digit downsweep (radix) */
+    uint32_t dominant_launches; /* launches averaged                        */
 } gt_timing;
 
 typedef struct gt_plan_s *gt_plan;

@@ -16,6 +16,8 @@ GT_OK = 0
 STATUS = {0: "GT_OK", 1: "GT_ERR_INVALID_ARG", 2: "GT_ERR_OUT_OF_RANGE", 3: "GT_ERR_BAD_ROW_PTR",
           4: "GT_ERR_NO_MEMORY", 5: "GT_ERR_CUDA", 6: "GT_ERR_TIMEOUT", 7: "GT_ERR_UNSUPPORTED"}
 FLAG_AGGREGATE = 1
+METHOD_HLH = 0
+METHOD_RADIX = 1
 
 
 class GtError(RuntimeError):
@@ -29,6 +31,7 @@ class Config(ctypes.Structure):
                 ("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("warp_edges", ctypes.c_uint32), ("stage_edges", ctypes.c_uint32),
                 ("sample_permille", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("method", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -55,7 +58,8 @@ class Stats(ctypes.Structure):
 class Timing(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_uint32), ("sample_ms", ctypes.c_float), ("count_ms", ctypes.c_float),
                 ("scan_ms", ctypes.c_float), ("scatter_ms", ctypes.c_float), ("sort_ms", ctypes.c_float),
-                ("total_ms", ctypes.c_float)]
+                ("total_ms", ctypes.c_float), ("dominant_ms", ctypes.c_float),
+                ("dominant_launches", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

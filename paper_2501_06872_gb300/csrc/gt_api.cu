@@ -14,6 +14,7 @@
 namespace gt {
 cudaError_t configure_steps();
 cudaError_t configure_sort();
+cudaError_t configure_radix();
 }  // namespace gt
 
 struct gt_plan_s {
@@ -38,8 +39,10 @@ struct gt_plan_s {
 
 namespace {
 void drop_events(gt_plan p) {
-  for (auto &e : p->events)
+  for (auto &e : p->events) {
     for (int i = 0; i < 6; ++i) cudaEventDestroy(e.ev[i]);
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(e.down[i]);
+  }
   p->events.clear();
 }
 }  // namespace
@@ -63,6 +66,7 @@ bool config_valid(const gt_config &c) {
   if (c.warp_edges < 32) return false;
   if (c.stage_edges != 0 && (c.stage_edges < 128 || c.stage_edges > 4096 || c.stage_edges % 128)) return false;
   if (c.sample_permille > 1000) return false;
+  if (c.method > GT_METHOD_RADIX || c.reserved != 0) return false;
   return true;
 }
 
@@ -94,6 +98,13 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   if (w.ntiles == 0) w.ntiles = 1;
   w.big_cap = (uint32_t)gt::worklist_entries(w.m);
   w.flag_mode = (w.has_vals && w.n <= 0x80000000u) ? 1 : 0;
+  w.method = (int)c.method;
+  w.rG = (uint32_t)num_sms * 4u;
+  if (w.method == GT_METHOD_RADIX) {
+    w.kmax = 0;
+    w.tlog2 = 0;
+    w.ns = 0;
+  }
   return GT_OK;
 }
 
@@ -132,6 +143,26 @@ gt_status plan_alloc_ws(gt_plan p) {
     if ((st = plan_alloc(p, (void **)&w.field, (bytes))) != GT_OK) return st; \
   } while (0)
   GT_AL(deg, n * 4);
+  GT_AL(scan_state, (size_t)w.ntiles * 8);
+  GT_AL(status, 4);
+  GT_AL(meta, gt::kMetaCount * 4);
+  GT_AL(meta64, 4 * 8);
+  if (w.method == GT_METHOD_RADIX) {
+    const size_t tiles = (m + 4095) / 4096;
+    GT_AL(r_a_key, m * 4);
+    GT_AL(r_a_u, m * 4);
+    if (w.has_vals) GT_AL(r_a_w, m * 4);
+    GT_AL(r_b_key, m * 4);
+    (void)tiles;
+    GT_AL(r_long, (m / 2049 + 1) * 4);
+    GT_AL(r_nlong, 4);
+    GT_AL(r_table, (size_t)w.rG * 256 * 4);
+    GT_AL(r_offsets, (size_t)w.rG * 256 * 8);
+    if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
+    if (cudaMemset(w.meta, 0, gt::kMetaCount * 4) != cudaSuccess) return GT_ERR_CUDA;
+    if (cudaMemset(w.meta64, 0, 32) != cudaSuccess) return GT_ERR_CUDA;
+    return GT_OK;
+  }
   GT_AL(cursor, n * 8);
   GT_AL(hdv_cnt, (size_t)w.P * (w.kmax ? w.kmax : 1) * 4);
   GT_AL(hdv_ids, (w.kmax ? w.kmax : 1) * 4);
@@ -139,10 +170,6 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(hkeys, T * 4);
   GT_AL(hvals, T * 2);
   GT_AL(part, ((size_t)w.P + 1) * 8);
-  GT_AL(scan_state, (size_t)w.ntiles * 8);
-  GT_AL(status, 4);
-  GT_AL(meta, gt::kMetaCount * 4);
-  GT_AL(meta64, 4 * 8);
   GT_AL(skeys, (w.kmax ? ts : 1) * 4);
   GT_AL(scnt, (w.kmax ? ts : 1) * 4);
   GT_AL(fhist, (w.kmax ? gt::kFreqBins : 1) * 4);
@@ -226,6 +253,9 @@ gt_status gt_default_config(gt_config *cfg, uint32_t n_vertices, uint64_t n_edge
   }
   cfg->hdv_k = k;
   cfg->table_log2 = k ? ceil_log2_u64(2ull * k) : 0;
+  // Graphs whose per-vertex arrays and output far exceed L2 make every random
+  // access of the HLH method a DRAM access; the radix method streams instead.
+  cfg->method = n_edges >= (1ull << 22) ? GT_METHOD_RADIX : GT_METHOD_HLH;
   return GT_OK;
 }
 
@@ -250,6 +280,7 @@ gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, i
   if (!configured) {
     cudaError_t e1 = gt::configure_steps();
     cudaError_t e2 = gt::configure_sort();
+    if (e2 == cudaSuccess) e2 = gt::configure_radix();
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       from_cuda(e1 != cudaSuccess ? e1 : e2);
       cudaGetLastError();
@@ -305,11 +336,14 @@ gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *co
     w.smem_scatter = gt::smem_scatter_bytes(w.W, w.kmax, w.tlog2, 0, 0, w.has_vals);
   }
   gt::Problem pb{row_ptr, col_idx, vals, col_ptr, row_idx, vals_out};
-  const gt::StepEvents *ev = nullptr;
+  gt::StepEvents *ev = nullptr;
   if (plan->timing) {
     gt::StepEvents e;
     for (int i = 0; i < 6; ++i)
       if (cudaEventCreate(&e.ev[i]) != cudaSuccess) return GT_ERR_CUDA;
+    for (int i = 0; i < 8; ++i)
+      if (cudaEventCreate(&e.down[i]) != cudaSuccess) return GT_ERR_CUDA;
+    e.ndown = 0;
     plan->events.push_back(e);
     ev = &plan->events.back();
   }
@@ -330,11 +364,26 @@ gt_status gt_plan_timing(gt_plan plan, gt_timing *t) {
   if (plan->events.empty()) return GT_OK;
   if (cudaEventSynchronize(plan->events.back().ev[5]) != cudaSuccess) return GT_ERR_CUDA;
   double acc[5] = {0, 0, 0, 0, 0};
+  double dom = 0;
+  uint32_t ndom = 0;
   for (auto &e : plan->events) {
     for (int i = 0; i < 5; ++i) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, e.ev[i], e.ev[i + 1]) != cudaSuccess) return GT_ERR_CUDA;
       acc[i] += ms;
+    }
+    if (e.ndown) {
+      for (uint32_t i = 0; i + 1 < e.ndown; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.down[i], e.down[i + 1]) != cudaSuccess) return GT_ERR_CUDA;
+        dom += ms;
+        ++ndom;
+      }
+    } else {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.ev[3], e.ev[4]) != cudaSuccess) return GT_ERR_CUDA;
+      dom += ms;
+      ++ndom;
     }
   }
   const double c = (double)plan->events.size();
@@ -344,6 +393,8 @@ gt_status gt_plan_timing(gt_plan plan, gt_timing *t) {
   t->scan_ms = (float)(acc[2] / c);
   t->scatter_ms = (float)(acc[3] / c);
   t->sort_ms = (float)(acc[4] / c);
+  t->dominant_ms = ndom ? (float)(dom / ndom) : 0.f;
+  t->dominant_launches = ndom;
   t->total_ms = (float)((acc[0] + acc[1] + acc[2] + acc[3] + acc[4]) / c);
   return GT_OK;
 }

@@ -179,4 +179,65 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
       : "memory");
 }
 
+// ---- row search over CSR offsets (shared by the scatter and the radix method) ----
+
+// Number of window entries (row ends, non-decreasing across lanes) <= e.
+__device__ __forceinline__ uint32_t count_le(uint64_t rend, uint64_t e) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (uint32_t s = 16; s > 0; s >>= 1) {
+    uint64_t x = __shfl_sync(kFull, rend, pos + s - 1);
+    if (x <= e) pos += s;
+  }
+  uint64_t x = __shfl_sync(kFull, rend, pos);
+  if (x <= e) pos += 1;
+  return pos;  // 0..32
+}
+
+// Index of the row containing edge e: largest u with row_ptr[u] <= e, searched
+// from row base_u on (warp-collective).  One 32-row window covers the dense
+// case; sparse stretches are walked 256 rows per round with independent loads.
+__device__ __forceinline__ uint32_t find_row(const uint64_t *__restrict__ row_ptr, uint32_t n, uint32_t base_u,
+                                             uint64_t e, bool act, uint32_t lane, uint32_t *status) {
+  bool found = !act;
+  uint32_t my_u = 0;
+  uint64_t bu = base_u;
+  {
+    uint64_t ri = bu + 1 + lane;
+    if (ri > n) ri = n;
+    uint32_t pos = count_le(row_ptr[ri], e);
+    if (!found && pos < 32) {
+      my_u = (uint32_t)(bu + pos);
+      found = true;
+    }
+  }
+  if (__all_sync(kFull, found)) return my_u;
+  bu += 32;
+#pragma unroll 1
+  while (bu < n) {
+    uint64_t r[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      uint64_t ri = bu + 1 + lane + 32u * i;
+      if (ri > n) ri = n;
+      r[i] = row_ptr[ri];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      uint32_t pos = count_le(r[i], e);
+      if (!found && pos < 32) {
+        my_u = (uint32_t)(bu + 32u * i + pos);
+        found = true;
+      }
+    }
+    if (__all_sync(kFull, found)) return my_u;
+    bu += 256;
+  }
+  if (!found) {
+    set_status(status, GT_ERR_BAD_ROW_PTR);
+    my_u = n - 1;
+  }
+  return my_u;
+}
+
 }  // namespace gt

@@ -57,6 +57,15 @@ struct DevWork {
   // source, bit 31 of the source tagging split rows) until the LDV sort moves them
   // to the outputs; both kinds reuse it as the radix sort's second buffer.
   void *scratch = nullptr;
+  // radix method
+  int method = 0;
+  uint32_t rG = 0;                            // persistent CTAs of the digit passes
+  uint32_t *r_a_key = nullptr, *r_a_u = nullptr, *r_a_w = nullptr;  // [m] ping buffer
+  uint32_t *r_b_key = nullptr;                // [m] keys of the pong buffer (u/w live in the outputs)
+  uint32_t *r_long = nullptr;                 // rows longer than the window expansion handles
+  uint32_t *r_nlong = nullptr;                // [1] (zeroed per call)
+  uint32_t *r_table = nullptr;                // [rG][256]
+  unsigned long long *r_offsets = nullptr;    // [rG][256]
 };
 
 struct Problem {
@@ -71,12 +80,18 @@ struct Problem {
 // Events recorded between the steps of one call (null = not timed).
 struct StepEvents {
   cudaEvent_t ev[6];
+  cudaEvent_t down[8];  // radix: around each downsweep launch (up to 4 passes)
+  uint32_t ndown = 0;
 };
 
 // Enqueues the whole transposition on `stream`.  Returns cudaSuccess or the
 // first launch error; *launches receives the number of kernels enqueued.
 cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem &pb, cudaStream_t stream,
-                          const StepEvents *events, uint32_t *launches);
+                          StepEvents *events, uint32_t *launches);
+
+// Radix method: enqueues the digit passes and the degree runs (deg must be zeroed).
+cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches,
+                      StepEvents *events);
 
 // Shared-memory bytes needed by the count / scatter kernels for a shape.
 uint32_t smem_count_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged, uint32_t stage_edges,

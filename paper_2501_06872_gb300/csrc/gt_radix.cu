@@ -1,0 +1,412 @@
+// Radix method: the CSC as a stable LSD radix sort of the CSR edge sequence
+// by destination.  Sec. II-A defines the transpose; sorting the (source,
+// destination, value) triples stably by destination from CSR order gives
+// every in-list in ascending source order with parallel edges in CSR order
+// (Gustavson's sort-based transposition, Sec. VI, done as a counting sort
+// per digit).  Every pass streams the data once, so the method is bound by
+// HBM bandwidth whatever the vertex order; it is the method the selector
+// picks for graphs whose working set is far larger than L2.
+//
+// Per digit pass (8-bit digits, passes = ceil(bits(n-1) / 8)):
+//   upsweep    each persistent CTA counts the digits of its contiguous tile
+//              range -> table[cta][digit]
+//   offsets    exclusive scan of the table in (digit, cta) order
+//   downsweep  each CTA re-reads its tiles in order, ranks every tile stably
+//              in shared memory and scatters with running per-digit offsets
+// The first pass reads the CSR (rows found with the warp window search);
+// the last one writes row_idx / vals_out and the sorted keys.  Degrees come
+// from the run boundaries of the sorted keys, then the look-back scan builds
+// col_ptr.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gt_device.cuh"
+#include "gt_internal.h"
+
+namespace gt {
+
+constexpr int kRThreads = 256;
+constexpr int kRWarps = kRThreads / 32;
+constexpr int kRItems = 16;
+constexpr uint32_t kRTile = kRThreads * kRItems;  // 4096 edges
+constexpr int kRBins = 256;
+
+// Lanes holding the same dbits-bit digit (and active): AND of one ballot per
+// bit -- cheaper than __match_any_sync for digits of a few bits.
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t dbits, bool act) {
+  uint32_t mm = __ballot_sync(kFull, act);
+  for (uint32_t b = 0; b < dbits; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t bb = __ballot_sync(kFull, bit);
+    mm &= bit ? bb : ~bb;
+  }
+  return mm;
+}
+
+struct RadixArgs {
+  // CSR (first pass)
+  const uint64_t *row_ptr;
+  const uint32_t *col_idx;
+  const float *vals;
+  uint32_t n;
+  uint64_t m;
+  const uint32_t *unused_rows;
+  // this pass
+  const uint32_t *in_key, *in_u, *in_w;
+  uint32_t *out_key, *out_u, *out_w;
+  uint32_t shift, dbits;
+  uint32_t ntiles, tiles_per_cta;
+  uint32_t *table;                    // [G][256] counts
+  const unsigned long long *offsets;  // [G][256] starting positions
+  uint32_t *status;
+};
+
+// Writes the source row of every edge (src[e] = u for e in row u).  Rows of
+// at most kLongRow edges: 32 rows per warp step, whose edges form one
+// contiguous range; each lane finds the row of its position among the 32 row
+// ends held in registers.  Longer rows are listed for k_expand_long.
+constexpr uint32_t kLongRow = 2048;
+
+__global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n, uint32_t *src, uint32_t *long_rows,
+                              uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n; r0 += warps * 32) {
+    const uint64_t r = r0 + lane;
+    uint64_t ri = r + 1;
+    if (ri > n) ri = n;
+    const uint64_t rend = row_ptr[ri];  // end of row r (clamped)
+    const uint64_t rbeg = r < n ? row_ptr[r] : rend;
+    const bool is_long = r < n && rend - rbeg > kLongRow;
+    if (is_long) {
+      uint32_t i = atomicAdd(n_long, 1u);
+      if (i < long_cap) long_rows[i] = (uint32_t)r;
+      else set_status(status, GT_ERR_UNSUPPORTED);
+    }
+    const uint32_t longmask = __ballot_sync(kFull, is_long);
+    const uint64_t b = __shfl_sync(kFull, rbeg, 0);
+    const uint64_t e = __shfl_sync(kFull, rend, 31);
+    if (longmask == 0) {
+      for (uint64_t p0 = b; p0 < e; p0 += 32) {
+        const uint64_t p = p0 + lane;
+        const uint32_t pos = count_le(rend, p);  // warp-collective
+        if (p < e) src[p] = (uint32_t)(r0 + pos);
+      }
+    } else {
+      // short rows of this window one by one (the long ones are skipped)
+      uint32_t todo = __ballot_sync(kFull, r < n && !is_long && rend > rbeg);
+      while (todo) {
+        const uint32_t j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint64_t qb = __shfl_sync(kFull, rbeg, j), qe = __shfl_sync(kFull, rend, j);
+        for (uint64_t p = qb + lane; p < qe; p += 32) src[p] = (uint32_t)(r0 + j);
+      }
+    }
+  }
+}
+
+// One CTA per long row.
+__global__ void k_expand_long(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ long_rows,
+                              const uint32_t *__restrict__ n_long, uint32_t long_cap, uint32_t *src) {
+  const uint32_t cnt = min(*n_long, long_cap);
+  for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const uint32_t r = long_rows[i];
+    const uint64_t b = row_ptr[r], e = row_ptr[r + 1];
+    for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) src[p] = r;
+  }
+}
+
+// Counts the digits of this CTA's tiles (8 loads in flight per thread).
+template <bool FIRST>
+__global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
+  __shared__ uint32_t cnt[kRBins];
+  for (uint32_t i = threadIdx.x; i < kRBins; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  const uint32_t mask = (1u << a.dbits) - 1u;
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint64_t t0 = (uint64_t)blockIdx.x * a.tiles_per_cta;
+  const uint64_t e0 = min64(t0 * kRTile, a.m), e1 = min64((t0 + a.tiles_per_cta) * kRTile, a.m);
+  const uint32_t *src = a.in_key;
+  constexpr int U = 8;
+  for (uint64_t c = e0 + (uint64_t)w * 32 * U; c < e1; c += (uint64_t)kRWarps * 32 * U) {
+    uint32_t key[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint64_t e = c + (uint64_t)i * 32 + lane;
+      key[i] = e < e1 ? __ldcs(src + e) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint64_t e = c + (uint64_t)i * 32 + lane;
+      const bool act = e < e1;
+      if (FIRST && act && key[i] >= a.n) set_status(a.status, GT_ERR_OUT_OF_RANGE);
+      const uint32_t d = act ? ((key[i] >> a.shift) & mask) : 0u;
+      const uint32_t mm = match_digit(d, a.dbits, act);
+      if (act && (mm & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(mm));
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kRBins; i += blockDim.x) a.table[(size_t)blockIdx.x * kRBins + i] = cnt[i];
+}
+
+// Exclusive scan of table[G][256] in (digit, cta) order -> offsets[G][256].
+// One CTA of 1024 threads: 4 segments of CTAs x 256 digits, 8 loads in flight.
+__global__ void __launch_bounds__(1024) k_radix_offsets(const uint32_t *__restrict__ table, uint32_t G,
+                                                        unsigned long long *offsets) {
+  __shared__ unsigned long long part[4][kRBins];
+  const uint32_t d = threadIdx.x & (kRBins - 1), seg = threadIdx.x >> 8;
+  const uint32_t per = (G + 3) / 4;
+  const uint32_t c0 = min(seg * per, G), c1 = min(c0 + per, G);
+  unsigned long long s = 0;
+  uint32_t c = c0;
+  for (; c + 8 <= c1; c += 8) {
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = table[(size_t)(c + i) * kRBins + d];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+  }
+  for (; c < c1; ++c) s += table[(size_t)c * kRBins + d];
+  part[seg][d] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // digit totals -> exclusive prefix over digits (one warp, 8 digits per lane)
+    unsigned long long tot[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t dd = threadIdx.x * 8 + i;
+      tot[i] = part[0][dd] + part[1][dd] + part[2][dd] + part[3][dd];
+      sum += tot[i];
+    }
+    unsigned long long inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(kFull, inc, o);
+      if (threadIdx.x >= (uint32_t)o) inc += y;
+    }
+    unsigned long long run = inc - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t dd = threadIdx.x * 8 + i;
+      // turn the four segment sums of digit dd into their starting positions
+      unsigned long long r = run;
+      for (int q = 0; q < 4; ++q) {
+        unsigned long long x = part[q][dd];
+        part[q][dd] = r;
+        r += x;
+      }
+      run += tot[i];
+    }
+  }
+  __syncthreads();
+  unsigned long long run = part[seg][d];
+  c = c0;
+  for (; c + 8 <= c1; c += 8) {
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = table[(size_t)(c + i) * kRBins + d];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      offsets[(size_t)(c + i) * kRBins + d] = run;
+      run += x[i];
+    }
+  }
+  for (; c < c1; ++c) {
+    offsets[(size_t)c * kRBins + d] = run;
+    run += table[(size_t)c * kRBins + d];
+  }
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
+  extern __shared__ __align__(16) uint32_t stage[];  // [kRTile] keys | [kRTile] sources | [kRTile] values
+  __shared__ uint32_t wcnt[kRWarps][kRBins];
+  __shared__ unsigned long long run_off[kRBins];
+  __shared__ uint32_t tile_tot[kRBins];
+  __shared__ uint32_t tile_start[kRBins];
+  __shared__ uint32_t wsum[kRWarps];
+  uint32_t *skey = stage, *su = stage + kRTile, *sw = stage + 2 * kRTile;
+  const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t mask = (1u << a.dbits) - 1u;
+  for (uint32_t d = threadIdx.x; d < kRBins; d += blockDim.x)
+    run_off[d] = a.offsets[(size_t)blockIdx.x * kRBins + d];
+  const uint64_t t0 = (uint64_t)blockIdx.x * a.tiles_per_cta;
+  const uint64_t t1 = min64(t0 + a.tiles_per_cta, a.ntiles);
+  for (uint64_t tile = t0; tile < t1; ++tile) {
+    for (uint32_t i = threadIdx.x; i < kRWarps * kRBins; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    const uint64_t tbase = tile * kRTile;
+    const uint64_t base = tbase + (uint64_t)w * (kRItems * 32);
+    const uint32_t tcount = (uint32_t)min64(kRTile, a.m - tbase);
+    uint32_t key[kRItems], uu[kRItems], ww[kRItems], rk[kRItems];
+    // all of this warp's loads are in flight before any ranking
+#pragma unroll
+    for (int i = 0; i < kRItems; ++i) {
+      const uint64_t e = base + (uint64_t)i * 32 + lane;
+      if (e < a.m) {
+        key[i] = __ldcs(a.in_key + e);
+        uu[i] = __ldcs(a.in_u + e);
+        ww[i] = VALS ? __ldcs(a.in_w + e) : 0u;
+      } else {
+        key[i] = 0u;
+        uu[i] = 0u;
+        ww[i] = 0u;
+      }
+    }
+    __syncthreads();
+    // stable rank within the warp: items in order, lanes in order
+#pragma unroll
+    for (int i = 0; i < kRItems; ++i) {
+      const bool act = base + (uint64_t)i * 32 + lane < a.m;
+      const uint32_t d = (key[i] >> a.shift) & mask;
+      const uint32_t mm = match_digit(d, a.dbits, act);
+      const uint32_t r = __popc(mm & lanemask_lt());
+      uint32_t b = 0;
+      if (act) b = wcnt[w][d];
+      __syncwarp();
+      if (act && r == 0) wcnt[w][d] = b + __popc(mm);
+      __syncwarp();
+      rk[i] = act ? (b + r) : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps and the tile total; then the
+    // tile-local start of every digit (exclusive scan over digits)
+    uint32_t tot = 0;
+    {
+      const uint32_t d = threadIdx.x;  // kRThreads == kRBins
+      uint32_t run = 0;
+#pragma unroll
+      for (int x = 0; x < kRWarps; ++x) {
+        uint32_t c = wcnt[x][d];
+        wcnt[x][d] = run;
+        run += c;
+      }
+      tot = run;
+      tile_tot[d] = run;
+      uint32_t inc = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+      }
+      if (lane == 31) wsum[w] = inc;
+      __syncthreads();
+      uint32_t before = 0;
+      for (uint32_t x = 0; x < w; ++x) before += wsum[x];
+      tile_start[d] = before + inc - run;
+    }
+    __syncthreads();
+    // place the tile in shared memory in (digit, rank) order
+#pragma unroll
+    for (int i = 0; i < kRItems; ++i) {
+      if (rk[i] != 0xFFFFFFFFu) {
+        const uint32_t d = (key[i] >> a.shift) & mask;
+        const uint32_t lp = tile_start[d] + wcnt[w][d] + rk[i];
+        skey[lp] = key[i];
+        su[lp] = uu[i];
+        if (VALS) sw[lp] = ww[i];
+      }
+    }
+    __syncthreads();
+    // consecutive threads write consecutive positions of each digit's run
+    for (uint32_t j = threadIdx.x; j < tcount; j += blockDim.x) {
+      const uint32_t k = skey[j];
+      const uint32_t d = (k >> a.shift) & mask;
+      const uint64_t pos = run_off[d] + (j - tile_start[d]);
+      a.out_key[pos] = k;
+      a.out_u[pos] = su[j];
+      if (VALS) a.out_w[pos] = sw[j];
+    }
+    __syncthreads();
+    run_off[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
+// Degrees from the runs of equal keys in the sorted key array:
+// deg[k] = (end of run) - (start of run), via two wrapping adds.
+__global__ void k_radix_runs(const uint32_t *__restrict__ key, uint64_t m, uint32_t n, uint32_t *deg) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = key[p];
+    if (k >= n) continue;
+    if (p == 0 || key[p - 1] != k) red_add_u32(&deg[k], (uint32_t)(0u - (uint32_t)p));
+    if (p + 1 == m || key[p + 1] != k) red_add_u32(&deg[k], (uint32_t)(p + 1));
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+static uint32_t key_bits_of(uint32_t n) {
+  uint32_t bits = 0;
+  while (bits < 32 && (n - 1) >> bits) ++bits;
+  return bits ? bits : 1u;
+}
+
+cudaError_t configure_radix() {
+  cudaError_t e1 = allow_max_dynamic_smem(k_radix_down<true>);
+  cudaError_t e2 = allow_max_dynamic_smem(k_radix_down<false>);
+  return e1 != cudaSuccess ? e1 : e2;
+}
+
+uint64_t radix_workspace_bytes(uint64_t m, int has_vals, uint32_t G) {
+  const uint64_t ntiles = (m + kRTile - 1) / kRTile;
+  return m * 4 * (has_vals ? 4 : 3) + ntiles * 4 + (uint64_t)G * kRBins * (4 + 8) + 4096;
+}
+
+cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint32_t *launches, StepEvents *ev) {
+  const uint64_t m = w.m;
+  const uint32_t n = w.n;
+  const bool vals = pb.vals != nullptr;
+  uint32_t nl = 0;
+  cudaError_t err;
+  const uint32_t bits = key_bits_of(n);
+  const uint32_t passes = (bits + 7) / 8;
+  const uint32_t dbits = (bits + passes - 1) / passes;
+  const uint32_t ntiles = (uint32_t)((m + kRTile - 1) / kRTile);
+  const uint32_t G = w.rG;
+  const uint32_t tpc = (ntiles + G - 1) / G;
+  if (m == 0) return cudaSuccess;
+  // buffers: A = (a_key, a_u, a_w); B = (b_key, row_idx, vals_out).  Pass p
+  // writes B when (passes - p) is even, so the last pass writes the outputs.
+  uint32_t *b_u = pb.row_idx, *b_w = (uint32_t *)pb.vals_out;
+  const bool first_to_b = ((passes - 1) % 2) == 0;
+  // source rows of the first pass go to the buffer the first pass does not write
+  uint32_t *src_rows = first_to_b ? w.r_a_u : b_u;
+  {
+    uint64_t warps = ((uint64_t)n + 31) / 32;
+    uint32_t g = (uint32_t)min64((warps + 7) / 8, (uint64_t)w.num_sms * 16);
+    if (g == 0) g = 1;
+    const uint32_t long_cap = (uint32_t)(m / (kLongRow + 1) + 1);
+    k_expand_rows<<<g, 256, 0, s>>>(pb.row_ptr, n, src_rows, w.r_long, w.r_nlong, long_cap, w.status);
+    k_expand_long<<<w.num_sms * 4, 256, 0, s>>>(pb.row_ptr, w.r_long, w.r_nlong, long_cap, src_rows);
+    nl += 2;
+  }
+  const uint32_t *in_key = pb.col_idx, *in_u = src_rows, *in_w = (const uint32_t *)pb.vals;
+  for (uint32_t p = 1; p <= passes; ++p) {
+    const bool toB = ((passes - p) % 2) == 0;
+    uint32_t *ok = toB ? w.r_b_key : w.r_a_key, *ou = toB ? b_u : w.r_a_u, *ow = toB ? b_w : w.r_a_w;
+    RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
+                 (p - 1) * dbits, dbits, ntiles, tpc, w.r_table, w.r_offsets, w.status};
+    if (p == 1) k_radix_up<true><<<G, kRThreads, 0, s>>>(ra);
+    else k_radix_up<false><<<G, kRThreads, 0, s>>>(ra);
+    k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G, w.r_offsets);
+    if (ev && ev->ndown + 2 <= 8) cudaEventRecord(ev->down[ev->ndown], s);
+    const size_t dsm = (size_t)kRTile * 4 * (vals ? 3 : 2);
+    if (vals) k_radix_down<true><<<G, kRThreads, dsm, s>>>(ra);
+    else k_radix_down<false><<<G, kRThreads, dsm, s>>>(ra);
+    if (ev && ev->ndown + 2 <= 8) {
+      cudaEventRecord(ev->down[ev->ndown + 1], s);
+      ev->ndown += 2;
+    }
+    nl += 3;
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    in_key = ok;
+    in_u = ou;
+    in_w = ow;
+  }
+  uint32_t g = (uint32_t)min64((m + 255) / 256, (uint64_t)w.num_sms * 16);
+  k_radix_runs<<<g, 256, 0, s>>>(w.r_b_key, m, n, w.deg);
+  ++nl;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+}  // namespace gt

@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
     uint64_t idx = base + i;
     if (idx < n) {
       col_ptr[idx] = run;
-      cursor[idx] = run;
+      if (cursor) cursor[idx] = run;
     }
     run += d[i];
     if (idx + 1 == n) {
@@ -639,65 +639,6 @@ struct ScatterArgs {
   int flag_mode;
   uint32_t stage_edges;
 };
-
-// Number of window entries (row ends, non-decreasing across lanes) <= e.
-__device__ __forceinline__ uint32_t count_le(uint64_t rend, uint64_t e) {
-  uint32_t pos = 0;
-#pragma unroll
-  for (uint32_t s = 16; s > 0; s >>= 1) {
-    uint64_t x = __shfl_sync(kFull, rend, pos + s - 1);
-    if (x <= e) pos += s;
-  }
-  uint64_t x = __shfl_sync(kFull, rend, pos);
-  if (x <= e) pos += 1;
-  return pos;  // 0..32
-}
-
-// Index of the row containing edge e: largest u with row_ptr[u] <= e, searched
-// from row base_u on (warp-collective).  One 32-row window covers the dense
-// case; sparse stretches are walked 256 rows per round with independent loads.
-__device__ __forceinline__ uint32_t find_row(const uint64_t *__restrict__ row_ptr, uint32_t n, uint32_t base_u,
-                                             uint64_t e, bool act, uint32_t lane, uint32_t *status) {
-  bool found = !act;
-  uint32_t my_u = 0;
-  uint64_t bu = base_u;
-  {
-    uint64_t ri = bu + 1 + lane;
-    if (ri > n) ri = n;
-    uint32_t pos = count_le(row_ptr[ri], e);
-    if (!found && pos < 32) {
-      my_u = (uint32_t)(bu + pos);
-      found = true;
-    }
-  }
-  if (__all_sync(kFull, found)) return my_u;
-  bu += 32;
-#pragma unroll 1
-  while (bu < n) {
-    uint64_t r[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint64_t ri = bu + 1 + lane + 32u * i;
-      if (ri > n) ri = n;
-      r[i] = row_ptr[ri];
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint32_t pos = count_le(r[i], e);
-      if (!found && pos < 32) {
-        my_u = (uint32_t)(bu + 32u * i + pos);
-        found = true;
-      }
-    }
-    if (__all_sync(kFull, found)) return my_u;
-    bu += 256;
-  }
-  if (!found) {
-    set_status(status, GT_ERR_BAD_ROW_PTR);
-    my_u = n - 1;
-  }
-  return my_u;
-}
 
 template <bool HDV, bool VALS, bool STAGED>
 __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
@@ -935,7 +876,7 @@ cudaError_t configure_steps() {
 cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &pb, cudaStream_t s);
 
 cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem &pb, cudaStream_t s,
-                          const StepEvents *ev, uint32_t *launches) {
+                          StepEvents *ev, uint32_t *launches) {
   cudaError_t err;
   uint32_t nl = 0;
   auto mark = [&](int i) {
@@ -951,6 +892,23 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   if ((err = cudaMemsetAsync(w.deg, 0, (size_t)w.n * sizeof(uint32_t), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(w.scan_state, 0, (size_t)w.ntiles * sizeof(unsigned long long), s)) != cudaSuccess)
     return err;
+
+  if (w.method == GT_METHOD_RADIX) {
+    // timing slots: count = digit passes and degree runs, scan = look-back scan
+    mark(1);
+    nl = 0;
+    if ((err = cudaMemsetAsync(w.r_nlong, 0, 4, s)) != cudaSuccess) return err;
+    if ((err = run_radix(w, pb, s, &nl, ev)) != cudaSuccess) return err;
+    mark(2);
+    k_scan<<<w.ntiles, kScanThreads, 0, s>>>(w.deg, w.n, w.m, pb.row_ptr, pb.col_ptr, nullptr, w.scan_state, w.meta,
+                                             w.status);
+    ++nl;
+    mark(3);
+    mark(4);
+    mark(5);
+    if (launches) *launches = nl;
+    return cudaGetLastError();
+  }
 
   // Step 0
   if (hdv) {

@@ -53,7 +53,7 @@ def assert_same(got, exp):
 def config(**kw):
     from paper_2501_06872_gb300 import binding
     base = dict(hdv_k=0, table_log2=0, block_threads=256, ctas_per_sm=4, warp_edges=256, stage_edges=0,
-                sample_permille=10, flags=1, seed=7)
+                sample_permille=10, flags=1, method=0, reserved=0, seed=7)
     base.update(kw)
     if base["hdv_k"] and not base["table_log2"]:
         base["table_log2"] = max(1, (2 * base["hdv_k"] - 1).bit_length())
@@ -67,6 +67,7 @@ CONFIGS = {
     "hdv4096_w1024": dict(hdv_k=4096, table_log2=13, block_threads=128, ctas_per_sm=1, warp_edges=2048),
     "noagg_staged": dict(hdv_k=16, flags=0, stage_edges=128),
     "big_blocks": dict(hdv_k=128, block_threads=1024, ctas_per_sm=1, warp_edges=64),
+    "radix": dict(method=1),
 }
 
 
@@ -91,7 +92,7 @@ def test_empty_and_degenerate():
     rp = np.arange(n + 1, dtype=np.uint64)
     ci = np.full(n, n - 1, np.uint32)
     vv = np.arange(n, dtype=np.float32)
-    for name in ["atomic", "hdv64"]:
+    for name in ["atomic", "hdv64", "radix"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), oracle.transpose(rp, ci, vv))
 
 
@@ -107,7 +108,7 @@ def test_random_graphs_all_configs(name, seed):
 def test_rmat_numpy_scale14(order):
     n, rp, ci, vv = inputs.rmat_csr(14, 16, seed=3, order=order, weighted=True)
     exp = oracle.transpose(rp, ci, vv)
-    for name in ["atomic", "hdv512_staged", "big_blocks"]:
+    for name in ["atomic", "hdv512_staged", "big_blocks", "radix"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
     assert_same(gpu_transpose(rp, ci, vv), exp)  # default configuration
 
@@ -132,7 +133,7 @@ def test_split_rows_with_parallel_edges():
     vv = rng.standard_normal(ci.size).astype(np.float32)
     exp = oracle.transpose(rp, ci, vv)
     for cfg in [config(hdv_k=0, warp_edges=64), config(hdv_k=8, warp_edges=128, stage_edges=128),
-                config(hdv_k=0, warp_edges=4096, block_threads=64)]:
+                config(hdv_k=0, warp_edges=4096, block_threads=64), config(method=1)]:
         assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
 
 
@@ -148,7 +149,7 @@ def test_split_hub_rows_into_radix_lists():
     ci = np.concatenate(rows).astype(np.uint32)
     vv = rng.standard_normal(ci.size).astype(np.float32)
     exp = oracle.transpose(rp, ci, vv)
-    for cfg in [config(hdv_k=0, warp_edges=256), config(hdv_k=4, warp_edges=512, stage_edges=256)]:
+    for cfg in [config(hdv_k=0, warp_edges=256), config(hdv_k=4, warp_edges=512, stage_edges=256), config(method=1)]:
         assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
     assert_same(gpu_transpose(rp, ci, None, config(hdv_k=0, warp_edges=256)), oracle.transpose(rp, ci, None))
 
@@ -162,7 +163,7 @@ def test_ragged_edge_counts_and_empty_rows():
         rp, ci, _ = inputs.csr_from_edges(n, src.astype(np.uint32), dst.astype(np.uint32))
         vv = key.standard_normal(m).astype(np.float32)
         exp = oracle.transpose(rp, ci, vv)
-        for name in ["atomic", "noagg_staged", "hdv512_staged"]:
+        for name in ["atomic", "noagg_staged", "hdv512_staged", "radix"]:
             assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
 
 
