@@ -221,12 +221,96 @@ def workload_config(name, n, m, weighted):
             "seed": SEED, "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"}
 
 
+def run_batched(args):
+    """Config 4: 4096 uneven matrices transposed by one batch plan (CUDA-graph
+    replay) vs one plain gt_transpose_sub launch sequence per matrix."""
+    import torch
+    from paper_2501_06872_gb300 import binding
+    from paper_2501_06872_gb300.inputs import gpu as ggen
+    b = ggen.batch(n_graphs=args.batch_graphs, seed=0x5EED0004)
+    m_tot, v_tot, ng = b["total_m"], b["total_v"], b["n_graphs"]
+    cp = torch.empty(v_tot + ng, dtype=torch.int64, device="cuda")
+    ri = torch.empty(m_tot, dtype=torch.int32, device="cuda")
+    vo = torch.empty(m_tot, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    cfg = None
+    if args.config:
+        cfg = binding.default_config(1 << 20, 1 << 24)
+        for k, v in json.loads(args.config).items():
+            setattr(cfg, k, int(v))
+    plan = binding.BatchPlan(ggen.batch_graphs(b, cp, ri, vo), True, cfg)
+    for _ in range(args.warmup):
+        plan.transpose(s)
+    plan.check()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(0) as clk:
+        ev0.record(s)
+        for _ in range(args.steps):
+            plan.transpose(s)
+        ev1.record(s)
+        torch.cuda.synchronize()
+    plan.check()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    info = plan.info()
+    plan.close()
+    # per-graph baseline: the library's default configuration per matrix size
+    nmax, mmax = int(b["n"].max()), int(b["m"].max())
+    plans = {}
+    for meth in (0, 1):
+        c = binding.default_config(nmax, mmax)
+        c.method = meth
+        plans[meth] = binding.Plan(nmax, mmax, True, c)
+    rp, ci, vv = b["row_ptr"], b["col_idx"], b["vals"]
+    cp2 = torch.empty_like(cp)
+    ri2 = torch.empty_like(ri)
+    vo2 = torch.empty_like(vo)
+
+    def per_graph():
+        for g in range(ng):
+            n, m = int(b["n"][g]), int(b["m"][g])
+            r0, e0 = int(b["voff"][g]) + g, int(b["eoff"][g])
+            meth = binding.default_config(n, m).method
+            plans[meth].transpose_sub(n, m, rp[r0:r0 + n + 1], ci[e0:e0 + m], vv[e0:e0 + m], cp2[r0:r0 + n + 1],
+                                      ri2[e0:e0 + m], vo2[e0:e0 + m], s)
+    per_graph()
+    torch.cuda.synchronize()
+    e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 2))
+    e0_.record(s)
+    for _ in range(reps):
+        per_graph()
+    e1_.record(s)
+    torch.cuda.synchronize()
+    ms_pg = e0_.elapsed_time(e1_) / reps
+    for p_ in plans.values():
+        p_.check()
+        p_.close()
+    same = bool(torch.equal(cp, cp2) and torch.equal(ri, ri2) and torch.equal(vo.view(torch.int32), vo2.view(torch.int32)))
+    peak, peak_kind = load_peaks()
+    lit = sum(algorithmic_bytes(int(b["n"][g]), int(b["m"][g]), True)[0] for g in range(ng))
+    gbs = lit / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": m_tot / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batched-4096-zipf", "graphs": ng, "n_edges": m_tot, "n_vertices": v_tot,
+                       "sizes": "n log-uniform [1024, 262144], Zipf(2) out-degree mean U[8,32], Zipf(1.5) dst",
+                       "l2": "inputs larger than L2 (no flush needed)"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": None, "kernel": "whole batch (CUDA graph replay)", "peak_kind": peak_kind},
+            "per_graph_baseline": {"value": m_tot / (ms_pg * 1e-3), "unit": UNIT, "ms_per_step": ms_pg,
+                                   "speedup_batched": ms_pg / ms, "identical_output": same},
+            "batch_info": info, "clocks": clk.summary(), "gpu_launches": info["kernel_launches"] * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="rmat28-degree", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat28-degree", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=None, help="JSON gt_config overrides")
     ap.add_argument("--no-e2e", action="store_true")
@@ -243,6 +327,14 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        import torch
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        if rank == 0:
+            run_batched(args)
         return
 
     import torch

@@ -70,17 +70,18 @@ typedef struct gt_config {
     uint32_t hdv_k;           /* max number of HDV (0 = pure atomic, Algorithm 1)         */
     uint32_t table_log2;      /* log2 of hash-table slots; 2^table_log2 >= 2*hdv_k       */
     uint32_t block_threads;   /* threads per CTA for the count/scatter passes (64..1024, multiple of 32) */
-    uint32_t ctas_per_sm;     /* CTAs per SM for the count/scatter passes (1..32)          */
+    uint32_t ctas_per_sm;     /* CTAs per SM for the count/scatter (HLH) or digit (radix) passes (1..32) */
     uint32_t warp_edges;      /* target edges per warp partition (>= 32)                   */
     uint32_t stage_edges;     /* edges per bulk-copy stage per warp (0 = direct loads; else 128..4096, multiple of 128) */
     uint32_t sample_permille; /* sample size in 1/1000 of n (Sec. IV-C uses 10 = 1 %)     */
     uint32_t flags;           /* GT_FLAG_* bits                                            */
     uint32_t method;          /* GT_METHOD_*                                               */
-    uint32_t reserved;        /* must be 0                                                 */
+    uint32_t radix_tile;      /* GT_METHOD_RADIX: edges per CTA tile, 2048 or 4096 (0 = 4096) */
     uint64_t seed;            /* seed of the sampling positions                            */
 } gt_config;
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
+#define GT_FLAG_NO_GRAPH 2u   /* batches: launch kernels directly, no CUDA graph        */
 
 /* GT_METHOD_HLH: PoTra's hash-based LDV-HDV method (Algorithm 2; hdv_k = 0 is
  *   Atomic GT, Algorithm 1) with the LDV list sort.
@@ -142,6 +143,13 @@ gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *co
                        const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out,
                        void *stream);
 
+/* gt_transpose for a graph no larger than the plan's (n_vertices <= the
+ * plan's n, n_edges <= the plan's m), on the plan's workspace: one plan can
+ * serve a stream of graphs of varying size. */
+gt_status gt_transpose_sub(gt_plan plan, uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
+                           const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
+                           float *vals_out, void *stream);
+
 /* Same as gt_transpose on HOST arrays (pinned memory recommended): copies the
  * inputs to plan-owned device buffers, transposes, copies the outputs back and
  * synchronises the stream.  Returns the device status as well. */
@@ -165,6 +173,52 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
 gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
                                const uint32_t *col_idx, const float *vals, uint64_t *col_ptr,
                                uint32_t *row_idx, float *vals_out, void *stream);
+
+/* ---- Batches: many independent graphs in one launch sequence ------------
+ * A batch plan transposes every graph of a fixed descriptor list with the
+ * radix method over the union of the graphs (key = graph, destination),
+ * split into sub-batches of at most ~2^31 edges; the whole kernel sequence
+ * is captured once into a CUDA graph and replayed by gt_transpose_batched.
+ * The output of every graph equals gt_transpose's. */
+typedef struct gt_graph_desc {
+    uint32_t n_vertices;
+    uint32_t reserved;        /* must be 0 */
+    uint64_t n_edges;
+    const uint64_t *row_ptr;  /* device, n_vertices + 1 */
+    const uint32_t *col_idx;  /* device, n_edges */
+    const float *vals;        /* device, n_edges, or NULL (all graphs alike) */
+    uint64_t *col_ptr;        /* device, n_vertices + 1 (output) */
+    uint32_t *row_idx;        /* device, n_edges (output) */
+    float *vals_out;          /* device, n_edges, NULL iff vals is NULL */
+} gt_graph_desc;
+
+typedef struct gt_batch_info {
+    uint32_t n_graphs;
+    uint32_t sub_batches;
+    uint32_t passes_max;      /* digit passes of the widest sub-batch          */
+    uint32_t kernel_launches; /* kernels in one batch transposition            */
+    uint64_t n_edges;         /* total edges                                  */
+    uint64_t workspace_bytes;
+} gt_batch_info;
+
+typedef struct gt_batch_plan_s *gt_batch_plan;
+
+/* descs: HOST array of n_graphs descriptors (copied; the pointers inside are
+ * used by every later gt_transpose_batched).  Graphs may be empty; every
+ * graph needs n_vertices >= 1.  cfg: method must be GT_METHOD_RADIX (or cfg
+ * NULL); radix_tile and ctas_per_sm apply; flags bit GT_FLAG_NO_GRAPH runs
+ * the kernels directly instead of through a CUDA graph. */
+gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_graph_desc *descs, int has_vals,
+                               const gt_config *cfg, void *stream);
+
+/* Enqueues the transposition of every graph of the plan on `stream`
+ * (captures the CUDA graph on the first call: make it before any outside
+ * capture of that stream).  Device errors: gt_batch_plan_status. */
+gt_status gt_transpose_batched(gt_batch_plan plan, void *stream);
+
+gt_status gt_batch_plan_status(gt_batch_plan plan);
+gt_status gt_batch_plan_info(gt_batch_plan plan, gt_batch_info *info);
+void gt_batch_plan_destroy(gt_batch_plan plan);
 
 /* Synchronises the plan's last stream and returns (then clears) the latched
  * device status. */

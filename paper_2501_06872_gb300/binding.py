@@ -31,7 +31,7 @@ class Config(ctypes.Structure):
                 ("block_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("warp_edges", ctypes.c_uint32), ("stage_edges", ctypes.c_uint32),
                 ("sample_permille", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("method", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("method", ctypes.c_uint32), ("radix_tile", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -65,12 +65,29 @@ class Timing(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p), ("vals_out", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_graphs", ctypes.c_uint32), ("sub_batches", ctypes.c_uint32), ("passes_max", ctypes.c_uint32),
+                ("kernel_launches", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan_get_config",
-           "gt_transpose", "gt_transpose_host", "gt_plan_status", "gt_plan_stats",
+           "gt_transpose", "gt_transpose_sub", "gt_transpose_host", "gt_plan_status", "gt_plan_stats",
            "gt_plan_enable_timing", "gt_plan_timing", "gt_plan_workspace_bytes", "gt_plan_destroy",
-           "gt_status_string", "gt_last_cuda_error", "gt_version", "gt_transpose_noalloc"]
+           "gt_status_string", "gt_last_cuda_error", "gt_version", "gt_transpose_noalloc",
+           "gt_batch_plan_create", "gt_transpose_batched", "gt_batch_plan_status", "gt_batch_plan_info",
+           "gt_batch_plan_destroy"]
 
 
 def load():
@@ -89,10 +106,21 @@ def load():
     lib.gt_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
     lib.gt_transpose.argtypes = [P, P, P, P, P, P, P, P]
     lib.gt_transpose_host.argtypes = [P, P, P, P, P, P, P, P]
+    lib.gt_transpose_sub.argtypes = [P, u32, u64, P, P, P, P, P, P, P]
+    lib.gt_transpose_sub.restype = ctypes.c_int
     lib.gt_plan_status.argtypes = [P]
     lib.gt_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.gt_transpose_noalloc.argtypes = [u32, u64, P, P, P, P, P, P, P]
     lib.gt_transpose_noalloc.restype = ctypes.c_int
+    lib.gt_batch_plan_create.argtypes = [ctypes.POINTER(P), u32, ctypes.POINTER(GraphDesc), ctypes.c_int,
+                                         ctypes.POINTER(Config), P]
+    lib.gt_transpose_batched.argtypes = [P, P]
+    lib.gt_batch_plan_status.argtypes = [P]
+    lib.gt_batch_plan_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
+    lib.gt_batch_plan_destroy.argtypes = [P]
+    lib.gt_batch_plan_destroy.restype = None
+    for f in ["gt_batch_plan_create", "gt_transpose_batched", "gt_batch_plan_status", "gt_batch_plan_info"]:
+        getattr(lib, f).restype = ctypes.c_int
     lib.gt_plan_enable_timing.argtypes = [P, ctypes.c_int]
     lib.gt_plan_timing.argtypes = [P, ctypes.POINTER(Timing)]
     lib.gt_plan_workspace_bytes.argtypes = [P]
@@ -176,6 +204,12 @@ class Plan:
                                     _ptr(row_idx), _ptr(vals_out), _stream(stream))
         _check(rc, "gt_transpose")
 
+    def transpose_sub(self, n, m, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
+        """Enqueue a graph no larger than the plan's on the plan's workspace."""
+        rc = self._lib.gt_transpose_sub(self._h, int(n), int(m), _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                        _ptr(col_ptr), _ptr(row_idx), _ptr(vals_out), _stream(stream))
+        _check(rc, "gt_transpose_sub")
+
     def transpose_host(self, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
         """CSR -> CSC on host arrays (pinned recommended); synchronous, returns status."""
         rc = self._lib.gt_transpose_host(self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
@@ -207,6 +241,58 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """Owns a gt_batch_plan over a fixed list of graphs (device pointers).
+
+    graphs: sequence of dicts with n, m, row_ptr, col_idx, vals, col_ptr,
+    row_idx, vals_out (torch tensors or raw device addresses)."""
+
+    def __init__(self, graphs, weighted: bool, config: Config | dict | None = None, stream=None):
+        lib = load()
+        self._lib = lib
+        arr = (GraphDesc * len(graphs))()
+
+        def addr(x):
+            if x is None:
+                return None
+            return x if isinstance(x, int) else x.data_ptr()
+        for i, g in enumerate(graphs):
+            arr[i] = GraphDesc(int(g["n"]), 0, int(g["m"]), addr(g["row_ptr"]), addr(g["col_idx"]),
+                               addr(g.get("vals")), addr(g["col_ptr"]), addr(g["row_idx"]), addr(g.get("vals_out")))
+        if isinstance(config, dict):
+            config = Config.from_dict(config)
+        h = ctypes.c_void_p()
+        cfgp = ctypes.byref(config) if config is not None else None
+        _check(lib.gt_batch_plan_create(ctypes.byref(h), len(graphs), arr, int(weighted), cfgp, None),
+               "gt_batch_plan_create")
+        self._h = h
+
+    def transpose(self, stream=None):
+        _check(self._lib.gt_transpose_batched(self._h, _stream(stream)), "gt_transpose_batched")
+
+    def status(self) -> int:
+        return self._lib.gt_batch_plan_status(self._h)
+
+    def check(self):
+        _check(self.status(), "batch device status")
+
+    def info(self) -> dict:
+        b = BatchInfo()
+        _check(self._lib.gt_batch_plan_info(self._h, ctypes.byref(b)), "gt_batch_plan_info")
+        return b.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gt_batch_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):

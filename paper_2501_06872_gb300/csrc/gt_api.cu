@@ -66,7 +66,8 @@ bool config_valid(const gt_config &c) {
   if (c.warp_edges < 32) return false;
   if (c.stage_edges != 0 && (c.stage_edges < 128 || c.stage_edges > 4096 || c.stage_edges % 128)) return false;
   if (c.sample_permille > 1000) return false;
-  if (c.method > GT_METHOD_RADIX || c.reserved != 0) return false;
+  if (c.method > GT_METHOD_RADIX) return false;
+  if (c.radix_tile != 0 && c.radix_tile != 2048 && c.radix_tile != 4096) return false;
   return true;
 }
 
@@ -99,7 +100,10 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   w.big_cap = (uint32_t)gt::worklist_entries(w.m);
   w.flag_mode = (w.has_vals && w.n <= 0x80000000u) ? 1 : 0;
   w.method = (int)c.method;
-  w.rG = (uint32_t)num_sms * 4u;
+  // radix method: radix_tile selects the tile (256 threads x 8 or 16 items),
+  // ctas_per_sm the persistent grid
+  w.r_items = c.radix_tile == 2048 ? 8u : 16u;
+  w.rG = (uint32_t)num_sms * c.ctas_per_sm;
   if (w.method == GT_METHOD_RADIX) {
     w.kmax = 0;
     w.tlog2 = 0;
@@ -318,17 +322,54 @@ gt_status gt_plan_get_config(gt_plan plan, gt_config *cfg) {
   return GT_OK;
 }
 
-gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
-                       uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+// Launch shape of a smaller graph on a plan's buffers (every buffer size is
+// monotone in n and m for a fixed configuration).
+static gt_status shape_for(gt_plan plan, uint32_t n, uint64_t m, gt::DevWork &w) {
+  w = plan->w;
+  if (n == w.n && m == w.m) return GT_OK;
+  gt::DevWork t;
+  t.n = n;
+  t.m = m;
+  t.has_vals = w.has_vals;
+  gt_status st = derive_shape(t, plan->cfg, w.num_sms);
+  if (st != GT_OK) return st;
+  w.n = t.n;
+  w.m = t.m;
+  w.kmax = t.kmax;
+  w.tlog2 = t.tlog2;
+  w.W = t.W;
+  w.G = t.G;
+  w.P = t.P;
+  w.psize = t.psize;
+  w.ns = t.ns;
+  w.ts_log2 = t.ts_log2;
+  w.ntiles = t.ntiles;
+  w.big_cap = t.big_cap;
+  w.flag_mode = t.flag_mode;
+  w.staged = t.staged;
+  w.stage_edges = t.stage_edges;
+  w.smem_count = t.smem_count;
+  w.smem_scatter = t.smem_scatter;
+  w.method = t.method;
+  w.rG = t.rG;
+  w.r_items = t.r_items;
+  return GT_OK;
+}
+
+static gt_status transpose_impl(gt_plan plan, uint32_t n, uint64_t m, const uint64_t *row_ptr,
+                                const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
+                                float *vals_out, void *stream) {
   if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
-  const gt::DevWork &w0 = plan->w;
-  if (w0.m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
+  if (m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
   if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
-  if (vals && !w0.has_vals) return GT_ERR_INVALID_ARG;
+  if (vals && !plan->w.has_vals) return GT_ERR_INVALID_ARG;
+  if (n == 0 && m != 0) return GT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   plan->last = s;
-  if (w0.n == 0) return from_cuda(cudaMemsetAsync(col_ptr, 0, 8, s));
-  gt::DevWork w = w0;
+  if (n == 0) return from_cuda(cudaMemsetAsync(col_ptr, 0, 8, s));
+  gt::DevWork w;
+  gt_status sst = shape_for(plan, n, m, w);
+  if (sst != GT_OK) return sst;
   // bulk copies need 16-byte aligned sources; fall back to direct loads otherwise
   if (w.staged && ((((uintptr_t)col_idx) & 15u) || (vals && (((uintptr_t)vals) & 15u)))) {
     w.staged = 0;
@@ -348,6 +389,20 @@ gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *co
     ev = &plan->events.back();
   }
   return from_cuda(gt::run_transpose(w, plan->cfg, pb, s, ev, &plan->launches));
+}
+
+gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                       uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  return transpose_impl(plan, plan->w.n, plan->w.m, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream);
+}
+
+gt_status gt_transpose_sub(gt_plan plan, uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
+                           const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
+                           float *vals_out, void *stream) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  if (n_vertices > plan->w.n || n_edges > plan->w.m) return GT_ERR_INVALID_ARG;
+  return transpose_impl(plan, n_vertices, n_edges, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream);
 }
 
 gt_status gt_plan_enable_timing(gt_plan plan, int enable) {

@@ -60,6 +60,7 @@ struct DevWork {
   // radix method
   int method = 0;
   uint32_t rG = 0;                            // persistent CTAs of the digit passes
+  uint32_t r_items = 16;                      // elements per thread of a downsweep tile (8 or 16)
   uint32_t *r_a_key = nullptr, *r_a_u = nullptr, *r_a_w = nullptr;  // [m] ping buffer
   uint32_t *r_b_key = nullptr;                // [m] keys of the pong buffer (u/w live in the outputs)
   uint32_t *r_long = nullptr;                 // rows longer than the window expansion handles
@@ -92,6 +93,41 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
 // Radix method: enqueues the digit passes and the degree runs (deg must be zeroed).
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches,
                       StepEvents *events);
+
+// One sub-batch of a batch plan (device pointers; sizes on the host).
+struct SubBatch {
+  uint32_t g0 = 0, ng = 0;                // graphs [g0, g0 + ng) of the plan
+  uint64_t m = 0;                         // union edges
+  uint32_t nv = 0;                        // union vertices
+  uint32_t vbits = 1, passes = 1, dbits = 1;
+  uint64_t windows = 0;                   // 32-row windows over all graphs
+  const gt_graph_desc *descs = nullptr;   // device, ng entries
+  unsigned long long *eoff = nullptr, *voff = nullptr, *woff = nullptr;  // device, ng + 1 each
+};
+
+struct BatchWork {
+  int has_vals = 0;
+  int num_sms = 0;
+  uint32_t rG = 0, r_items = 16;
+  uint32_t *a_key = nullptr, *a_u = nullptr, *a_w = nullptr;  // [max m]
+  uint32_t *b_key = nullptr, *b_u = nullptr, *b_w = nullptr;  // [max m]
+  uint32_t *deg = nullptr;                                      // [max nv]
+  unsigned long long *ucp = nullptr;                            // [max nv + 1]
+  unsigned long long *scan_state = nullptr;                     // [max nv tiles]
+  uint32_t *table = nullptr;                                    // [rG][256]
+  unsigned long long *offsets = nullptr;                        // [rG][256]
+  uint32_t *long_g = nullptr, *long_r = nullptr, *n_long = nullptr;
+  uint32_t long_cap = 0;
+  uint32_t *status = nullptr, *meta = nullptr;
+};
+
+cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_t s, uint32_t *launches);
+
+// Exclusive look-back scan (Step 2) as a separate launch; row_ptr may be null
+// (no row-pointer validation); cursor may be null.
+cudaError_t launch_scan(const uint32_t *deg, uint32_t n, uint64_t m, const uint64_t *row_ptr, uint64_t *col_ptr,
+                        unsigned long long *cursor, unsigned long long *state, uint32_t ntiles, uint32_t *meta,
+                        uint32_t *status, cudaStream_t s);
 
 // Shared-memory bytes needed by the count / scatter kernels for a shape.
 uint32_t smem_count_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged, uint32_t stage_edges,

@@ -27,8 +27,6 @@ namespace gt {
 
 constexpr int kRThreads = 256;
 constexpr int kRWarps = kRThreads / 32;
-constexpr int kRItems = 16;
-constexpr uint32_t kRTile = kRThreads * kRItems;  // 4096 edges
 constexpr int kRBins = 256;
 
 // Lanes holding the same dbits-bit digit (and active): AND of one ballot per
@@ -41,6 +39,26 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t dbits, bool
     mm &= bit ? bb : ~bb;
   }
   return mm;
+}
+
+// Batch view: graphs g0 .. g0+ng-1 of the descriptor array, laid out one after
+// another in a union edge space (eoff) and vertex space (voff); a union key is
+// (local graph << vbits) | vertex.
+struct BatchView {
+  const gt_graph_desc *descs;         // descriptors of this sub-batch (device)
+  const unsigned long long *eoff;     // [ng + 1]
+  const unsigned long long *voff;     // [ng + 1]
+  uint32_t ng, vbits;
+};
+
+__device__ __forceinline__ uint32_t upper_graph(const unsigned long long *off, uint32_t ng, uint64_t x) {
+  uint32_t lo = 0, hi = ng;  // largest g with off[g] <= x
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) / 2;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
 struct RadixArgs {
@@ -56,10 +74,18 @@ struct RadixArgs {
   uint32_t *out_key, *out_u, *out_w;
   uint32_t shift, dbits;
   uint32_t ntiles, tiles_per_cta;
+  uint32_t tile;  // elements per tile (threads * items)
   uint32_t *table;                    // [G][256] counts
   const unsigned long long *offsets;  // [G][256] starting positions
   uint32_t *status;
+  BatchView batch;
 };
+
+// Pass modes: plain arrays, or a batch whose first pass loads through the
+// descriptors and whose last pass stores through them.
+enum RadixMode : int { kPlain = 0, kBatchFirst = 1, kBatchLast = 2, kBatchOnly = 3 };
+__host__ __device__ constexpr bool loads_batch(int mode) { return mode == kBatchFirst || mode == kBatchOnly; }
+__host__ __device__ constexpr bool stores_batch(int mode) { return mode == kBatchLast || mode == kBatchOnly; }
 
 // Writes the source row of every edge (src[e] = u for e in row u).  Rows of
 // at most kLongRow edges: 32 rows per warp step, whose edges form one
@@ -67,16 +93,20 @@ struct RadixArgs {
 // ends held in registers.  Longer rows are listed for k_expand_long.
 constexpr uint32_t kLongRow = 2048;
 
-__global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n, uint32_t *src, uint32_t *long_rows,
-                              uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
+__global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n, uint64_t m, uint32_t *src,
+                              uint32_t *long_rows, uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n; r0 += warps * 32) {
     const uint64_t r = r0 + lane;
     uint64_t ri = r + 1;
     if (ri > n) ri = n;
-    const uint64_t rend = row_ptr[ri];  // end of row r (clamped)
-    const uint64_t rbeg = r < n ? row_ptr[r] : rend;
+    uint64_t rend = row_ptr[ri];  // end of row r (clamped)
+    uint64_t rbeg = r < n ? row_ptr[r] : rend;
+    if (rend > m || rbeg > rend) {  // invalid row pointers: report, write nothing out of range
+      set_status(status, GT_ERR_BAD_ROW_PTR);
+      rend = rbeg = 0;
+    }
     const bool is_long = r < n && rend - rbeg > kLongRow;
     if (is_long) {
       uint32_t i = atomicAdd(n_long, 1u);
@@ -111,42 +141,65 @@ __global__ void k_expand_long(const uint64_t *__restrict__ row_ptr, const uint32
   const uint32_t cnt = min(*n_long, long_cap);
   for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const uint32_t r = long_rows[i];
-    const uint64_t b = row_ptr[r], e = row_ptr[r + 1];
+    const uint64_t b = row_ptr[r], e = row_ptr[r + 1];  // checked by k_expand_rows
     for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) src[p] = r;
   }
 }
 
-// Counts the digits of this CTA's tiles (8 loads in flight per thread).
-template <bool FIRST>
+// Counts the digits of this CTA's tiles: per-warp shared-memory histograms,
+// 8 loads in flight per thread.
+template <bool FIRST, int MODE>
 __global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
-  __shared__ uint32_t cnt[kRBins];
-  for (uint32_t i = threadIdx.x; i < kRBins; i += blockDim.x) cnt[i] = 0;
+  __shared__ uint32_t cnt[kRWarps][kRBins];
+  for (uint32_t i = threadIdx.x; i < kRWarps * kRBins; i += blockDim.x) (&cnt[0][0])[i] = 0;
   __syncthreads();
   const uint32_t mask = (1u << a.dbits) - 1u;
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
   const uint64_t t0 = (uint64_t)blockIdx.x * a.tiles_per_cta;
-  const uint64_t e0 = min64(t0 * kRTile, a.m), e1 = min64((t0 + a.tiles_per_cta) * kRTile, a.m);
+  const uint64_t e0 = min64(t0 * a.tile, a.m), e1 = min64((t0 + a.tiles_per_cta) * a.tile, a.m);
   const uint32_t *src = a.in_key;
   constexpr int U = 8;
+  uint32_t bad = 0;
   for (uint64_t c = e0 + (uint64_t)w * 32 * U; c < e1; c += (uint64_t)kRWarps * 32 * U) {
     uint32_t key[U];
+    if (loads_batch(MODE)) {
+      uint32_t g = upper_graph(a.batch.eoff, a.batch.ng, c < e1 ? c : e1 - 1);
 #pragma unroll
-    for (int i = 0; i < U; ++i) {
-      const uint64_t e = c + (uint64_t)i * 32 + lane;
-      key[i] = e < e1 ? __ldcs(src + e) : 0u;
+      for (int i = 0; i < U; ++i) {
+        const uint64_t e = c + (uint64_t)i * 32 + lane;
+        key[i] = 0xFFFFFFFFu;
+        if (e < e1) {
+          while (e >= a.batch.eoff[g + 1]) ++g;
+          const gt_graph_desc &d = a.batch.descs[g];
+          const uint32_t v = __ldcs(d.col_idx + (e - a.batch.eoff[g]));
+          if (v >= d.n_vertices) bad = 1;
+          key[i] = (g << a.batch.vbits) | (v & ((1u << a.batch.vbits) - 1u));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const uint64_t e = c + (uint64_t)i * 32 + lane;
+        key[i] = e < e1 ? __ldcs(src + e) : 0xFFFFFFFFu;
+      }
     }
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint64_t e = c + (uint64_t)i * 32 + lane;
-      const bool act = e < e1;
-      if (FIRST && act && key[i] >= a.n) set_status(a.status, GT_ERR_OUT_OF_RANGE);
-      const uint32_t d = act ? ((key[i] >> a.shift) & mask) : 0u;
-      const uint32_t mm = match_digit(d, a.dbits, act);
-      if (act && (mm & lanemask_lt()) == 0) atomicAdd(&cnt[d], __popc(mm));
+      if (e < e1) {
+        if (FIRST && !loads_batch(MODE) && key[i] >= a.n) bad = 1;
+        atomicAdd(&cnt[w][(key[i] >> a.shift) & mask], 1u);
+      }
     }
   }
+  if (bad) set_status(a.status, GT_ERR_OUT_OF_RANGE);
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kRBins; i += blockDim.x) a.table[(size_t)blockIdx.x * kRBins + i] = cnt[i];
+  for (uint32_t d = threadIdx.x; d < kRBins; d += blockDim.x) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int x = 0; x < kRWarps; ++x) t += cnt[x][d];
+    a.table[(size_t)blockIdx.x * kRBins + d] = t;
+  }
 }
 
 // Exclusive scan of table[G][256] in (digit, cta) order -> offsets[G][256].
@@ -216,15 +269,16 @@ __global__ void __launch_bounds__(1024) k_radix_offsets(const uint32_t *__restri
   }
 }
 
-template <bool VALS>
+template <bool VALS, int ITEMS, int MODE>
 __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
-  extern __shared__ __align__(16) uint32_t stage[];  // [kRTile] keys | [kRTile] sources | [kRTile] values
+  constexpr uint32_t TILE = kRThreads * ITEMS;
+  extern __shared__ __align__(16) uint32_t stage[];  // [TILE] keys | [TILE] sources | [TILE] values
   __shared__ uint32_t wcnt[kRWarps][kRBins];
   __shared__ unsigned long long run_off[kRBins];
   __shared__ uint32_t tile_tot[kRBins];
   __shared__ uint32_t tile_start[kRBins];
   __shared__ uint32_t wsum[kRWarps];
-  uint32_t *skey = stage, *su = stage + kRTile, *sw = stage + 2 * kRTile;
+  uint32_t *skey = stage, *su = stage + TILE, *sw = stage + 2 * TILE;
   const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t mask = (1u << a.dbits) - 1u;
   for (uint32_t d = threadIdx.x; d < kRBins; d += blockDim.x)
@@ -233,28 +287,47 @@ __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
   const uint64_t t1 = min64(t0 + a.tiles_per_cta, a.ntiles);
   for (uint64_t tile = t0; tile < t1; ++tile) {
     for (uint32_t i = threadIdx.x; i < kRWarps * kRBins; i += blockDim.x) (&wcnt[0][0])[i] = 0;
-    const uint64_t tbase = tile * kRTile;
-    const uint64_t base = tbase + (uint64_t)w * (kRItems * 32);
-    const uint32_t tcount = (uint32_t)min64(kRTile, a.m - tbase);
-    uint32_t key[kRItems], uu[kRItems], ww[kRItems], rk[kRItems];
+    const uint64_t tbase = tile * TILE;
+    const uint64_t base = tbase + (uint64_t)w * (ITEMS * 32);
+    const uint32_t tcount = (uint32_t)min64(TILE, a.m - tbase);
+    uint32_t key[ITEMS], uu[ITEMS], ww[ITEMS], rk[ITEMS];
     // all of this warp's loads are in flight before any ranking
+    if (loads_batch(MODE)) {
+      uint32_t g = upper_graph(a.batch.eoff, a.batch.ng, base < a.m ? base : a.m - 1);
 #pragma unroll
-    for (int i = 0; i < kRItems; ++i) {
-      const uint64_t e = base + (uint64_t)i * 32 + lane;
-      if (e < a.m) {
-        key[i] = __ldcs(a.in_key + e);
-        uu[i] = __ldcs(a.in_u + e);
-        ww[i] = VALS ? __ldcs(a.in_w + e) : 0u;
-      } else {
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint64_t e = base + (uint64_t)i * 32 + lane;
         key[i] = 0u;
         uu[i] = 0u;
         ww[i] = 0u;
+        if (e < a.m) {
+          while (e >= a.batch.eoff[g + 1]) ++g;
+          const gt_graph_desc &d = a.batch.descs[g];
+          const uint64_t le = e - a.batch.eoff[g];
+          key[i] = (g << a.batch.vbits) | (__ldcs(d.col_idx + le) & ((1u << a.batch.vbits) - 1u));
+          uu[i] = __ldcs(a.in_u + e);
+          if (VALS) ww[i] = __float_as_uint(__ldcs(d.vals + le));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint64_t e = base + (uint64_t)i * 32 + lane;
+        if (e < a.m) {
+          key[i] = __ldcs(a.in_key + e);
+          uu[i] = __ldcs(a.in_u + e);
+          ww[i] = VALS ? __ldcs(a.in_w + e) : 0u;
+        } else {
+          key[i] = 0u;
+          uu[i] = 0u;
+          ww[i] = 0u;
+        }
       }
     }
     __syncthreads();
     // stable rank within the warp: items in order, lanes in order
 #pragma unroll
-    for (int i = 0; i < kRItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       const bool act = base + (uint64_t)i * 32 + lane < a.m;
       const uint32_t d = (key[i] >> a.shift) & mask;
       const uint32_t mm = match_digit(d, a.dbits, act);
@@ -296,7 +369,7 @@ __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
     __syncthreads();
     // place the tile in shared memory in (digit, rank) order
 #pragma unroll
-    for (int i = 0; i < kRItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       if (rk[i] != 0xFFFFFFFFu) {
         const uint32_t d = (key[i] >> a.shift) & mask;
         const uint32_t lp = tile_start[d] + wcnt[w][d] + rk[i];
@@ -312,8 +385,16 @@ __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
       const uint32_t d = (k >> a.shift) & mask;
       const uint64_t pos = run_off[d] + (j - tile_start[d]);
       a.out_key[pos] = k;
-      a.out_u[pos] = su[j];
-      if (VALS) a.out_w[pos] = sw[j];
+      if (stores_batch(MODE)) {
+        const uint32_t g = k >> a.batch.vbits;
+        const gt_graph_desc &gd = a.batch.descs[g];
+        const uint64_t lp = pos - a.batch.eoff[g];
+        gd.row_idx[lp] = su[j];
+        if (VALS) gd.vals_out[lp] = __uint_as_float(sw[j]);
+      } else {
+        a.out_u[pos] = su[j];
+        if (VALS) a.out_w[pos] = sw[j];
+      }
     }
     __syncthreads();
     run_off[threadIdx.x] += tot;
@@ -340,15 +421,31 @@ static uint32_t key_bits_of(uint32_t n) {
   return bits ? bits : 1u;
 }
 
-cudaError_t configure_radix() {
-  cudaError_t e1 = allow_max_dynamic_smem(k_radix_down<true>);
-  cudaError_t e2 = allow_max_dynamic_smem(k_radix_down<false>);
+template <int ITEMS, int MODE>
+static cudaError_t allow_down() {
+  cudaError_t e1 = allow_max_dynamic_smem(k_radix_down<true, ITEMS, MODE>);
+  cudaError_t e2 = allow_max_dynamic_smem(k_radix_down<false, ITEMS, MODE>);
   return e1 != cudaSuccess ? e1 : e2;
 }
 
-uint64_t radix_workspace_bytes(uint64_t m, int has_vals, uint32_t G) {
-  const uint64_t ntiles = (m + kRTile - 1) / kRTile;
-  return m * 4 * (has_vals ? 4 : 3) + ntiles * 4 + (uint64_t)G * kRBins * (4 + 8) + 4096;
+cudaError_t configure_radix() {
+  cudaError_t e[8] = {allow_down<8, kPlain>(),      allow_down<16, kPlain>(),     allow_down<8, kBatchFirst>(),
+                      allow_down<16, kBatchFirst>(), allow_down<8, kBatchLast>(),  allow_down<16, kBatchLast>(),
+                      allow_down<8, kBatchOnly>(),   allow_down<16, kBatchOnly>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
+
+template <int MODE>
+static void launch_down(bool vals, uint32_t items, uint32_t G, size_t dsm, cudaStream_t s, const RadixArgs &ra) {
+  if (items == 8) {
+    if (vals) k_radix_down<true, 8, MODE><<<G, kRThreads, dsm, s>>>(ra);
+    else k_radix_down<false, 8, MODE><<<G, kRThreads, dsm, s>>>(ra);
+  } else {
+    if (vals) k_radix_down<true, 16, MODE><<<G, kRThreads, dsm, s>>>(ra);
+    else k_radix_down<false, 16, MODE><<<G, kRThreads, dsm, s>>>(ra);
+  }
 }
 
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint32_t *launches, StepEvents *ev) {
@@ -360,7 +457,9 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   const uint32_t bits = key_bits_of(n);
   const uint32_t passes = (bits + 7) / 8;
   const uint32_t dbits = (bits + passes - 1) / passes;
-  const uint32_t ntiles = (uint32_t)((m + kRTile - 1) / kRTile);
+  const uint32_t items = w.r_items;
+  const uint32_t tile = kRThreads * items;
+  const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
   const uint32_t G = w.rG;
   const uint32_t tpc = (ntiles + G - 1) / G;
   if (m == 0) return cudaSuccess;
@@ -375,7 +474,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     uint32_t g = (uint32_t)min64((warps + 7) / 8, (uint64_t)w.num_sms * 16);
     if (g == 0) g = 1;
     const uint32_t long_cap = (uint32_t)(m / (kLongRow + 1) + 1);
-    k_expand_rows<<<g, 256, 0, s>>>(pb.row_ptr, n, src_rows, w.r_long, w.r_nlong, long_cap, w.status);
+    k_expand_rows<<<g, 256, 0, s>>>(pb.row_ptr, n, m, src_rows, w.r_long, w.r_nlong, long_cap, w.status);
     k_expand_long<<<w.num_sms * 4, 256, 0, s>>>(pb.row_ptr, w.r_long, w.r_nlong, long_cap, src_rows);
     nl += 2;
   }
@@ -384,14 +483,13 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     const bool toB = ((passes - p) % 2) == 0;
     uint32_t *ok = toB ? w.r_b_key : w.r_a_key, *ou = toB ? b_u : w.r_a_u, *ow = toB ? b_w : w.r_a_w;
     RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
-                 (p - 1) * dbits, dbits, ntiles, tpc, w.r_table, w.r_offsets, w.status};
-    if (p == 1) k_radix_up<true><<<G, kRThreads, 0, s>>>(ra);
-    else k_radix_up<false><<<G, kRThreads, 0, s>>>(ra);
+                 (p - 1) * dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status, BatchView{}};
+    if (p == 1) k_radix_up<true, kPlain><<<G, kRThreads, 0, s>>>(ra);
+    else k_radix_up<false, kPlain><<<G, kRThreads, 0, s>>>(ra);
     k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G, w.r_offsets);
     if (ev && ev->ndown + 2 <= 8) cudaEventRecord(ev->down[ev->ndown], s);
-    const size_t dsm = (size_t)kRTile * 4 * (vals ? 3 : 2);
-    if (vals) k_radix_down<true><<<G, kRThreads, dsm, s>>>(ra);
-    else k_radix_down<false><<<G, kRThreads, dsm, s>>>(ra);
+    const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
+    launch_down<kPlain>(vals, items, G, dsm, s, ra);
     if (ev && ev->ndown + 2 <= 8) {
       cudaEventRecord(ev->down[ev->ndown + 1], s);
       ev->ndown += 2;
@@ -405,6 +503,172 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   uint32_t g = (uint32_t)min64((m + 255) / 256, (uint64_t)w.num_sms * 16);
   k_radix_runs<<<g, 256, 0, s>>>(w.r_b_key, m, n, w.deg);
   ++nl;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches (sub-batch of graphs laid out in union edge / vertex spaces)
+// ---------------------------------------------------------------------------
+
+// Per graph: row_ptr[0] == 0 and row_ptr[n] == m.
+__global__ void k_b_check(BatchView bv, uint32_t *status) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < bv.ng; g += gridDim.x * blockDim.x) {
+    const gt_graph_desc &d = bv.descs[g];
+    if (d.n_vertices == 0 || d.row_ptr[0] != 0 || d.row_ptr[d.n_vertices] != d.n_edges)
+      set_status(status, GT_ERR_BAD_ROW_PTR);
+  }
+}
+
+// Source rows of every union edge: windows of 32 rows of one graph per warp step.
+__global__ void k_b_expand(BatchView bv, const unsigned long long *__restrict__ woff, uint64_t windows, uint32_t *src,
+                           uint32_t *long_g, uint32_t *long_r, uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t wi = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); wi < windows; wi += warps) {
+    const uint32_t g = upper_graph(woff, bv.ng, wi);
+    const gt_graph_desc &d = bv.descs[g];
+    const uint32_t n = d.n_vertices;
+    const uint64_t m = d.n_edges, base = bv.eoff[g];
+    const uint64_t r0 = (wi - woff[g]) * 32;
+    const uint64_t r = r0 + lane;
+    uint64_t ri = r + 1;
+    if (ri > n) ri = n;
+    uint64_t rend = d.row_ptr[ri];
+    uint64_t rbeg = r < n ? d.row_ptr[r] : rend;
+    if (rend > m || rbeg > rend) {
+      set_status(status, GT_ERR_BAD_ROW_PTR);
+      rend = rbeg = 0;
+    }
+    const bool is_long = r < n && rend - rbeg > kLongRow;
+    if (is_long) {
+      uint32_t i = atomicAdd(n_long, 1u);
+      if (i < long_cap) {
+        long_g[i] = g;
+        long_r[i] = (uint32_t)r;
+      } else {
+        set_status(status, GT_ERR_UNSUPPORTED);
+      }
+    }
+    const uint32_t longmask = __ballot_sync(kFull, is_long);
+    const uint64_t b = __shfl_sync(kFull, rbeg, 0);
+    const uint64_t e = __shfl_sync(kFull, rend, 31);
+    const bool sane = __all_sync(kFull, !(rend > m || rbeg > rend)) && e >= b;
+    if (longmask == 0 && sane) {
+      for (uint64_t p0 = b; p0 < e; p0 += 32) {
+        const uint64_t p = p0 + lane;
+        const uint32_t pos = count_le(rend, p);  // warp-collective
+        if (p < e) src[base + p] = (uint32_t)(r0 + pos);
+      }
+    } else {
+      uint32_t todo = __ballot_sync(kFull, r < n && !is_long && rend > rbeg);
+      while (todo) {
+        const uint32_t j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint64_t qb = __shfl_sync(kFull, rbeg, j), qe = __shfl_sync(kFull, rend, j);
+        for (uint64_t p = qb + lane; p < qe; p += 32) src[base + p] = (uint32_t)(r0 + j);
+      }
+    }
+  }
+}
+
+__global__ void k_b_expand_long(BatchView bv, const uint32_t *__restrict__ long_g, const uint32_t *__restrict__ long_r,
+                                const uint32_t *__restrict__ n_long, uint32_t long_cap, uint32_t *src) {
+  const uint32_t cnt = min(*n_long, long_cap);
+  for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const uint32_t g = long_g[i], r = long_r[i];
+    const gt_graph_desc &d = bv.descs[g];
+    const uint64_t b = d.row_ptr[r], e = d.row_ptr[r + 1], base = bv.eoff[g];
+    for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) src[base + p] = r;
+  }
+}
+
+// Degrees of the union vertices from the runs of equal sorted keys.
+__global__ void k_b_runs(BatchView bv, const uint32_t *__restrict__ key, uint64_t m, uint32_t *deg) {
+  const uint32_t vmask = (1u << bv.vbits) - 1u;
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = key[p];
+    const uint32_t g = k >> bv.vbits, v = k & vmask;
+    if (g >= bv.ng || v >= bv.descs[g].n_vertices) continue;
+    uint32_t *dv = deg + bv.voff[g] + v;
+    if (p == 0 || key[p - 1] != k) red_add_u32(dv, (uint32_t)(0u - (uint32_t)p));
+    if (p + 1 == m || key[p + 1] != k) red_add_u32(dv, (uint32_t)(p + 1));
+  }
+}
+
+// col_ptr of every graph from the union exclusive scan (and the last entry).
+__global__ void k_b_colptr(BatchView bv, const unsigned long long *__restrict__ ucp, uint64_t nv) {
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nv + bv.ng;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    if (x < nv) {
+      const uint32_t g = upper_graph(bv.voff, bv.ng, x);
+      bv.descs[g].col_ptr[x - bv.voff[g]] = ucp[x] - bv.eoff[g];
+    } else {
+      const uint32_t g = (uint32_t)(x - nv);
+      const gt_graph_desc &d = bv.descs[g];
+      d.col_ptr[d.n_vertices] = d.n_edges;
+    }
+  }
+}
+
+cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_t s, uint32_t *launches) {
+  uint32_t nl = 0;
+  cudaError_t err;
+  BatchView bv{sb.descs, sb.eoff, sb.voff, sb.ng, sb.vbits};
+  const bool vals = bw.has_vals != 0;
+  const uint64_t m = sb.m;
+  const uint32_t items = bw.r_items, tile = kRThreads * items;
+  const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
+  const uint32_t G = bw.rG;
+  const uint32_t tpc = ntiles ? (ntiles + G - 1) / G : 0;
+  const uint32_t passes = sb.passes, dbits = sb.dbits;
+  const uint32_t stiles = (sb.nv + kScanTile - 1) / kScanTile;
+  if ((err = cudaMemsetAsync(bw.deg, 0, (size_t)sb.nv * 4, s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(bw.scan_state, 0, (size_t)stiles * 8, s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(bw.meta, 0, kMetaCount * 4, s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(bw.n_long, 0, 4, s)) != cudaSuccess) return err;
+  k_b_check<<<(sb.ng + 255) / 256, 256, 0, s>>>(bv, bw.status);
+  ++nl;
+  if (m > 0) {
+    const bool first_to_b = ((passes - 1) % 2) == 0;
+    uint32_t *src_rows = first_to_b ? bw.a_u : bw.b_u;
+    uint32_t g = (uint32_t)min64((sb.windows + 7) / 8, (uint64_t)bw.num_sms * 16);
+    if (g == 0) g = 1;
+    k_b_expand<<<g, 256, 0, s>>>(bv, sb.woff, sb.windows, src_rows, bw.long_g, bw.long_r, bw.n_long, bw.long_cap,
+                                 bw.status);
+    k_b_expand_long<<<bw.num_sms * 4, 256, 0, s>>>(bv, bw.long_g, bw.long_r, bw.n_long, bw.long_cap, src_rows);
+    nl += 2;
+    const uint32_t *in_key = nullptr, *in_u = src_rows, *in_w = nullptr;
+    for (uint32_t p = 1; p <= passes; ++p) {
+      const bool toB = ((passes - p) % 2) == 0;
+      uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
+      RadixArgs ra{nullptr, nullptr, nullptr, 0, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
+                   (p - 1) * dbits, dbits, ntiles, tpc, tile, bw.table, bw.offsets, bw.status, bv};
+      if (p == 1) k_radix_up<true, kBatchFirst><<<G, kRThreads, 0, s>>>(ra);
+      else k_radix_up<false, kPlain><<<G, kRThreads, 0, s>>>(ra);
+      k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, G, bw.offsets);
+      const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
+      if (p == 1 && p == passes) launch_down<kBatchOnly>(vals, items, G, dsm, s, ra);
+      else if (p == 1) launch_down<kBatchFirst>(vals, items, G, dsm, s, ra);
+      else if (p == passes) launch_down<kBatchLast>(vals, items, G, dsm, s, ra);
+      else launch_down<kPlain>(vals, items, G, dsm, s, ra);
+      nl += 3;
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      in_key = ok;
+      in_u = ou;
+      in_w = ow;
+    }
+    uint32_t gr = (uint32_t)min64((m + 255) / 256, (uint64_t)bw.num_sms * 16);
+    k_b_runs<<<gr, 256, 0, s>>>(bv, bw.b_key, m, bw.deg);
+    ++nl;
+  }
+  if ((err = launch_scan(bw.deg, sb.nv, m, nullptr, (uint64_t *)bw.ucp, nullptr, bw.scan_state, stiles, bw.meta, bw.status, s)) !=
+      cudaSuccess)
+    return err;
+  uint32_t gc = (uint32_t)min64((sb.nv + sb.ng + 255) / 256, (uint64_t)bw.num_sms * 16);
+  k_b_colptr<<<gc, 256, 0, s>>>(bv, bw.ucp, sb.nv);
+  nl += 2;
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
     for (int i = 0; i < kScanItems; ++i) d[i] = (base + i < n) ? deg[base + i] : 0u;
   }
   // row_ptr validation on the same index range
-  {
+  if (row_ptr) {
     bool bad = false;
     for (int i = 0; i < kScanItems; ++i) {
       uint64_t r = base + i;
@@ -600,6 +600,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
       if (run != m) set_status(status, GT_ERR_OUT_OF_RANGE);
     }
   }
+}
+
+cudaError_t launch_scan(const uint32_t *deg, uint32_t n, uint64_t m, const uint64_t *row_ptr, uint64_t *col_ptr,
+                        unsigned long long *cursor, unsigned long long *state, uint32_t ntiles, uint32_t *meta,
+                        uint32_t *status, cudaStream_t s) {
+  k_scan<<<ntiles, kScanThreads, 0, s>>>(deg, n, m, row_ptr, col_ptr, cursor, state, meta, status);
+  return cudaGetLastError();
 }
 
 __global__ void k_hdv_start(const uint32_t *__restrict__ meta, const uint32_t *__restrict__ hdv_ids,

@@ -189,6 +189,103 @@ __global__ void k_vals(uint64_t m, uint64_t key, float lo, float hi, float *vals
   }
 }
 
+// ---- batched Zipf-degree matrices -------------------------------------------
+
+// Zipf(s) on {1..N} by rejection-inversion (Hormann, Derflinger 1996) with
+// H(x) = (x^(1-s) - 1) / (1-s), the integral of x^-s (s != 1).
+struct ZipfRI {
+  double s, N, hx1, hN, sp;
+  __device__ double H(double x) const { return (pow(x, 1.0 - s) - 1.0) / (1.0 - s); }
+  __device__ double Hinv(double y) const { return pow(1.0 + y * (1.0 - s), 1.0 / (1.0 - s)); }
+  __device__ double h(double x) const { return pow(x, -s); }
+  __device__ void init(double s_, double N_) {
+    s = s_;
+    N = N_;
+    hx1 = H(1.5) - 1.0;
+    hN = H(N + 0.5);
+    sp = 2.0 - Hinv(H(2.5) - h(2.0));
+  }
+  __device__ uint32_t sample(Stream &rs) const {
+    for (int it = 0; it < 1000; ++it) {
+      const double u = hN + rs.uniform() * (hx1 - hN);
+      const double x = Hinv(u);
+      double k = floor(x + 0.5);
+      if (k < 1.0) k = 1.0;
+      if (k > N) k = N;
+      if (k - x <= sp || u >= H(k + 0.5) - h(k)) return (uint32_t)k;
+    }
+    return 1u;
+  }
+};
+
+__device__ inline uint32_t find_graph(const unsigned long long *off, uint32_t ng, uint64_t x) {
+  uint32_t lo = 0, hi = ng;  // largest g with off[g] <= x
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) / 2;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Out-degree of every row of every matrix: round(Z * mean / mu), clamped to [1, n].
+__global__ void k_zipf_degrees(uint32_t ng, const unsigned long long *voff, const uint32_t *nv, const double *scale,
+                               double s_out, uint64_t key, unsigned long long *deg) {
+  const uint64_t total = voff[ng];
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total; x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = find_graph(voff, ng, x);
+    const uint64_t r = x - voff[g];
+    ZipfRI z;
+    z.init(s_out, (double)nv[g]);
+    Stream rs{fold(fold(key, g), r), 0};
+    double d = floor((double)z.sample(rs) * scale[g] + 0.5);
+    if (d < 1.0) d = 1.0;
+    if (d > (double)nv[g]) d = (double)nv[g];
+    deg[x] = (unsigned long long)d;
+  }
+}
+
+// Row pointers of every matrix inside one buffer: matrix g's n_g + 1 entries
+// start at voff[g] + g; ex is the exclusive prefix of the union degrees.
+__global__ void k_batch_rowptr(uint32_t ng, const unsigned long long *voff, const unsigned long long *ex,
+                               unsigned long long *rp) {
+  const uint64_t total = voff[ng];
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < total + ng;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    // x indexes the row-pointer buffer: graph g owns [voff[g] + g, voff[g+1] + g + 1)
+    uint32_t lo = 0, hi = ng;
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) / 2;
+      if (voff[mid] + mid <= x) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t g = lo;
+    const uint64_t i = x - (voff[g] + g);  // 0..n_g
+    rp[x] = ex[voff[g] + i] - ex[voff[g]];
+  }
+}
+
+// Destinations: Zipf(s_in) rank over a seeded Feistel permutation of [0, n_g).
+__global__ void k_zipf_dst(uint32_t ng, const unsigned long long *eoff, const uint32_t *nv, double s_in, uint64_t key,
+                           uint64_t pkey, uint32_t *col) {
+  const uint64_t total = eoff[ng];
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = find_graph(eoff, ng, e);
+    const uint64_t le = e - eoff[g];
+    const uint32_t n = nv[g];
+    ZipfRI z;
+    z.init(s_in, (double)n);
+    Stream rs{fold(fold(key, g), le), 0};
+    const uint32_t rank = z.sample(rs) - 1u;
+    uint32_t bits = 2;
+    while (bits < 32 && (1u << bits) < n) ++bits;
+    if (bits % 2) ++bits;
+    const uint64_t gk = fold(pkey, g);
+    const uint64_t keys[4] = {fold(gk, 0), fold(gk, 1), fold(gk, 2), fold(gk, 3)};
+    col[e] = (uint32_t)feistel(rank, bits / 2, keys, n);
+  }
+}
+
 inline uint32_t grid_for(uint64_t n, uint32_t threads) {
   uint64_t g = (n + threads - 1) / threads;
   if (g > 65535ull * 8) g = 65535ull * 8;
@@ -267,6 +364,27 @@ int gtgen_histogram(const uint32_t *col_idx, uint64_t m, uint32_t *counts, void 
 
 int gtgen_vals(uint64_t m, uint64_t key, float lo, float hi, float *vals, void *stream) {
   k_vals<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(m, key, lo, hi, vals);
+  return (int)cudaGetLastError();
+}
+
+// Batched Zipf matrices (see k_zipf_degrees / k_zipf_dst): voff/eoff are the
+// union vertex / edge offsets (ng + 1 entries), nv the sizes, scale[g] =
+// mean_g / mu_g.  deg: [voff[ng]] out-degrees (u64).
+int gtgen_zipf_degrees(uint32_t ng, const unsigned long long *voff, const uint32_t *nv, const double *scale,
+                       double s_out, uint64_t key, unsigned long long *deg, void *stream) {
+  k_zipf_degrees<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(ng, voff, nv, scale, s_out, key, deg);
+  return (int)cudaGetLastError();
+}
+
+int gtgen_batch_rowptr(uint32_t ng, const unsigned long long *voff, const unsigned long long *ex,
+                       unsigned long long *rp, void *stream) {
+  k_batch_rowptr<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(ng, voff, ex, rp);
+  return (int)cudaGetLastError();
+}
+
+int gtgen_zipf_dst(uint32_t ng, const unsigned long long *eoff, const uint32_t *nv, double s_in, uint64_t key,
+                   uint64_t pkey, uint32_t *col, void *stream) {
+  k_zipf_dst<<<152 * 32, 256, 0, (cudaStream_t)stream>>>(ng, eoff, nv, s_in, key, pkey, col);
   return (int)cudaGetLastError();
 }
 

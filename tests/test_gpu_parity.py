@@ -53,7 +53,7 @@ def assert_same(got, exp):
 def config(**kw):
     from paper_2501_06872_gb300 import binding
     base = dict(hdv_k=0, table_log2=0, block_threads=256, ctas_per_sm=4, warp_edges=256, stage_edges=0,
-                sample_permille=10, flags=1, method=0, reserved=0, seed=7)
+                sample_permille=10, flags=1, method=0, radix_tile=0, seed=7)
     base.update(kw)
     if base["hdv_k"] and not base["table_log2"]:
         base["table_log2"] = max(1, (2 * base["hdv_k"] - 1).bit_length())
@@ -68,6 +68,7 @@ CONFIGS = {
     "noagg_staged": dict(hdv_k=16, flags=0, stage_edges=128),
     "big_blocks": dict(hdv_k=128, block_threads=1024, ctas_per_sm=1, warp_edges=64),
     "radix": dict(method=1),
+    "radix2048": dict(method=1, radix_tile=2048, ctas_per_sm=6),
 }
 
 
@@ -108,7 +109,7 @@ def test_random_graphs_all_configs(name, seed):
 def test_rmat_numpy_scale14(order):
     n, rp, ci, vv = inputs.rmat_csr(14, 16, seed=3, order=order, weighted=True)
     exp = oracle.transpose(rp, ci, vv)
-    for name in ["atomic", "hdv512_staged", "big_blocks", "radix"]:
+    for name in ["atomic", "hdv512_staged", "big_blocks", "radix", "radix2048"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
     assert_same(gpu_transpose(rp, ci, vv), exp)  # default configuration
 
