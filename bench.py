@@ -184,6 +184,7 @@ def run_reference(args, rank, world):
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
     torch.cuda.set_device(0)
     n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=SEED, order=order, weighted=weighted)
+    m_full = ci.numel()
     target = min(args.ref_sample_edges, ci.numel())
     R = int(torch.searchsorted(rp, torch.tensor([target], device=rp.device)).item())
     R = max(1, min(R, n))
@@ -208,10 +209,28 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": workload_config(args.workload, n, int(mS), weighted),
+            "data": "synthetic", "config": workload_config(args.workload, n, m_full, weighted),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def aggregate_ranks(ms_step, m, world, device=None):
+    """Max over ranks of the per-step time (every rank transposes its own
+    replica of m edges); the whole-job value is the edges of all ranks over
+    that time.  No collective touches the data path."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms_step)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    return ms_step, m * world / (ms_step * 1e-3)
+
+
+def replica_seed(rank):
+    """Each replica transposes its own seeded graph of the same shape."""
+    return SEED + rank
 
 
 def workload_config(name, n, m, weighted):
@@ -348,7 +367,7 @@ def main():
     from paper_2501_06872_gb300.inputs import gpu as ggen
 
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
-    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=SEED + rank, order=order, weighted=weighted)
+    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=replica_seed(rank), order=order, weighted=weighted)
     m = ci.numel()
     cfg = binding.default_config(n, m)
     if args.config:
@@ -382,12 +401,7 @@ def main():
     timing = plan.timing()
     stats = plan.stats()
     plan.enable_timing(False)
-    ms_step = ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = m * world / (ms_step * 1e-3)
+    ms_step, value = aggregate_ranks(ms / args.steps, m, world, device="cuda")
 
     peak, peak_kind = load_peaks()
     method = plan.config().method

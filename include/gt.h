@@ -220,6 +220,99 @@ gt_status gt_batch_plan_status(gt_batch_plan plan);
 gt_status gt_batch_plan_info(gt_batch_plan plan, gt_batch_info *info);
 void gt_batch_plan_destroy(gt_batch_plan plan);
 
+/* ---- Configuration search: features, grid, analytic model, autotuner, -----
+ * ---- learned selector.  None of it changes the output bytes. ------------- */
+
+#define GT_N_FEATURES 41  /* graph features of gt_graph_features            */
+#define GT_TUNE_GRID 12   /* configurations of the search grid              */
+#define GT_SEL_HIDDEN 64  /* width of the selector's two hidden layers      */
+
+/* Graph features (device f32[GT_N_FEATURES] written on `stream`), computed by
+ * kernels from row_ptr and a seeded sample of col_idx:
+ *   [0..31]  fraction of vertices per out-degree bin: bin 0 = degree 0, bin b
+ *            (1..31) = degree in [2^(b-1), 2^b), bin 31 also holds larger
+ *   [32]     log2(n)/32    [33] log2(m+1)/32    [34] log2(max out-degree+1)/32
+ *   [35]     fraction of edges leaving the ceil(n/100) vertices of highest
+ *            out-degree, estimated from the log2 bins (per-bin vertex counts
+ *            and edge sums, proportional share of the boundary bin)
+ *   [36]     coverage (Sec. IV-B): share of ns samples of col_idx that fall on
+ *            the 512 most frequent sampled destinations; ns = clamp(ceil(n/100),
+ *            1024, 2^20), sample j at floor(r_j m / 2^64), r_j = SplitMix64
+ *            output j (j = 1..ns: mix(seed + j*0x9E3779B97F4A7C15))
+ *   [37]     log2(max sample frequency * m / ns + 1)/32 (estimated max in-degree)
+ *   [38],[39] locality over 4096 sampled rows u_j = floor(r'_j n / 2^64)
+ *            (r' from seed ^ 0x4C4F43), first 32 neighbour pairs (a, b) of each
+ *            row with >= 2 edges: mean log2(|a-b|+1)/32, and the fraction of
+ *            pairs with a/32 == b/32 (same 128-byte line of a u32 array)
+ *   [40]     has_vals
+ * Allocates its small workspace stream-ordered (cudaMallocAsync). */
+gt_status gt_graph_features(uint32_t n_vertices, uint64_t n_edges, int has_vals, const uint64_t *row_ptr,
+                            const uint32_t *col_idx, uint64_t seed, float *features, void *stream);
+
+/* Grid point `index` (0..GT_TUNE_GRID-1) for a graph of this size:
+ *   0 Atomic GT (hdv_k = 0, Algorithm 1)   1 same without warp aggregation
+ *   2 HLH k=64   3 HLH k=512 (Eq. 1)   4 k=512, 1024-edge bulk-copy stages
+ *   5 k=2048   6 k=512, 1024-edge partitions   7 k=512, 512 threads x 2 CTAs/SM
+ *   8 radix 4096-edge tiles, 2 CTAs/SM   9 radix 4096, 4/SM   10 radix 2048, 4/SM
+ *   11 radix 2048, 8/SM
+ * An HDV count above n/2 becomes 0 (the point then equals Atomic GT). */
+gt_status gt_tune_grid_config(uint32_t index, uint32_t n_vertices, uint64_t n_edges, gt_config *cfg);
+
+/* Analytic choice (the Sec. IV-B cost model, Eqs. 2-3, with GB300 rates and a
+ * streaming term for the radix method) from host copies of the features:
+ * writes the grid index (0, 3 or 9). */
+gt_status gt_tune_analytic(const float *features, uint32_t n_vertices, uint64_t n_edges, uint32_t *index);
+
+typedef struct gt_selector_s *gt_selector;
+
+/* Learned selector: an MLP GT_N_FEATURES -> 64 -> 64 -> GT_TUNE_GRID (ReLU),
+ * f32, on the device.  Parameter vector (gt_selector_param_count floats):
+ * mu[F], sd[F] (input standardisation, x' = (x - mu) / sd, not trained),
+ * W1[64][F], b1[64], W2[64][64], b2[64], W3[K][64], b3[K].  Output i is a
+ * score for grid point i; the learned mode takes the smallest.
+ * host_params == NULL: mu = 0, sd = 1, weights uniform in +-sqrt(6/fan_in)
+ * from SplitMix64(seed), biases 0. */
+uint64_t gt_selector_param_count(void);
+gt_status gt_selector_create(gt_selector *sel, const float *host_params, uint64_t seed);
+gt_status gt_selector_get_params(gt_selector sel, float *host_params);
+/* Replaces all parameters (every sd must be > 0) and resets Adam's state. */
+gt_status gt_selector_set_params(gt_selector sel, const float *host_params);
+/* scores (device f32[batch][GT_TUNE_GRID]) for features (device f32[batch][F]). */
+gt_status gt_selector_forward(gt_selector sel, const float *features, uint32_t batch, float *scores,
+                              void *stream);
+/* Forward + backward of the masked mean squared error
+ *   L = sum_{b,i} M[b][i] (y[b][i] - T[b][i])^2 / max(1, sum M)
+ * into the selector's gradient buffer; loss (device f32[1]) and grads (device
+ * f32[param_count], mu/sd entries 0) are optional copies. */
+gt_status gt_selector_backward(gt_selector sel, const float *features, const float *target, const float *mask,
+                               uint32_t batch, float *loss, float *grads, void *stream);
+/* One Adam step (bias-corrected) with the last gradients on W and b. */
+gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float beta2, float eps, void *stream);
+void gt_selector_destroy(gt_selector sel);
+
+typedef struct gt_tune_entry {
+    gt_config cfg;    /* grid point                                           */
+    float ms;         /* exhaustive: median device time of the timed calls; -1 if not run */
+    float score;      /* learned: the selector's score                        */
+    int32_t status;   /* gt_status of this point's run                        */
+} gt_tune_entry;
+
+#define GT_TUNE_ANALYTIC 0    /* features + gt_tune_analytic                  */
+#define GT_TUNE_EXHAUSTIVE 1  /* time every grid point (1 warm-up + reps calls) */
+#define GT_TUNE_LEARNED 2     /* features + selector, smallest score           */
+
+/* Chooses a configuration for the plan's graph and installs it
+ * (gt_plan_set_config).  The exhaustive mode runs real transpositions into
+ * the given outputs (which then hold the CSC).  table: optional host array of
+ * GT_TUNE_GRID entries; chosen: optional grid index.  Synchronous. */
+gt_status gt_plan_tune(gt_plan plan, int mode, gt_selector sel, const uint64_t *row_ptr, const uint32_t *col_idx,
+                       const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, uint32_t reps,
+                       gt_tune_entry *table, uint32_t *chosen, void *stream);
+
+/* Sizes the plan was created for. */
+uint32_t gt_plan_vertices(gt_plan plan);
+uint64_t gt_plan_edges(gt_plan plan);
+
 /* Synchronises the plan's last stream and returns (then clears) the latched
  * device status. */
 gt_status gt_plan_status(gt_plan plan);

@@ -71,6 +71,10 @@ class GraphDesc(ctypes.Structure):
                 ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p), ("vals_out", ctypes.c_void_p)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("cfg", Config), ("ms", ctypes.c_float), ("score", ctypes.c_float), ("status", ctypes.c_int32)]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_uint32), ("sub_batches", ctypes.c_uint32), ("passes_max", ctypes.c_uint32),
                 ("kernel_launches", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
@@ -87,7 +91,15 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_plan_enable_timing", "gt_plan_timing", "gt_plan_workspace_bytes", "gt_plan_destroy",
            "gt_status_string", "gt_last_cuda_error", "gt_version", "gt_transpose_noalloc",
            "gt_batch_plan_create", "gt_transpose_batched", "gt_batch_plan_status", "gt_batch_plan_info",
-           "gt_batch_plan_destroy"]
+           "gt_batch_plan_destroy", "gt_graph_features", "gt_tune_grid_config", "gt_tune_analytic",
+           "gt_selector_param_count", "gt_selector_create", "gt_selector_get_params", "gt_selector_set_params",
+           "gt_selector_forward", "gt_selector_backward", "gt_selector_adam_step", "gt_selector_destroy",
+           "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges"]
+
+N_FEATURES = 41
+TUNE_GRID = 12
+SEL_HIDDEN = 64
+TUNE_ANALYTIC, TUNE_EXHAUSTIVE, TUNE_LEARNED = 0, 1, 2
 
 
 def load():
@@ -120,6 +132,29 @@ def load():
     lib.gt_batch_plan_destroy.argtypes = [P]
     lib.gt_batch_plan_destroy.restype = None
     for f in ["gt_batch_plan_create", "gt_transpose_batched", "gt_batch_plan_status", "gt_batch_plan_info"]:
+        getattr(lib, f).restype = ctypes.c_int
+    F = ctypes.c_float
+    lib.gt_graph_features.argtypes = [u32, u64, ctypes.c_int, P, P, u64, P, P]
+    lib.gt_tune_grid_config.argtypes = [u32, u32, u64, ctypes.POINTER(Config)]
+    lib.gt_tune_analytic.argtypes = [P, u32, u64, ctypes.POINTER(u32)]
+    lib.gt_selector_param_count.restype = u64
+    lib.gt_selector_create.argtypes = [ctypes.POINTER(P), P, u64]
+    lib.gt_selector_get_params.argtypes = [P, P]
+    lib.gt_selector_set_params.argtypes = [P, P]
+    lib.gt_selector_forward.argtypes = [P, P, u32, P, P]
+    lib.gt_selector_backward.argtypes = [P, P, P, P, u32, P, P, P]
+    lib.gt_selector_adam_step.argtypes = [P, F, F, F, F, P]
+    lib.gt_selector_destroy.argtypes = [P]
+    lib.gt_selector_destroy.restype = None
+    lib.gt_plan_tune.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, u32, ctypes.POINTER(TuneEntry),
+                                 ctypes.POINTER(u32), P]
+    lib.gt_plan_vertices.argtypes = [P]
+    lib.gt_plan_vertices.restype = u32
+    lib.gt_plan_edges.argtypes = [P]
+    lib.gt_plan_edges.restype = u64
+    for f in ["gt_graph_features", "gt_tune_grid_config", "gt_tune_analytic", "gt_selector_create",
+              "gt_selector_get_params", "gt_selector_set_params", "gt_selector_forward", "gt_selector_backward",
+              "gt_selector_adam_step", "gt_plan_tune"]:
         getattr(lib, f).restype = ctypes.c_int
     lib.gt_plan_enable_timing.argtypes = [P, ctypes.c_int]
     lib.gt_plan_timing.argtypes = [P, ctypes.POINTER(Timing)]
@@ -238,6 +273,18 @@ class Plan:
     def workspace_bytes(self) -> int:
         return int(self._lib.gt_plan_workspace_bytes(self._h))
 
+    def tune(self, mode, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, selector=None, reps=3, stream=None):
+        """gt_plan_tune: installs the chosen grid point; returns (index, table)."""
+        table = (TuneEntry * TUNE_GRID)()
+        chosen = ctypes.c_uint32()
+        rc = self._lib.gt_plan_tune(self._h, int(mode), selector.handle if selector is not None else None,
+                                    _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr), _ptr(row_idx),
+                                    _ptr(vals_out), int(reps), table, ctypes.byref(chosen), _stream(stream))
+        _check(rc, "gt_plan_tune")
+        rows = [{"cfg": t.cfg.as_dict(), "ms": float(t.ms), "score": float(t.score), "status": int(t.status)}
+                for t in table]
+        return int(chosen.value), rows
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gt_plan_destroy(self._h)
@@ -293,6 +340,99 @@ class BatchPlan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gt_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_config(index: int, n: int, m: int) -> Config:
+    c = Config()
+    _check(load().gt_tune_grid_config(int(index), int(n), int(m), ctypes.byref(c)), "gt_tune_grid_config")
+    return c
+
+
+def graph_features(row_ptr, col_idx, weighted: bool, seed: int = 0x5EED0001, out=None, stream=None):
+    """gt_graph_features into a device f32 tensor of N_FEATURES (allocated if out is None)."""
+    import torch
+    n = row_ptr.numel() - 1
+    m = col_idx.numel()
+    if out is None:
+        out = torch.empty(N_FEATURES, dtype=torch.float32, device=row_ptr.device)
+    _check(load().gt_graph_features(n, m, int(weighted), _ptr(row_ptr), _ptr(col_idx), int(seed), _ptr(out),
+                                    _stream(stream)), "gt_graph_features")
+    return out
+
+
+def analytic_index(features_host, n: int, m: int) -> int:
+    """gt_tune_analytic on a host float32 numpy array of N_FEATURES."""
+    import numpy as np
+    f = np.ascontiguousarray(features_host, dtype=np.float32)
+    idx = ctypes.c_uint32()
+    _check(load().gt_tune_analytic(ctypes.c_void_p(f.ctypes.data), int(n), int(m), ctypes.byref(idx)),
+           "gt_tune_analytic")
+    return int(idx.value)
+
+
+class Selector:
+    """Owns a gt_selector (MLP on the device; forward/backward/Adam in libgt)."""
+
+    def __init__(self, params=None, seed: int = 1):
+        import numpy as np
+        lib = load()
+        self._lib = lib
+        self.n_params = int(lib.gt_selector_param_count())
+        h = ctypes.c_void_p()
+        arr = None
+        if params is not None:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            if arr.size != self.n_params:
+                raise ValueError(f"expected {self.n_params} parameters, got {arr.size}")
+        _check(lib.gt_selector_create(ctypes.byref(h), None if arr is None else ctypes.c_void_p(arr.ctypes.data),
+                                      int(seed)), "gt_selector_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self._lib.gt_selector_get_params(self._h, ctypes.c_void_p(out.ctypes.data)), "gt_selector_get_params")
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        if arr.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {arr.size}")
+        _check(self._lib.gt_selector_set_params(self._h, ctypes.c_void_p(arr.ctypes.data)), "gt_selector_set_params")
+
+    def forward(self, features, out=None, stream=None):
+        import torch
+        b = features.shape[0]
+        if out is None:
+            out = torch.empty(b, TUNE_GRID, dtype=torch.float32, device=features.device)
+        _check(self._lib.gt_selector_forward(self._h, _ptr(features), b, _ptr(out), _stream(stream)),
+               "gt_selector_forward")
+        return out
+
+    def backward(self, features, target, mask, loss=None, grads=None, stream=None):
+        b = features.shape[0]
+        _check(self._lib.gt_selector_backward(self._h, _ptr(features), _ptr(target), _ptr(mask), b, _ptr(loss),
+                                              _ptr(grads), _stream(stream)), "gt_selector_backward")
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(self._lib.gt_selector_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps),
+                                               _stream(stream)), "gt_selector_adam_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gt_selector_destroy(self._h)
             self._h = None
 
     def __del__(self):

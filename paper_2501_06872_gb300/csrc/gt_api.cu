@@ -492,6 +492,10 @@ gt_status gt_plan_stats(gt_plan plan, gt_stats *stats) {
 
 uint64_t gt_plan_workspace_bytes(gt_plan plan) { return plan ? plan->ws_bytes : 0; }
 
+uint32_t gt_plan_vertices(gt_plan plan) { return plan ? plan->w.n : 0; }
+
+uint64_t gt_plan_edges(gt_plan plan) { return plan ? plan->w.m : 0; }
+
 gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
                             uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
   if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;

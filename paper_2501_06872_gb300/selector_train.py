@@ -1,0 +1,222 @@
+"""Training of the learned configuration selector on the library's own timings.
+
+    python -m paper_2501_06872_gb300.selector_train --out DIR [--graphs 256 --train 192]
+
+1. Dataset: `graphs` seeded R-MAT graphs with a ~ U[0.25, 0.70],
+   b = c = (1 - a - d) / 2, d = 0.05, scale ~ U{18..26}, edge factor ~
+   U{8..32}, vertex order degree-sorted or seeded-random, weighted or not.
+   For each: the features (gt_graph_features) and the exhaustive autotuner's
+   table (gt_plan_tune, every grid point timed with CUDA events, median of 3),
+   plus the analytic model's and the default configuration's grid points.
+2. Training: targets are log-regrets ln(t_i / min_j t_j) per grid point; the
+   network (gt_selector, GPU forward/backward/Adam) fits them with a masked
+   MSE, full batch, on the first `train` graphs.
+3. Evaluation on the held-out graphs: time of the selected point over the
+   best point (regret), for the learned, analytic and default choices.
+Writes dataset.npz, selector_params.f32 and selector_report.json into --out.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+PARAMS_FILE = os.path.join(PKG, "selector_params.f32")
+DATASET_FILE = os.path.join(PKG, "selector_dataset.npz")
+D_PARAM = 0.05
+
+
+def graph_spec(i: int, seed: int = 0x5EED0005):
+    rng = np.random.default_rng([seed, i])
+    a = float(rng.uniform(0.25, 0.70))
+    b = (1.0 - a - D_PARAM) / 2.0
+    return {"a": a, "b": b, "c": b, "scale": int(rng.integers(18, 27)), "edge_factor": int(rng.integers(8, 33)),
+            "order": "degree" if rng.random() < 0.5 else "random", "weighted": bool(rng.random() < 0.5),
+            "seed": int(seed + 1000 + i)}
+
+
+def _norm(c: dict) -> tuple:
+    if c["method"] == 1:
+        return (1, c["radix_tile"] or 4096, c["ctas_per_sm"])
+    return (0, c["hdv_k"], c["table_log2"], c["block_threads"], c["ctas_per_sm"], c["warp_edges"],
+            c["stage_edges"], c["flags"])
+
+
+def default_index(n: int, m: int) -> int:
+    """Grid point equal to gt_default_config for this size (-1 if none)."""
+    from . import binding
+    d = _norm(binding.default_config(n, m).as_dict())
+    for i in range(binding.TUNE_GRID):
+        if _norm(binding.grid_config(i, n, m).as_dict()) == d:
+            return i
+    return -1
+
+
+def build_dataset(count: int, reps: int = 3, log=print):
+    import torch
+    from . import binding
+    from .inputs import gpu as ggen
+    feats, times, meta = [], [], []
+    for i in range(count):
+        sp = graph_spec(i)
+        t0 = time.time()
+        n, rp, ci, vv = ggen.graph(sp["scale"], sp["edge_factor"], "rmat", sp["a"], sp["b"], sp["c"], sp["seed"],
+                                   sp["order"], sp["weighted"])
+        m = ci.numel()
+        cp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        ri = torch.empty(m, dtype=torch.int32, device="cuda")
+        vo = torch.empty(m, dtype=torch.float32, device="cuda") if vv is not None else None
+        f = binding.graph_features(rp, ci, sp["weighted"]).cpu().numpy()
+        plan = binding.Plan(n, m, sp["weighted"])
+        _, table = plan.tune(binding.TUNE_EXHAUSTIVE, rp, ci, vv, cp, ri, vo, reps=reps)
+        plan.close()
+        ms = np.array([t["ms"] for t in table], dtype=np.float64)
+        an = binding.analytic_index(f, n, m)
+        di = default_index(n, m)
+        feats.append(f)
+        times.append(ms)
+        meta.append({**sp, "n": n, "m": m, "analytic": an, "default": di})
+        log(f"[{i + 1}/{count}] scale {sp['scale']} ef {sp['edge_factor']} a {sp['a']:.2f} {sp['order']} "
+            f"w{int(sp['weighted'])}: best {int(np.argmin(np.where(ms > 0, ms, np.inf)))} "
+            f"{ms[ms > 0].min():.3f} ms, analytic {an}, default {di} ({time.time() - t0:.1f} s)")
+        del rp, ci, vv, cp, ri, vo
+        torch.cuda.empty_cache()
+    return np.stack(feats), np.stack(times), meta
+
+
+def targets(times: np.ndarray):
+    valid = times > 0
+    best = np.where(valid, times, np.inf).min(axis=1, keepdims=True)
+    y = np.where(valid, np.log(np.where(valid, times, 1.0) / best), 0.0)
+    return y.astype(np.float32), valid.astype(np.float32)
+
+
+def standardise(x: np.ndarray):
+    mu = x.mean(axis=0)
+    sd = x.std(axis=0) + 1e-3
+    return mu.astype(np.float32), sd.astype(np.float32)
+
+
+def train(feats, times, steps=4000, lr=3e-3, seed=7, val=None, every=250, log=print):
+    """Full-batch Adam on the masked MSE of log-regrets.  With val = (features,
+    times), keeps the checkpoint (every `every` steps) of lowest mean
+    validation regret."""
+    import torch
+    from . import binding
+    sel = binding.Selector(seed=seed)
+    p = sel.params()
+    mu, sd = standardise(feats)
+    F = binding.N_FEATURES
+    p[:F] = mu
+    p[F:2 * F] = sd
+    sel.set_params(p)
+    y, mask = targets(times)
+    X = torch.from_numpy(feats.astype(np.float32)).cuda()
+    T = torch.from_numpy(y).cuda()
+    M = torch.from_numpy(mask).cuda()
+    Xv = None if val is None else torch.from_numpy(val[0].astype(np.float32)).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    best = (np.inf, 0, sel.params())
+    for it in range(1, steps + 1):
+        sel.backward(X, T, M, loss=loss)
+        sel.adam_step(lr=lr)
+        if it % every == 0 or it == steps:
+            torch.cuda.synchronize()
+            rec = {"step": it, "loss": float(loss.item())}
+            if Xv is not None:
+                idx = sel.forward(Xv).cpu().numpy().argmin(axis=1)
+                rec["val_regret"] = float(regrets(val[1], idx).mean())
+                if rec["val_regret"] < best[0]:
+                    best = (rec["val_regret"], it, sel.params())
+            hist.append(rec)
+            log(json.dumps(rec))
+    params = sel.params() if Xv is None else best[2]
+    sel.close()
+    return params, hist, best[1] if Xv is not None else steps
+
+
+def picks(params, feats):
+    import torch
+    from . import binding
+    sel = binding.Selector(params)
+    s = sel.forward(torch.from_numpy(feats.astype(np.float32)).cuda()).cpu().numpy()
+    sel.close()
+    return s.argmin(axis=1), s
+
+
+def regrets(times, idx):
+    best = np.where(times > 0, times, np.inf).min(axis=1)
+    chosen = times[np.arange(len(idx)), idx]
+    chosen = np.where(chosen > 0, chosen, np.inf)
+    return chosen / best
+
+
+def summary(r):
+    r = np.asarray(r, dtype=np.float64)
+    return {"mean": float(r.mean()), "geomean": float(np.exp(np.log(r).mean())), "max": float(r.max()),
+            "optimal_share": float((r <= 1.0 + 1e-9).mean())}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--graphs", type=int, default=256)
+    ap.add_argument("--train", type=int, default=192)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--val", type=int, default=32, help="training graphs held out for checkpoint choice")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--dataset", default=None, help="reuse a dataset.npz instead of timing")
+    args = ap.parse_args()
+    import __graft_entry__
+    __graft_entry__.build()
+    os.makedirs(args.out, exist_ok=True)
+    logf = open(os.path.join(args.out, "train.log"), "a")
+
+    def log(msg):
+        print(msg, flush=True)
+        logf.write(msg + "\n")
+        logf.flush()
+    if args.dataset:
+        d = np.load(args.dataset, allow_pickle=False)
+        feats, times = d["features"], d["times"]
+        meta = json.loads(str(d["meta"]))
+    else:
+        feats, times, meta = build_dataset(args.graphs, args.reps, log)
+        np.savez(os.path.join(args.out, "dataset.npz"), features=feats, times=times, meta=json.dumps(meta))
+    tr = slice(0, args.train)
+    te = slice(args.train, len(feats))
+    fit = slice(0, args.train - args.val)
+    va = slice(args.train - args.val, args.train)
+    params, hist, chosen_step = train(feats[fit], times[fit], steps=args.steps,
+                                      val=(feats[va], times[va]) if args.val else None, log=log)
+    params.astype("<f4").tofile(os.path.join(args.out, "selector_params.f32"))
+    idx_te, _ = picks(params, feats[te])
+    idx_tr, _ = picks(params, feats[tr])
+    an = np.array([m["analytic"] for m in meta])
+    de = np.array([m["default"] for m in meta])
+    report = {
+        "graphs": len(feats), "n_train": args.train, "n_test": len(feats) - args.train, "steps": args.steps,
+        "n_val": args.val, "chosen_step": chosen_step, "loss": hist,
+        "test": {"learned": summary(regrets(times[te], idx_te)),
+                 "analytic": summary(regrets(times[te], an[te])),
+                 "default": summary(regrets(times[te], de[te])),
+                 "time_learned_ms": float(times[te][np.arange(len(idx_te)), idx_te].sum()),
+                 "time_analytic_ms": float(times[te][np.arange(len(idx_te)), an[te]].sum()),
+                 "time_default_ms": float(times[te][np.arange(len(idx_te)), de[te]].sum()),
+                 "time_best_ms": float(np.where(times[te] > 0, times[te], np.inf).min(axis=1).sum())},
+        "train_fit": {"learned": summary(regrets(times[tr], idx_tr))},
+        "grid_best_counts": np.bincount(np.where(times > 0, times, np.inf).argmin(axis=1),
+                                        minlength=times.shape[1]).tolist(),
+    }
+    with open(os.path.join(args.out, "selector_report.json"), "w") as fh:
+        json.dump(report, fh, indent=1)
+    log(json.dumps(report["test"]))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+"""Pins of the selector oracle (features, MLP, Adam) -- CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import selector as so
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_splitmix64_published_outputs():
+    vals = [int(l, 16) for l in open(os.path.join(HERE, "golden", "splitmix64_seed0.txt")) if l.startswith("0x")]
+    assert so.stream(0, 3) == vals
+
+
+def test_scaled_is_floor_of_product():
+    for r in [0, 1, (1 << 64) - 1, 0x8000000000000000, 12345678901234567890]:
+        for b in [1, 7, 1000, (1 << 32) + 3]:
+            assert so.scaled(r, b) == (r * b) // (1 << 64)
+            assert 0 <= so.scaled(r, b) < b
+
+
+def star_in(n):
+    # every vertex u >= 1 has one edge u -> 0
+    row_ptr = np.concatenate([[0, 0], np.arange(1, n)]).astype(np.int64)
+    col_idx = np.zeros(n - 1, dtype=np.int64)
+    return row_ptr, col_idx
+
+
+def test_features_in_star_closed_forms():
+    n = 1000
+    rp, ci = star_in(n)
+    m = n - 1
+    f = so.features(n, m, rp, ci, False, 5).astype(np.float64)
+    assert f[0] == pytest.approx(1 / n) and f[1] == pytest.approx((n - 1) / n)
+    assert f[2:32].sum() == 0
+    assert f[32] == pytest.approx(math.log2(n) / 32)
+    assert f[33] == pytest.approx(math.log2(m + 1) / 32)
+    assert f[34] == pytest.approx(1 / 32)
+    # 10 vertices of the 999 in bin 1 (one edge each): 10 edges of 999
+    assert f[35] == pytest.approx(10 / m, rel=1e-6)
+    assert f[36] == 1.0  # every sample lands on vertex 0
+    assert f[37] == pytest.approx(math.log2(m + 1) / 32, rel=1e-6)
+    assert f[38] == 0 and f[39] == 0  # no row has two edges
+    assert f[40] == 0
+    assert so.features(n, m, rp, ci, True, 5)[40] == 1
+
+
+def test_features_consecutive_neighbours():
+    # u -> u+1, u+2 while u+2 < n: every neighbour pair differs by one
+    n = 5000
+    rows = [[u + 1, u + 2] if u + 2 < n else [] for u in range(n)]
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.array([v for r in rows for v in r], dtype=np.int64)
+    f = so.features(n, len(ci), rp, ci, False, 9)
+    assert f[38] == pytest.approx(1 / 32)
+    assert 0.9 < f[39] < 1.0
+    assert f[2] == pytest.approx((n - 2) / n)  # degree 2 -> bin 2
+
+
+def test_features_top_fraction_at_bin_edge():
+    # 200 vertices: two of degree 100 (bin 7), 198 of degree 1 -> the top
+    # ceil(200/100) = 2 vertices hold exactly 200 of 398 edges
+    n = 200
+    deg = np.array([100, 100] + [1] * 198)
+    rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)
+    ci = np.arange(rp[-1]) % n
+    f = so.features(n, int(rp[-1]), rp, ci, False, 3)
+    assert f[35] == pytest.approx(200 / 398, rel=1e-7)
+    assert f[7] == pytest.approx(2 / n) and f[1] == pytest.approx(198 / n)
+
+
+def test_coverage_matches_counter_brute_force():
+    from collections import Counter
+    rng = np.random.default_rng(4)
+    n, m = 3000, 40000
+    ci = (rng.zipf(1.6, size=m) % n).astype(np.int64)
+    rp = np.sort(rng.integers(0, m + 1, size=n + 1))
+    rp[0], rp[-1] = 0, m
+    f = so.features(n, m, rp, ci, False, 11)
+    ns = so.sample_count(n, m)
+    c = Counter(int(ci[so.scaled(r, m)]) for r in so.stream(11, ns))
+    top = sum(v for _, v in c.most_common(512))
+    assert f[36] == pytest.approx(top / ns, rel=1e-6)
+    assert f[37] == pytest.approx(math.log2(max(c.values()) * m / ns + 1) / 32, rel=1e-6)
+
+
+def test_empty_graph_features():
+    f = so.features(10, 0, np.zeros(11, dtype=np.int64), np.zeros(0, dtype=np.int64), False, 1)
+    assert f[0] == 1.0 and f[33] == 0 and f[35] == 0 and f[36] == 0 and f[38] == 0
+
+
+def small_net(seed, F=5, H=6, K=3, B=9):
+    rng = np.random.default_rng(seed)
+    lo = so.layout(F, H, K)
+    p = rng.normal(size=lo["total"])
+    p[lo["sd"][0]:lo["sd"][0] + F] = rng.uniform(0.5, 2.0, size=F)
+    X = rng.normal(size=(B, F))
+    T = rng.normal(size=(B, K))
+    M = (rng.random(size=(B, K)) < 0.8).astype(np.float64)
+    return p, X, T, M, lo
+
+
+def fd_check(backward, seed=0, F=5, H=6, K=3):
+    p, X, T, M, lo = small_net(seed, F, H, K)
+    _, g = backward(p, X, T, M, F, H, K)
+    worst = 0.0
+    for i in range(lo["W1"][0], lo["total"]):
+        num = five_point(p, i, lambda q: so.loss(q, X, T, M, F, H, K))
+        worst = max(worst, abs(num - g[i]) / max(1e-2, abs(num) + abs(g[i])))
+    return worst
+
+
+def five_point(p, i, fn, h=1e-5):
+    """Central difference of fourth order: (-f(+2h) + 8 f(+h) - 8 f(-h) + f(-2h)) / 12h."""
+    vals = []
+    for k in (2, 1, -1, -2):
+        q = p.copy()
+        q[i] += k * h
+        vals.append(fn(q))
+    return (-vals[0] + 8 * vals[1] - 8 * vals[2] + vals[3]) / (12 * h)
+
+
+def test_backward_matches_central_differences():
+    for seed in range(3):
+        assert fd_check(so.backward, seed) < 1e-6
+
+
+def test_full_size_backward_spot_check():
+    rng = np.random.default_rng(1)
+    lo = so.layout()
+    p = rng.normal(scale=0.2, size=lo["total"])
+    p[lo["sd"][0]:lo["sd"][0] + so.N_FEATURES] = 1.0
+    X = rng.normal(size=(16, so.N_FEATURES))
+    T = rng.normal(size=(16, so.GRID))
+    M = np.ones((16, so.GRID))
+    _, g = so.backward(p, X, T, M)
+    for i in rng.choice(np.arange(lo["W1"][0], lo["total"]), size=60, replace=False):
+        num = five_point(p, i, lambda q: so.loss(q, X, T, M))
+        assert abs(num - g[i]) <= 1e-6 * max(1.0, abs(num))
+
+
+def test_planted_mistake_is_caught():
+    """A backward pass that drops the second ReLU mask fails the pin."""
+    def bad_backward(p, X, T, M, F, H, K):
+        mu, sd, W1, b1, W2, b2, W3, b3 = so.unpack(p, F, H, K)
+        y, (xn, a1, h1, a2, h2) = so.forward(p, X, F, H, K)
+        den = max(1.0, M.sum())
+        dy = 2.0 * M * (y - T) / den
+        da2 = dy @ W3  # mask dropped
+        da1 = (da2 @ W2) * (a1 > 0)
+        lo = so.layout(F, H, K)
+        g = np.zeros(lo["total"])
+        for name, arr in (("W1", da1.T @ xn), ("b1", da1.sum(0)), ("W2", da2.T @ h1), ("b2", da2.sum(0)),
+                          ("W3", dy.T @ h2), ("b3", dy.sum(0))):
+            o, s = lo[name]
+            g[o:o + s] = arr.reshape(-1)
+        return 0.0, g
+    assert fd_check(bad_backward, 0) > 1e-2
+
+
+def test_masked_entries_do_not_contribute():
+    p, X, T, M, lo = small_net(2)
+    T2 = T.copy()
+    T2[M == 0] += 100.0
+    assert so.loss(p, X, T, M, 5, 6, 3) == pytest.approx(so.loss(p, X, T2, M, 5, 6, 3))
+
+
+def test_zero_weights_give_bias_and_bias_gradient():
+    p, X, T, M, lo = small_net(3)
+    p[lo["W3"][0]:lo["W3"][0] + lo["W3"][1]] = 0.0
+    y, _ = so.forward(p, X, 5, 6, 3)
+    b3 = p[lo["b3"][0]:lo["b3"][0] + 3]
+    assert np.allclose(y, b3)
+    _, g = so.backward(p, X, T, M, 5, 6, 3)
+    expect = (2 * M * (b3 - T)).sum(0) / max(1.0, M.sum())
+    assert np.allclose(g[lo["b3"][0]:lo["b3"][0] + 3], expect)
+
+
+def test_adam_first_step_closed_form():
+    rng = np.random.default_rng(5)
+    p = rng.normal(size=50)
+    g = rng.normal(size=50)
+    z = np.zeros(50)
+    lr, eps = 1e-2, 1e-8
+    p1, m1, m2 = so.adam(p, g, z, z, 1, lr, eps=eps)
+    # step 1: bias-corrected moments are g and g^2
+    assert np.allclose(p1, p - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    p2, _, _ = so.adam(p, g, z, z, 1, lr, first=10)
+    assert np.array_equal(p2[:10], p[:10])
