@@ -408,7 +408,8 @@ def main():
     stage_ms = {"count": timing["count_ms"], "scan": timing["scan_ms"], "scatter": timing["scatter_ms"],
                 "sort": timing["sort_ms"], "sample": timing["sample_ms"]}
     if method == 1:
-        kname = "k_radix_down"
+        # the bulk-staged downsweep runs when radix_tile is 0 and every array is 16-byte aligned (torch's are)
+        kname = "k_radix_down_bulk" if plan.config().radix_tile == 0 else "k_radix_down"
         passes = radix_passes(n)
         per_edge = radix_down_bytes_per_edge(weighted, passes)
         dom_bytes = int(per_edge * m + 8 * (n + 1) / passes)

@@ -76,7 +76,9 @@ typedef struct gt_config {
     uint32_t sample_permille; /* sample size in 1/1000 of n (Sec. IV-C uses 10 = 1 %)     */
     uint32_t flags;           /* GT_FLAG_* bits                                            */
     uint32_t method;          /* GT_METHOD_*                                               */
-    uint32_t radix_tile;      /* GT_METHOD_RADIX: edges per CTA tile, 2048 or 4096 (0 = 4096) */
+    uint32_t radix_tile;      /* GT_METHOD_RADIX: 0 = bulk-copy staged 4096-edge tiles, one 512-thread
+                                 CTA per SM (needs 16-byte aligned arrays, else as 4096); 2048 or 4096 =
+                                 register tiles of 256 threads, ctas_per_sm CTAs per SM */
     uint64_t seed;            /* seed of the sampling positions                            */
 } gt_config;
 
@@ -111,8 +113,8 @@ typedef struct gt_timing {
     float scan_ms;     /* Step 2: HDV insertion points + look-back scan      */
     float scatter_ms;  /* Step 3: scatter                                    */
     float sort_ms;     /* LDV list sort                                      */
-    float total_ms;    /* GT_METHOD_RADIX: count_ms holds the digit passes and
-                          degree runs, scan_ms the scan, the rest are 0      */
+    float total_ms;    /* GT_METHOD_RADIX: count_ms holds the row expansion, the
+                          digit passes and col_ptr; the rest are 0           */
     float dominant_ms; /* average duration of one launch of the dominant
                           kernel: the scatter (HLH) or a digit downsweep (radix) */
     uint32_t dominant_launches; /* launches averaged                        */
@@ -253,14 +255,14 @@ gt_status gt_graph_features(uint32_t n_vertices, uint64_t n_edges, int has_vals,
  *   0 Atomic GT (hdv_k = 0, Algorithm 1)   1 same without warp aggregation
  *   2 HLH k=64   3 HLH k=512 (Eq. 1)   4 k=512, 1024-edge bulk-copy stages
  *   5 k=2048   6 k=512, 1024-edge partitions   7 k=512, 512 threads x 2 CTAs/SM
- *   8 radix 4096-edge tiles, 2 CTAs/SM   9 radix 4096, 4/SM   10 radix 2048, 4/SM
- *   11 radix 2048, 8/SM
+ *   8 radix, bulk-copy staged 4096-edge tiles, one 512-thread CTA per SM
+ *   9 radix, register tiles of 4096 edges, 2 CTAs/SM   10 same, 4/SM   11 2048-edge tiles, 4/SM
  * An HDV count above n/2 becomes 0 (the point then equals Atomic GT). */
 gt_status gt_tune_grid_config(uint32_t index, uint32_t n_vertices, uint64_t n_edges, gt_config *cfg);
 
 /* Analytic choice (the Sec. IV-B cost model, Eqs. 2-3, with GB300 rates and a
  * streaming term for the radix method) from host copies of the features:
- * writes the grid index (0, 3 or 9). */
+ * writes the grid index (0, 3 or 8). */
 gt_status gt_tune_analytic(const float *features, uint32_t n_vertices, uint64_t n_edges, uint32_t *index);
 
 typedef struct gt_selector_s *gt_selector;

@@ -103,6 +103,7 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   // radix method: radix_tile selects the tile (256 threads x 8 or 16 items),
   // ctas_per_sm the persistent grid
   w.r_items = c.radix_tile == 2048 ? 8u : 16u;
+  w.r_bulk = c.radix_tile == 0 ? 1 : 0;
   w.rG = (uint32_t)num_sms * c.ctas_per_sm;
   if (w.method == GT_METHOD_RADIX) {
     w.kmax = 0;
@@ -159,9 +160,12 @@ gt_status plan_alloc_ws(gt_plan p) {
     GT_AL(r_b_key, m * 4);
     (void)tiles;
     GT_AL(r_long, (m / 2049 + 1) * 4);
+    w.r_gap_cap = (uint32_t)(n / 1024 + 2);
+    GT_AL(r_gaps, (1 + 2 * (size_t)w.r_gap_cap) * 8);
     GT_AL(r_nlong, 4);
-    GT_AL(r_table, (size_t)w.rG * 256 * 4);
-    GT_AL(r_offsets, (size_t)w.rG * 256 * 8);
+    const size_t rows = w.rG > (uint32_t)w.num_sms * 4u ? w.rG : (size_t)w.num_sms * 4u;  // bulk: sms x 4 sub-CTAs
+    GT_AL(r_table, rows * 256 * 4);
+    GT_AL(r_offsets, rows * 256 * 8);
     if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
     if (cudaMemset(w.meta, 0, gt::kMetaCount * 4) != cudaSuccess) return GT_ERR_CUDA;
     if (cudaMemset(w.meta64, 0, 32) != cudaSuccess) return GT_ERR_CUDA;
@@ -353,6 +357,8 @@ static gt_status shape_for(gt_plan plan, uint32_t n, uint64_t m, gt::DevWork &w)
   w.method = t.method;
   w.rG = t.rG;
   w.r_items = t.r_items;
+  w.r_bulk = t.r_bulk;
+  w.r_gap_cap = (uint32_t)(t.n / 1024 + 2) < w.r_gap_cap ? (uint32_t)(t.n / 1024 + 2) : w.r_gap_cap;
   return GT_OK;
 }
 

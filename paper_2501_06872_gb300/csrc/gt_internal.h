@@ -61,9 +61,12 @@ struct DevWork {
   int method = 0;
   uint32_t rG = 0;                            // persistent CTAs of the digit passes
   uint32_t r_items = 16;                      // elements per thread of a downsweep tile (8 or 16)
+  int r_bulk = 0;                             // bulk-copy staged downsweep (one 512-thread CTA per SM)
   uint32_t *r_a_key = nullptr, *r_a_u = nullptr, *r_a_w = nullptr;  // [m] ping buffer
   uint32_t *r_b_key = nullptr;                // [m] keys of the pong buffer (u/w live in the outputs)
   uint32_t *r_long = nullptr;                 // rows longer than the window expansion handles
+  unsigned long long *r_gaps = nullptr;       // [1 + 2 * r_gap_cap]: count, then (lo << 32 | hi, value) ranges
+  uint32_t r_gap_cap = 0;                     // long col_ptr ranges listed per call
   uint32_t *r_nlong = nullptr;                // [1] (zeroed per call)
   uint32_t *r_table = nullptr;                // [rG][256]
   unsigned long long *r_offsets = nullptr;    // [rG][256]

@@ -79,6 +79,7 @@ struct RadixArgs {
   const unsigned long long *offsets;  // [G][256] starting positions
   uint32_t *status;
   BatchView batch;
+  uint32_t sub = 1;  // upsweep CTAs per downsweep CTA (table rows = G * sub)
 };
 
 // Pass modes: plain arrays, or a batch whose first pass loads through the
@@ -97,6 +98,8 @@ __global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n, 
                               uint32_t *long_rows, uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (row_ptr[0] != 0 || row_ptr[n] != m))
+    set_status(status, GT_ERR_BAD_ROW_PTR);
   for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n; r0 += warps * 32) {
     const uint64_t r = r0 + lane;
     uint64_t ri = r + 1;
@@ -155,8 +158,13 @@ __global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
   __syncthreads();
   const uint32_t mask = (1u << a.dbits) - 1u;
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-  const uint64_t t0 = (uint64_t)blockIdx.x * a.tiles_per_cta;
-  const uint64_t e0 = min64(t0 * a.tile, a.m), e1 = min64((t0 + a.tiles_per_cta) * a.tile, a.m);
+  const uint64_t t0 = (uint64_t)(blockIdx.x / a.sub) * a.tiles_per_cta;
+  uint64_t e0 = min64(t0 * a.tile, a.m), e1 = min64((t0 + a.tiles_per_cta) * a.tile, a.m);
+  if (a.sub > 1) {  // this CTA counts part (blockIdx.x % sub) of the downsweep CTA's range
+    const uint64_t part = (e1 - e0 + a.sub - 1) / a.sub, s0 = e0 + (blockIdx.x % a.sub) * part;
+    e1 = min64(s0 + part, e1);
+    e0 = min64(s0, e1);
+  }
   const uint32_t *src = a.in_key;
   constexpr int U = 8;
   uint32_t bad = 0;
@@ -402,6 +410,293 @@ __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
   }
 }
 
+// Downsweep with bulk-copy staging (plain arrays, 16-byte aligned): two
+// persistent CTAs of 256 threads per SM, each walking its contiguous tiles of
+// 4096 edges.  The next tile's keys, sources and values arrive in shared
+// memory through cp.async.bulk (the TMA engine), double-buffered behind
+// mbarriers, while the current tile is ranked (ballot digit matching,
+// stable).  The tile is then pulled into registers and written back to the
+// same buffer in (digit, rank) order, and leaves as coalesced digit runs;
+// the freed buffer receives the tile after next.  A ragged final tile is
+// loaded with plain loads.  Every mbarrier wait is bounded; on expiry the CTA
+// reports GT_ERR_TIMEOUT, waits (bounded) for its copies in flight and
+// returns.
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kBItems = 16;
+constexpr uint32_t kBTile = kBThreads * kBItems;
+constexpr uint32_t kBCtasPerSm = 2;
+
+__host__ __device__ constexpr uint32_t bulk_arrays(bool vals) { return vals ? 3u : 2u; }
+__host__ constexpr size_t bulk_dyn_smem(bool vals) { return (size_t)2 * bulk_arrays(vals) * kBTile * 4; }
+
+template <bool VALS>
+__global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(RadixArgs a) {
+  constexpr uint32_t NA = bulk_arrays(VALS);
+  extern __shared__ __align__(128) uint32_t dsm[];  // buf[2][NA][TILE]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t wcnt[kBWarps][kRBins];
+  __shared__ unsigned long long run_off[kRBins];
+  __shared__ uint32_t tile_start[kRBins];
+  __shared__ uint32_t wsum[kBWarps];
+  __shared__ uint32_t s_abort;
+  const uint32_t tid = threadIdx.x, w = tid >> 5, lane = tid & 31u;
+  const uint32_t mask = (1u << a.dbits) - 1u;
+  const uint64_t t0 = (uint64_t)blockIdx.x * a.tiles_per_cta;
+  const uint64_t t1 = min64(t0 + a.tiles_per_cta, a.ntiles);
+  if (t0 >= t1) return;
+  run_off[tid] = a.offsets[(size_t)blockIdx.x * a.sub * kRBins + tid];  // kBThreads == kRBins
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto full = [&](uint64_t t) { return (t + 1) * kBTile <= a.m; };
+  auto issue = [&](uint64_t t, uint32_t b) {  // one thread
+    uint32_t *dst = dsm + b * NA * kBTile;
+    const uint64_t e = t * kBTile;
+    mbar_arrive_expect_tx(&bar[b], NA * kBTile * 4u);
+    bulk_g2s(dst, a.in_key + e, kBTile * 4u, &bar[b]);
+    bulk_g2s(dst + kBTile, a.in_u + e, kBTile * 4u, &bar[b]);
+    if (VALS) bulk_g2s(dst + 2 * kBTile, a.in_w + e, kBTile * 4u, &bar[b]);
+  };
+  if (tid == 0) {
+    if (full(t0)) issue(t0, 0);
+    if (t0 + 1 < t1 && full(t0 + 1)) issue(t0 + 1, 1);
+  }
+  // bit b: a copy into buffer b is in flight / parity of its next phase
+  uint32_t pending = (full(t0) ? 1u : 0u) | ((t0 + 1 < t1 && full(t0 + 1)) ? 2u : 0u);
+  uint32_t par = 0u;
+  for (uint64_t t = t0; t < t1; ++t) {
+    const uint32_t b = (uint32_t)((t - t0) & 1u);
+    uint32_t *bk = dsm + b * NA * kBTile, *bu = bk + kBTile, *bw = bk + 2 * kBTile;
+    const uint64_t tbase = t * kBTile;
+    const uint32_t tcount = (uint32_t)min64(kBTile, a.m - tbase);
+#pragma unroll
+    for (int x = 0; x < kBWarps; ++x) wcnt[x][tid] = 0;
+    if (tcount == kBTile) {
+      if (!mbar_wait(&bar[b], (par >> b) & 1u)) s_abort = 1;
+      par ^= 1u << b;
+      pending &= ~(1u << b);
+    } else {
+      for (uint32_t j = tid; j < tcount; j += kBThreads) {
+        bk[j] = __ldcs(a.in_key + tbase + j);
+        bu[j] = __ldcs(a.in_u + tbase + j);
+        if (VALS) bw[j] = __ldcs(a.in_w + tbase + j);
+      }
+    }
+    __syncthreads();
+    if (s_abort) {
+      if (tid == 0) {
+        set_status(a.status, GT_ERR_TIMEOUT);
+        for (uint32_t q = 0; q < 2; ++q)
+          if ((pending >> q) & 1u) mbar_wait(&bar[q], (par >> q) & 1u);
+      }
+      return;
+    }
+    // stable rank within the warp (items in order, lanes in order); the
+    // tile moves into registers
+    uint32_t key[kBItems], uu[kBItems], ww[kBItems], rk[kBItems];
+#pragma unroll
+    for (int i = 0; i < kBItems; ++i) {
+      const uint32_t j = w * (kBItems * 32) + i * 32 + lane;
+      const bool act = j < tcount;
+      key[i] = act ? bk[j] : 0u;
+      uu[i] = act ? bu[j] : 0u;
+      ww[i] = (VALS && act) ? bw[j] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kBItems; ++i) {
+      const bool act = w * (kBItems * 32) + i * 32 + lane < tcount;
+      const uint32_t d = (key[i] >> a.shift) & mask;
+      const uint32_t mm = match_digit(d, a.dbits, act);
+      const uint32_t r = __popc(mm & lanemask_lt());
+      uint32_t c = 0;
+      if (act) c = wcnt[w][d];
+      __syncwarp();
+      if (act && r == 0) wcnt[w][d] = c + __popc(mm);
+      __syncwarp();
+      rk[i] = act ? (c + r) : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    // per digit (one thread each): exclusive prefix over warps, tile total,
+    // then the tile-local start of every digit
+    uint32_t run = 0;
+#pragma unroll
+    for (int x = 0; x < kBWarps; ++x) {
+      const uint32_t c = wcnt[x][tid];
+      wcnt[x][tid] = run;
+      run += c;
+    }
+    const uint32_t tot = run;
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    {
+      uint32_t before = 0;
+#pragma unroll
+      for (int x = 0; x < kBWarps; ++x) before += (x < (int)w) ? wsum[x] : 0u;
+      tile_start[tid] = before + inc - tot;
+    }
+    __syncthreads();
+    // back into the same buffer in (digit, rank) order
+#pragma unroll
+    for (int i = 0; i < kBItems; ++i) {
+      if (rk[i] != 0xFFFFFFFFu) {
+        const uint32_t d = (key[i] >> a.shift) & mask;
+        const uint32_t lp = tile_start[d] + wcnt[w][d] + rk[i];
+        bk[lp] = key[i];
+        bu[lp] = uu[i];
+        if (VALS) bw[lp] = ww[i];
+      }
+    }
+    __syncthreads();
+    if (tcount == kBTile) {
+#pragma unroll 4
+      for (int q = 0; q < kBItems; ++q) {
+        const uint32_t j = q * kBThreads + tid;
+        const uint32_t k = bk[j];
+        const uint32_t d = (k >> a.shift) & mask;
+        const uint64_t pos = run_off[d] + (j - tile_start[d]);
+        a.out_key[pos] = k;
+        a.out_u[pos] = bu[j];
+        if (VALS) a.out_w[pos] = bw[j];
+      }
+    } else {
+      for (uint32_t j = tid; j < tcount; j += kBThreads) {
+        const uint32_t k = bk[j];
+        const uint32_t d = (k >> a.shift) & mask;
+        const uint64_t pos = run_off[d] + (j - tile_start[d]);
+        a.out_key[pos] = k;
+        a.out_u[pos] = bu[j];
+        if (VALS) a.out_w[pos] = bw[j];
+      }
+    }
+    __syncthreads();
+    run_off[tid] += tot;
+    // the buffer is free: prefetch tile t + 2 into it
+    if (t + 2 < t1 && full(t + 2)) {
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(t + 2, b);
+      }
+      pending |= 1u << b;
+    }
+  }
+}
+
+// col_ptr straight from the sorted keys: col_ptr[v] = #edges with key < v.
+// Each warp takes chunks of 256 positions [c, c + 256).  The entries the
+// chunk determines form one vertex range [key[c-1] + 1, key of the chunk's
+// last position] (up to n for the last chunk), and for v in it col_ptr[v] =
+// c + (chunk keys < v), a binary search over the chunk's keys in shared
+// memory: the warp stores the range with coalesced writes, no atomics.  A
+// chunk whose range is longer than kChunkRange (a long run of empty
+// vertices) stores per run start instead: short ranges by their lane, medium
+// ones by the warp together, long ones listed for k_radix_gaps.  Keys >= n
+// (an out-of-range input, already reported) are treated as n.
+constexpr uint32_t kGapLong = 1024;
+constexpr uint32_t kCpChunk = 256;
+constexpr uint32_t kChunkRange = 4096;
+
+__device__ __forceinline__ void colptr_range(uint64_t a, uint64_t b, uint64_t val, uint64_t *col_ptr,
+                                             unsigned long long *gaps, uint32_t gap_cap, uint32_t *status,
+                                             uint32_t lane) {
+  const uint64_t len = b >= a ? b - a + 1 : 0;
+  if (len > 0 && len <= 32)
+    for (uint64_t v = a; v <= b; ++v) col_ptr[v] = val;
+  if (len > kGapLong) {
+    const uint32_t i = atomicAdd((uint32_t *)gaps, 1u);
+    if (i < gap_cap) {
+      gaps[1 + 2 * (uint64_t)i] = (a << 32) | b;
+      gaps[2 + 2 * (uint64_t)i] = val;
+    } else {
+      set_status(status, GT_ERR_UNSUPPORTED);
+    }
+  }
+  uint32_t mid = __ballot_sync(kFull, len > 32 && len <= kGapLong);
+  while (mid) {  // the warp stores each medium range together
+    const int j = __ffs(mid) - 1;
+    mid &= mid - 1;
+    const uint64_t ja = __shfl_sync(kFull, a, j), jb = __shfl_sync(kFull, b, j);
+    const uint64_t jv = __shfl_sync(kFull, val, j);
+    for (uint64_t v = ja + lane; v <= jb; v += 32) col_ptr[v] = jv;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_radix_colptr(const uint32_t *__restrict__ key, uint64_t m, uint32_t n,
+                                                      uint64_t *col_ptr, unsigned long long *gaps, uint32_t gap_cap,
+                                                      uint32_t *status) {
+  __shared__ uint32_t sk[8][kCpChunk];
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  uint32_t *ck = sk[w];
+  const uint64_t nwarps = (uint64_t)gridDim.x * 8;
+  for (uint64_t c = ((uint64_t)blockIdx.x * 8 + w) * kCpChunk; c < m; c += nwarps * kCpChunk) {
+    const uint32_t cnt = (uint32_t)min64(kCpChunk, m - c);
+#pragma unroll
+    for (int i = 0; i < (int)(kCpChunk / 32); ++i) {
+      const uint32_t j = i * 32 + lane;
+      ck[j] = j < cnt ? min(__ldcs(key + c + j), n) : 0xFFFFFFFFu;
+    }
+    __syncwarp();
+    const uint64_t lo = c == 0 ? 0 : (uint64_t)min(key[c - 1], n) + 1;
+    const uint64_t hi = (c + cnt == m) ? (uint64_t)n : (uint64_t)ck[cnt - 1];
+    if (hi + 1 <= lo + kChunkRange) {
+      for (uint64_t v = lo + lane; v <= hi; v += 32) {
+        uint32_t l = 0, r = cnt;  // first chunk index with key >= v
+        while (l < r) {
+          const uint32_t mid = (l + r) >> 1;
+          if ((uint64_t)ck[mid] < v) l = mid + 1;
+          else r = mid;
+        }
+        col_ptr[v] = c + l;
+      }
+    } else {
+      // per run start: (key[p-1], key[p]] gets p; the last position also
+      // (key[m-1], n] gets m
+#pragma unroll 1
+      for (uint32_t i = 0; i < kCpChunk / 32; ++i) {
+        const uint32_t j = i * 32 + lane;
+        const uint64_t p = c + j;
+        uint64_t a = 1, b = 0, a2 = 1, b2 = 0;
+        if (j < cnt) {
+          const uint32_t k = ck[j];
+          const uint64_t kp = j ? (uint64_t)ck[j - 1] : (c == 0 ? ~0ull : lo - 1);
+          if (p == 0 || kp != k) {
+            a = p == 0 ? 0 : kp + 1;
+            b = k;
+          }
+          if (p + 1 == m) {
+            a2 = (uint64_t)k + 1;
+            b2 = n;
+          }
+        }
+        colptr_range(a, b, p, col_ptr, gaps, gap_cap, status, lane);
+        colptr_range(a2, b2, m, col_ptr, gaps, gap_cap, status, lane);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// The listed long ranges, each by the whole grid.
+__global__ void k_radix_gaps(const unsigned long long *__restrict__ gaps, uint32_t gap_cap, uint64_t *col_ptr) {
+  const uint32_t cnt = min(*(const uint32_t *)gaps, gap_cap);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const uint64_t r = gaps[1 + 2 * (uint64_t)i], val = gaps[2 + 2 * (uint64_t)i];
+    const uint64_t a = r >> 32, b = r & 0xFFFFFFFFull;
+    for (uint64_t v = a + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= b; v += stride) col_ptr[v] = val;
+  }
+}
+
 // Degrees from the runs of equal keys in the sorted key array:
 // deg[k] = (end of run) - (start of run), via two wrapping adds.
 __global__ void k_radix_runs(const uint32_t *__restrict__ key, uint64_t m, uint32_t n, uint32_t *deg) {
@@ -434,7 +729,9 @@ cudaError_t configure_radix() {
                       allow_down<8, kBatchOnly>(),   allow_down<16, kBatchOnly>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
-  return cudaSuccess;
+  cudaError_t b1 = allow_max_dynamic_smem(k_radix_down_bulk<true>);
+  cudaError_t b2 = allow_max_dynamic_smem(k_radix_down_bulk<false>);
+  return b1 != cudaSuccess ? b1 : b2;
 }
 
 template <int MODE>
@@ -458,14 +755,18 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   const uint32_t passes = (bits + 7) / 8;
   const uint32_t dbits = (bits + passes - 1) / passes;
   const uint32_t items = w.r_items;
-  const uint32_t tile = kRThreads * items;
-  const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
-  const uint32_t G = w.rG;
-  const uint32_t tpc = (ntiles + G - 1) / G;
-  if (m == 0) return cudaSuccess;
   // buffers: A = (a_key, a_u, a_w); B = (b_key, row_idx, vals_out).  Pass p
   // writes B when (passes - p) is even, so the last pass writes the outputs.
   uint32_t *b_u = pb.row_idx, *b_w = (uint32_t *)pb.vals_out;
+  // bulk-staged downsweep: every array a pass reads must be 16-byte aligned
+  auto al16 = [](const void *p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
+  const bool bulk = w.r_bulk && al16(pb.col_idx) && al16(pb.vals) && al16(b_u) && al16(b_w) && al16(w.r_a_key) &&
+                    al16(w.r_a_u) && al16(w.r_a_w) && al16(w.r_b_key);
+  const uint32_t tile = bulk ? kBTile : kRThreads * items;
+  const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
+  const uint32_t G = bulk ? (uint32_t)w.num_sms * kBCtasPerSm : w.rG;
+  const uint32_t sub = bulk ? 2u : 1u;
+  const uint32_t tpc = (ntiles + G - 1) / G;
   const bool first_to_b = ((passes - 1) % 2) == 0;
   // source rows of the first pass go to the buffer the first pass does not write
   uint32_t *src_rows = first_to_b ? w.r_a_u : b_u;
@@ -478,18 +779,27 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     k_expand_long<<<w.num_sms * 4, 256, 0, s>>>(pb.row_ptr, w.r_long, w.r_nlong, long_cap, src_rows);
     nl += 2;
   }
+  if (m == 0) {  // the expansion only validated row_ptr
+    if (launches) *launches += nl;
+    return cudaGetLastError();
+  }
   const uint32_t *in_key = pb.col_idx, *in_u = src_rows, *in_w = (const uint32_t *)pb.vals;
   for (uint32_t p = 1; p <= passes; ++p) {
     const bool toB = ((passes - p) % 2) == 0;
     uint32_t *ok = toB ? w.r_b_key : w.r_a_key, *ou = toB ? b_u : w.r_a_u, *ow = toB ? b_w : w.r_a_w;
     RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
-                 (p - 1) * dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status, BatchView{}};
-    if (p == 1) k_radix_up<true, kPlain><<<G, kRThreads, 0, s>>>(ra);
-    else k_radix_up<false, kPlain><<<G, kRThreads, 0, s>>>(ra);
-    k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G, w.r_offsets);
+                 (p - 1) * dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status, BatchView{}, sub};
+    if (p == 1) k_radix_up<true, kPlain><<<G * sub, kRThreads, 0, s>>>(ra);
+    else k_radix_up<false, kPlain><<<G * sub, kRThreads, 0, s>>>(ra);
+    k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G * sub, w.r_offsets);
     if (ev && ev->ndown + 2 <= 8) cudaEventRecord(ev->down[ev->ndown], s);
-    const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
-    launch_down<kPlain>(vals, items, G, dsm, s, ra);
+    if (bulk) {
+      if (vals) k_radix_down_bulk<true><<<G, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else k_radix_down_bulk<false><<<G, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+    } else {
+      const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
+      launch_down<kPlain>(vals, items, G, dsm, s, ra);
+    }
     if (ev && ev->ndown + 2 <= 8) {
       cudaEventRecord(ev->down[ev->ndown + 1], s);
       ev->ndown += 2;
@@ -501,8 +811,9 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     in_w = ow;
   }
   uint32_t g = (uint32_t)min64((m + 255) / 256, (uint64_t)w.num_sms * 16);
-  k_radix_runs<<<g, 256, 0, s>>>(w.r_b_key, m, n, w.deg);
-  ++nl;
+  k_radix_colptr<<<g, 256, 0, s>>>(w.r_b_key, m, n, pb.col_ptr, w.r_gaps, w.r_gap_cap, w.status);
+  k_radix_gaps<<<w.num_sms * 4, 256, 0, s>>>(w.r_gaps, w.r_gap_cap, pb.col_ptr);
+  nl += 2;
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

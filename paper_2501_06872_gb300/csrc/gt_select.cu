@@ -563,10 +563,10 @@ gt_status gt_tune_grid_config(uint32_t index, uint32_t n_vertices, uint64_t n_ed
     case 5: k = 2048; break;
     case 6: k = 512; cfg->warp_edges = 1024; break;          // finer partitions
     case 7: k = 512; cfg->block_threads = 512; cfg->ctas_per_sm = 2; break;
-    case 8: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 4096; cfg->ctas_per_sm = 2; break;
-    case 9: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 4096; cfg->ctas_per_sm = 4; break;
-    case 10: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 2048; cfg->ctas_per_sm = 4; break;
-    default: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 2048; cfg->ctas_per_sm = 8; break;
+    case 8: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 0; cfg->ctas_per_sm = 4; break;  // bulk-staged
+    case 9: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 4096; cfg->ctas_per_sm = 2; break;
+    case 10: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 4096; cfg->ctas_per_sm = 4; break;
+    default: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 2048; cfg->ctas_per_sm = 4; break;
   }
   if (cfg->method == GT_METHOD_RADIX || k > n_vertices / 2) k = 0;
   cfg->hdv_k = k;
@@ -617,7 +617,7 @@ gt_status gt_tune_analytic(const float *features, uint32_t n_vertices, uint64_t 
     best = 3;
     t = hlh;
   }
-  if (radix < t) best = 9;
+  if (radix < t) best = 8;
   (void)n_edges;
   *index = best;
   return GT_OK;

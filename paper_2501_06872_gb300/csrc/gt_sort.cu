@@ -301,11 +301,118 @@ struct Buf {
   __device__ uint32_t getw(uint32_t i) const { return packed ? (uint32_t)(packed[i] >> 32) : (w ? w[i] : 0u); }
 };
 
+// Sorts a[0, len) (u32 positions of one split-row run; all distinct) with the
+// whole CTA: bitonic in shared memory up to kRunSmem values, else a stable
+// LSD radix sort (8-bit digits over the bits of the largest value) through
+// tmp[0, len), the result back in a.  smem: at least 2 * 256 * 32 words.
+constexpr uint32_t kRunSmem = 4096;
+
+__device__ void cta_sort_run(uint32_t *a, uint32_t *tmp, uint32_t len, uint32_t *smem) {
+  __shared__ uint32_t s_max;
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31u;
+  if (len <= kRunSmem) {
+    uint32_t cap = 2;
+    while (cap < len) cap <<= 1;
+    for (uint32_t i = tid; i < cap; i += nt) smem[i] = i < len ? a[i] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= cap; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = tid; i < cap; i += nt) {
+          const uint32_t l = i ^ j;
+          if (l > i) {
+            const uint32_t x = smem[i], y = smem[l];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              smem[i] = y;
+              smem[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = tid; i < len; i += nt) a[i] = smem[i];
+    __syncthreads();
+    return;
+  }
+  if (tid == 0) s_max = 0;
+  __syncthreads();
+  uint32_t mx = 0;
+  for (uint32_t i = tid; i < len; i += nt) mx = max(mx, a[i]);
+  atomicMax(&s_max, mx);
+  __syncthreads();
+  const uint32_t bits = 32u - (uint32_t)__clz((int)(s_max | 1u));
+  const uint32_t passes = (bits + 7) / 8;
+  uint32_t *hist = smem, *tot = smem + 256 * 32;  // hist[digit][warp], tot[digit]
+  const uint32_t nwarps = nt >> 5;
+  const uint32_t chunk = (len + nwarps - 1) / nwarps;
+  uint32_t *src = a, *dst = tmp;
+  for (uint32_t ps = 0; ps < passes; ++ps) {
+    const uint32_t shift = ps * 8;
+    for (uint32_t i = tid; i < 256 * 32; i += nt) hist[i] = 0;
+    __syncthreads();
+    const uint32_t r0 = min(w * chunk, len), r1 = min(r0 + chunk, len);
+    for (uint32_t i = r0 + lane; i < r1; i += 32) atomicAdd(&hist[((src[i] >> shift) & 255u) * 32 + w], 1u);
+    __syncthreads();
+    for (uint32_t d = w; d < 256; d += nwarps) {  // per digit: prefix over warps
+      const uint32_t x = hist[d * 32 + lane];
+      uint32_t inc = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+      }
+      hist[d * 32 + lane] = inc - x;
+      if (lane == 31) tot[d] = inc;
+    }
+    __syncthreads();
+    if (w == 0) {  // prefix over digits
+      uint32_t run = 0;
+      for (uint32_t d0 = 0; d0 < 256; d0 += 32) {
+        const uint32_t t = tot[d0 + lane];
+        uint32_t inc = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, inc, o);
+          if (lane >= (uint32_t)o) inc += y;
+        }
+        tot[d0 + lane] = run + inc - t;
+        run += __shfl_sync(kFull, inc, 31);
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < 256 * 32; i += nt) hist[i] += tot[i >> 5];
+    __syncthreads();
+    for (uint32_t c = r0; c < r1; c += 32) {  // stable scatter, each warp in order
+      const uint32_t i = c + lane;
+      const bool act = i < r1;
+      const uint32_t x = act ? src[i] : 0u;
+      const uint32_t d = act ? ((x >> shift) & 255u) : 256u;
+      const uint32_t mm = __match_any_sync(kFull, d);
+      const uint32_t rank = __popc(mm & lanemask_lt());
+      uint32_t base = 0;
+      if (act) base = hist[d * 32 + w];
+      __syncwarp();
+      if (act && rank == 0) hist[d * 32 + w] = base + __popc(mm);
+      __syncwarp();
+      if (act) dst[base + rank] = x;
+    }
+    __syncthreads();
+    uint32_t *t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != a)
+    for (uint32_t i = tid; i < len; i += nt) a[i] = src[i];
+  __syncthreads();
+}
+
 template <bool VALS>
 __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (cta_status_set(a.status)) return;
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item, s_tagged, s_nlong;
+  __shared__ uint32_t s_long_i[kRadixThreads], s_long_n[kRadixThreads];
   const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t umask = umask_of(a);
   const uint32_t nlarge = min(a.meta[kMetaLargeN], a.large_cap);
@@ -336,12 +443,19 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
       scr = Buf{a.scr32 + s0, nullptr, nullptr};
       src = out;
     }
-    // first pass's per-warp counts
+    // first pass's per-warp counts; notes whether any entry is tagged
     for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) s_tagged = 0;
     __syncthreads();
     {
       const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
-      for (uint32_t i = r0 + lane; i < r1; i += 32) atomicAdd(&hist[(src.getu(i) & umask & (nb - 1)) * 32 + w], 1u);
+      uint32_t anytag = 0;
+      for (uint32_t i = r0 + lane; i < r1; i += 32) {
+        const uint32_t u = src.getu(i);
+        anytag |= u & ~umask;
+        atomicAdd(&hist[(u & umask & (nb - 1)) * 32 + w], 1u);
+      }
+      if (anytag) s_tagged = 1;
     }
     __syncthreads();
     Buf dst = VALS ? out : scr;
@@ -410,26 +524,49 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
       src = dst;
       dst = (dst.u == out.u) ? scr : out;
     }
-    // src holds the sorted list (SoA): order tagged runs by position, then
-    // write the outputs (in place when src is the output buffer)
-    if (VALS && a.flag_mode) {
-      for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-        const uint32_t u = src.u[i];
-        if (!(u & kSplitFlag)) continue;
-        if (i > 0 && src.u[i - 1] == u) continue;  // not the first of its run
-        uint32_t j = i + 1;
-        while (j < L && src.u[j] == u) ++j;
-        for (uint32_t x = i + 1; x < j; ++x) {
-          const uint32_t tpos = src.w[x];
-          uint32_t y = x;
-          while (y > i && src.w[y - 1] > tpos) {
-            src.w[y] = src.w[y - 1];
-            --y;
+    // src holds the sorted list (SoA): order tagged runs (split rows) by
+    // their position in the row, then write the outputs (in place when src
+    // is the output buffer).  A run of <= 64 entries is sorted by the thread
+    // at its start; longer ones by the whole CTA, window by window.
+    if (VALS && a.flag_mode && s_tagged) {
+      Buf other = (src.u == out.u) ? scr : out;
+      for (uint32_t base = 0; base < L; base += blockDim.x) {
+        if (threadIdx.x == 0) s_nlong = 0;
+        __syncthreads();
+        const uint32_t i = base + threadIdx.x;
+        if (i < L) {
+          const uint32_t u = src.u[i];
+          if ((u & kSplitFlag) && (i == 0 || src.u[i - 1] != u)) {
+            uint32_t lo = i, hi = L;  // end of the run: first index past i with another source
+            while (hi - lo > 1) {
+              const uint32_t mid = lo + (hi - lo) / 2;
+              if (src.u[mid] == u) lo = mid;
+              else hi = mid;
+            }
+            const uint32_t j = hi;
+            if (j - i <= 64) {
+              for (uint32_t x = i + 1; x < j; ++x) {
+                const uint32_t tpos = src.w[x];
+                uint32_t y = x;
+                while (y > i && src.w[y - 1] > tpos) {
+                  src.w[y] = src.w[y - 1];
+                  --y;
+                }
+                src.w[y] = tpos;
+              }
+            } else {
+              const uint32_t q = atomicAdd(&s_nlong, 1u);
+              s_long_i[q] = i;
+              s_long_n[q] = j - i;
+            }
           }
-          src.w[y] = tpos;
         }
+        __syncthreads();
+        const uint32_t nl = s_nlong;
+        for (uint32_t q = 0; q < nl; ++q)
+          cta_sort_run(src.w + s_long_i[q], other.w + s_long_i[q], s_long_n[q], (uint32_t *)smem);
+        __syncthreads();
       }
-      __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
       uint32_t u = src.u[i];

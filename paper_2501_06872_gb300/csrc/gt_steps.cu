@@ -896,26 +896,25 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   if ((err = cudaMemsetAsync(w.status, 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(w.meta, 0, kMetaCount * sizeof(uint32_t), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(w.meta64, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return err;
-  if ((err = cudaMemsetAsync(w.deg, 0, (size_t)w.n * sizeof(uint32_t), s)) != cudaSuccess) return err;
-  if ((err = cudaMemsetAsync(w.scan_state, 0, (size_t)w.ntiles * sizeof(unsigned long long), s)) != cudaSuccess)
-    return err;
-
   if (w.method == GT_METHOD_RADIX) {
-    // timing slots: count = digit passes and degree runs, scan = look-back scan
+    // timing slots: count = row expansion, digit passes and col_ptr; the rest are 0
     mark(1);
     nl = 0;
     if ((err = cudaMemsetAsync(w.r_nlong, 0, 4, s)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(w.r_gaps, 0, 8, s)) != cudaSuccess) return err;
+    if (w.m == 0 && (err = cudaMemsetAsync(pb.col_ptr, 0, ((size_t)w.n + 1) * 8, s)) != cudaSuccess) return err;
     if ((err = run_radix(w, pb, s, &nl, ev)) != cudaSuccess) return err;
     mark(2);
-    k_scan<<<w.ntiles, kScanThreads, 0, s>>>(w.deg, w.n, w.m, pb.row_ptr, pb.col_ptr, nullptr, w.scan_state, w.meta,
-                                             w.status);
-    ++nl;
     mark(3);
     mark(4);
     mark(5);
     if (launches) *launches = nl;
     return cudaGetLastError();
   }
+
+  if ((err = cudaMemsetAsync(w.deg, 0, (size_t)w.n * sizeof(uint32_t), s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(w.scan_state, 0, (size_t)w.ntiles * sizeof(unsigned long long), s)) != cudaSuccess)
+    return err;
 
   // Step 0
   if (hdv) {

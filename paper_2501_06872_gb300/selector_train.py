@@ -40,8 +40,8 @@ def graph_spec(i: int, seed: int = 0x5EED0005):
 
 
 def _norm(c: dict) -> tuple:
-    if c["method"] == 1:
-        return (1, c["radix_tile"] or 4096, c["ctas_per_sm"])
+    if c["method"] == 1:  # the bulk-staged kernel (tile 0) has one CTA per SM whatever ctas_per_sm says
+        return (1, c["radix_tile"], c["ctas_per_sm"] if c["radix_tile"] else 0)
     return (0, c["hdv_k"], c["table_log2"], c["block_threads"], c["ctas_per_sm"], c["warp_edges"],
             c["stage_edges"], c["flags"])
 
@@ -56,12 +56,24 @@ def default_index(n: int, m: int) -> int:
     return -1
 
 
-def build_dataset(count: int, reps: int = 3, log=print):
+def save_dataset(path, feats, times, meta):
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, features=np.stack(feats), times=np.stack(times), meta=json.dumps(meta))
+    os.replace(tmp, path)
+
+
+def build_dataset(count: int, reps: int = 3, log=print, path=None):
+    """Times every grid point on `count` graphs; with `path`, saves after every
+    graph and resumes from what an earlier run saved there."""
     import torch
     from . import binding
     from .inputs import gpu as ggen
     feats, times, meta = [], [], []
-    for i in range(count):
+    if path and os.path.exists(path):
+        d = np.load(path, allow_pickle=False)
+        feats, times, meta = list(d["features"]), list(d["times"]), json.loads(str(d["meta"]))
+        log(f"resuming after {len(meta)} graphs")
+    for i in range(len(meta), count):
         sp = graph_spec(i)
         t0 = time.time()
         n, rp, ci, vv = ggen.graph(sp["scale"], sp["edge_factor"], "rmat", sp["a"], sp["b"], sp["c"], sp["seed"],
@@ -85,6 +97,8 @@ def build_dataset(count: int, reps: int = 3, log=print):
             f"{ms[ms > 0].min():.3f} ms, analytic {an}, default {di} ({time.time() - t0:.1f} s)")
         del rp, ci, vv, cp, ri, vo
         torch.cuda.empty_cache()
+        if path:
+            save_dataset(path, feats, times, meta)
     return np.stack(feats), np.stack(times), meta
 
 
@@ -186,8 +200,7 @@ def main():
         feats, times = d["features"], d["times"]
         meta = json.loads(str(d["meta"]))
     else:
-        feats, times, meta = build_dataset(args.graphs, args.reps, log)
-        np.savez(os.path.join(args.out, "dataset.npz"), features=feats, times=times, meta=json.dumps(meta))
+        feats, times, meta = build_dataset(args.graphs, args.reps, log, os.path.join(args.out, "dataset.npz"))
     tr = slice(0, args.train)
     te = slice(args.train, len(feats))
     fit = slice(0, args.train - args.val)

@@ -67,7 +67,8 @@ CONFIGS = {
     "hdv4096_w1024": dict(hdv_k=4096, table_log2=13, block_threads=128, ctas_per_sm=1, warp_edges=2048),
     "noagg_staged": dict(hdv_k=16, flags=0, stage_edges=128),
     "big_blocks": dict(hdv_k=128, block_threads=1024, ctas_per_sm=1, warp_edges=64),
-    "radix": dict(method=1),
+    "radix": dict(method=1),  # bulk-copy staged downsweep
+    "radix4096": dict(method=1, radix_tile=4096, ctas_per_sm=3),
     "radix2048": dict(method=1, radix_tile=2048, ctas_per_sm=6),
 }
 
@@ -109,9 +110,63 @@ def test_random_graphs_all_configs(name, seed):
 def test_rmat_numpy_scale14(order):
     n, rp, ci, vv = inputs.rmat_csr(14, 16, seed=3, order=order, weighted=True)
     exp = oracle.transpose(rp, ci, vv)
-    for name in ["atomic", "hdv512_staged", "big_blocks", "radix", "radix2048"]:
+    for name in ["atomic", "hdv512_staged", "big_blocks", "radix", "radix4096", "radix2048"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
     assert_same(gpu_transpose(rp, ci, vv), exp)  # default configuration
+
+
+@pytest.mark.parametrize("m", [1, 4095, 4096, 4097, 8192 * 152 + 4096 * 3 + 17, 4096 * 700])
+def test_radix_tile_boundaries(m):
+    """Edge counts around the 4096-edge tile of the bulk-staged downsweep:
+    one ragged tile, exactly one tile, a ragged last tile after full ones,
+    uneven tiles per CTA, and a whole number of tiles."""
+    n = 3000
+    _, rp, ci, vv = inputs.random_csr(n, m, seed=m % 97, weighted=True, hot=5, hot_frac=0.3)
+    exp = oracle.transpose(rp, ci, vv)
+    assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS["radix"])), exp)
+    assert_same(gpu_transpose(rp, ci, None, config(**CONFIGS["radix"])), oracle.transpose(rp, ci, None))
+
+
+def test_long_parallel_edge_runs_in_split_rows():
+    """A hub row split over many partitions sends 100,000 parallel edges into
+    one long list and 3,000 into another: the tagged runs must come out in
+    CSR order (long runs take the CTA sort paths, not a quadratic one)."""
+    rng = np.random.default_rng(21)
+    n = 6000
+    rows = [np.concatenate([np.full(100000, 7), np.full(3000, 9), rng.integers(0, n, 50000)])]
+    rows += [rng.integers(0, n, rng.integers(0, 40)) for _ in range(n - 1)]
+    for r in rows[1:200]:
+        r[:] = 7 if len(r) else r  # more sources into list 7
+    rp = np.zeros(n + 1, np.uint64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate(rows).astype(np.uint32)
+    vv = rng.standard_normal(len(ci)).astype(np.float32)
+    exp = oracle.transpose(rp, ci, vv)
+    for name in ["atomic", "hdv64", "noagg_staged", "radix"]:
+        assert_same(gpu_transpose(rp, ci, vv, config(**dict(CONFIGS[name], warp_edges=2048))), exp)
+
+
+def test_radix_unaligned_arrays_fall_back():
+    """Arrays that are not 16-byte aligned take the register downsweep."""
+    from paper_2501_06872_gb300 import binding
+    n, rp, ci, vv = inputs.rmat_csr(13, 8, seed=12, order="random", weighted=True)
+    m = len(ci)
+    exp = oracle.transpose(rp, ci, vv)
+    d = torch.device("cuda:0")
+    rpd = torch.from_numpy(rp.view(np.int64)).to(d)
+    ci_big = torch.zeros(m + 1, dtype=torch.int32, device=d)
+    ci_big[1:] = torch.from_numpy(ci.view(np.int32)).to(d)
+    vv_big = torch.zeros(m + 1, dtype=torch.float32, device=d)
+    vv_big[1:] = torch.from_numpy(vv).to(d)
+    cp = torch.empty(n + 1, dtype=torch.int64, device=d)
+    ri_big = torch.empty(m + 1, dtype=torch.int32, device=d)
+    vo_big = torch.empty(m + 1, dtype=torch.float32, device=d)
+    plan = binding.Plan(n, m, True, config(**CONFIGS["radix"]))
+    plan.transpose(rpd, ci_big[1:], vv_big[1:], cp, ri_big[1:], vo_big[1:])
+    plan.check()
+    plan.close()
+    got = (cp.cpu().numpy().view(np.uint64), ri_big[1:].cpu().numpy().view(np.uint32), vo_big[1:].cpu().numpy())
+    assert_same(got, exp)
 
 
 def test_split_rows_with_parallel_edges():
@@ -168,23 +223,21 @@ def test_ragged_edge_counts_and_empty_rows():
             assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
 
 
-def test_errors_are_reported_not_faulted():
+@pytest.mark.parametrize("name", ["atomic", "hdv64", "radix", "radix4096"])
+def test_errors_are_reported_not_faulted(name):
     from paper_2501_06872_gb300 import binding
-    rp = np.array([0, 2, 3, 4], np.uint64)
-    ci = np.array([1, 2, 3, 0], np.uint32)  # 3 >= n
-    with pytest.raises(binding.GtError) as ei:
-        gpu_transpose(rp, ci)
-    assert ei.value.code == 2
-    rp = np.array([0, 3, 2, 4], np.uint64)  # decreasing
-    ci = np.array([1, 2, 0, 0], np.uint32)
-    with pytest.raises(binding.GtError) as ei:
-        gpu_transpose(rp, ci)
-    assert ei.value.code == 3
-    rp = np.array([0, 1, 2, 3], np.uint64)  # row_ptr[n] != m
-    ci = np.array([1, 2, 0, 0], np.uint32)
-    with pytest.raises(binding.GtError) as ei:
-        gpu_transpose(rp, ci)
-    assert ei.value.code == 3
+    cfg = config(**CONFIGS[name])
+    cases = [
+        (np.array([0, 2, 3, 4], np.uint64), np.array([1, 2, 3, 0], np.uint32), 2),  # 3 >= n
+        (np.array([0, 3, 2, 4], np.uint64), np.array([1, 2, 0, 0], np.uint32), 3),  # decreasing
+        (np.array([0, 1, 2, 3], np.uint64), np.array([1, 2, 0, 0], np.uint32), 3),  # row_ptr[n] != m
+        (np.array([1, 2, 3, 4], np.uint64), np.array([1, 2, 0, 0], np.uint32), 3),  # row_ptr[0] != 0
+        (np.array([0, 0, 1, 1], np.uint64), np.zeros(0, np.uint32), 3),             # m = 0, row_ptr not zero
+    ]
+    for rp, ci, code in cases:
+        with pytest.raises(binding.GtError) as ei:
+            gpu_transpose(rp, ci, None, cfg)
+        assert ei.value.code == code, (rp, ci)
 
 
 def test_host_path_matches_device_path():
