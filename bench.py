@@ -33,6 +33,7 @@ WORKLOADS = {
     "rmat16": ("rmat", 16, 16, "natural", False),
     "rmat20-degree": ("rmat", 20, 16, "degree", True),
     "rmat22-degree": ("rmat", 22, 16, "degree", True),
+    "rmat23-degree": ("rmat", 23, 16, "degree", True),
     "rmat24-degree": ("rmat", 24, 16, "degree", True),
     "rmat25-degree": ("rmat", 25, 16, "degree", True),
     "rmat26-degree": ("rmat", 26, 16, "degree", True),
@@ -425,6 +426,10 @@ def main():
             "launches_timed": timing["dominant_launches"], "peak_kind": peak_kind}
     step_gbs = lit / (ms_step * 1e-3) / 1e9
 
+    learned = None
+    if rank == 0:
+        learned = selector_summary(plan, rp, ci, vv, cp, ri, vo, n, m)
+
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = run_e2e(plan, rp, ci, vv, n, m, weighted, args)
@@ -454,11 +459,29 @@ def main():
                 "coverage": stats["hdv_edges"] / max(1, m),
                 "clocks": clk.summary(),
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps,
-                "e2e": e2e, "cpu_baseline": cpu}
+                "learned": learned, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def selector_summary(plan, rp, ci, vv, cp, ri, vo, n, m):
+    """Grid points the learned selector, the analytic model and the default
+    configuration choose for this workload (gt_plan_tune; the plan keeps its
+    configuration), plus the selector's held-out evaluation (regret = time of
+    the chosen grid point / the exhaustive optimum, 64 graphs)."""
+    from paper_2501_06872_gb300 import binding, selector_train
+    keep = plan.config()
+    sel = binding.Selector.pretrained()
+    li, _ = plan.tune(binding.TUNE_LEARNED, rp, ci, vv, cp, ri, vo, selector=sel)
+    ai, _ = plan.tune(binding.TUNE_ANALYTIC, rp, ci, vv, cp, ri, vo)
+    sel.close()
+    plan.set_config(keep)
+    rep = json.load(open(os.path.join(ROOT, "paper_2501_06872_gb300", "selector_report.json")))
+    return {"pick_learned": li, "pick_analytic": ai, "pick_default": selector_train.default_index(n, m),
+            "heldout_regret": {k: rep["test"][k]["mean"] for k in ("learned", "analytic", "default")},
+            "heldout_graphs": rep["n_test"]}
 
 
 def run_e2e(plan, rp, ci, vv, n, m, weighted, args):

@@ -430,6 +430,14 @@ class Selector:
         _check(self._lib.gt_selector_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps),
                                                _stream(stream)), "gt_selector_adam_step")
 
+    @classmethod
+    def pretrained(cls):
+        """The selector trained by selector_train.py on the library's own
+        timings (parameters shipped beside this module)."""
+        import numpy as np
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_params.f32")
+        return cls(np.fromfile(path, dtype="<f4"))
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gt_selector_destroy(self._h)

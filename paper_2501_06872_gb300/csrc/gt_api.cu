@@ -163,7 +163,8 @@ gt_status plan_alloc_ws(gt_plan p) {
     w.r_gap_cap = (uint32_t)(n / 1024 + 2);
     GT_AL(r_gaps, (1 + 2 * (size_t)w.r_gap_cap) * 8);
     GT_AL(r_nlong, 4);
-    const size_t rows = w.rG > (uint32_t)w.num_sms * 4u ? w.rG : (size_t)w.num_sms * 4u;  // bulk: sms x 4 sub-CTAs
+    // bulk-staged passes: up to 4 CTAs per SM x 2 sub-CTAs of the upsweep
+    const size_t rows = w.rG > (uint32_t)w.num_sms * 8u ? w.rG : (size_t)w.num_sms * 8u;
     GT_AL(r_table, rows * 256 * 4);
     GT_AL(r_offsets, rows * 256 * 8);
     if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;

@@ -232,11 +232,13 @@ gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_
       GT_BA(a_w, M * 4);
       GT_BA(b_w, M * 4);
     }
-    GT_BA(deg, NV * 4);
     GT_BA(ucp, (NV + 1) * 8);
-    GT_BA(scan_state, ((NV + gt::kScanTile - 1) / gt::kScanTile + 1) * 8);
-    GT_BA(table, (size_t)bw.rG * 256 * 4);
-    GT_BA(offsets, (size_t)bw.rG * 256 * 8);
+    // rows: the register passes' CTAs, or the bulk passes' CTAs (up to 4 per SM) x 2 sub-CTAs
+    const size_t rows = bw.rG > (uint32_t)bw.num_sms * 8u ? bw.rG : (size_t)bw.num_sms * 8u;
+    GT_BA(table, rows * 256 * 4);
+    GT_BA(offsets, rows * 256 * 8);
+    bw.gap_cap = (uint32_t)(NV / 1024 + 2);
+    GT_BA(gaps, (1 + 2 * (size_t)bw.gap_cap) * 8);
     GT_BA(long_g, (size_t)bw.long_cap * 4);
     GT_BA(long_r, (size_t)bw.long_cap * 4);
     GT_BA(n_long, 4);

@@ -114,13 +114,13 @@ struct BatchWork {
   uint32_t rG = 0, r_items = 16;
   uint32_t *a_key = nullptr, *a_u = nullptr, *a_w = nullptr;  // [max m]
   uint32_t *b_key = nullptr, *b_u = nullptr, *b_w = nullptr;  // [max m]
-  uint32_t *deg = nullptr;                                      // [max nv]
   unsigned long long *ucp = nullptr;                            // [max nv + 1]
-  unsigned long long *scan_state = nullptr;                     // [max nv tiles]
   uint32_t *table = nullptr;                                    // [rG][256]
   unsigned long long *offsets = nullptr;                        // [rG][256]
   uint32_t *long_g = nullptr, *long_r = nullptr, *n_long = nullptr;
   uint32_t long_cap = 0;
+  unsigned long long *gaps = nullptr;  // [1 + 2 * gap_cap] long col_ptr ranges
+  uint32_t gap_cap = 0;
   uint32_t *status = nullptr, *meta = nullptr;
 };
 

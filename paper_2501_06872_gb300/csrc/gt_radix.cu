@@ -425,18 +425,21 @@ constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBItems = 16;
 constexpr uint32_t kBTile = kBThreads * kBItems;
-constexpr uint32_t kBCtasPerSm = 2;
+constexpr uint32_t kBCtasPerSm = 2;  // registers (~120 x 256 threads) and 2 x ~109 KB of shared memory
 
 __host__ __device__ constexpr uint32_t bulk_arrays(bool vals) { return vals ? 3u : 2u; }
 __host__ constexpr size_t bulk_dyn_smem(bool vals) { return (size_t)2 * bulk_arrays(vals) * kBTile * 4; }
 
-template <bool VALS>
+template <bool VALS, int MODE>
 __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(RadixArgs a) {
+  static_assert(!loads_batch(MODE), "the bulk downsweep reads plain arrays");
+  constexpr int ITEMS = kBItems;
   constexpr uint32_t NA = bulk_arrays(VALS);
   extern __shared__ __align__(128) uint32_t dsm[];  // buf[2][NA][TILE]
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t wcnt[kBWarps][kRBins];
   __shared__ unsigned long long run_off[kRBins];
+  __shared__ unsigned long long dst_base[kRBins];  // run_off[d] - tile_start[d] of the current tile
   __shared__ uint32_t tile_start[kRBins];
   __shared__ uint32_t wsum[kBWarps];
   __shared__ uint32_t s_abort;
@@ -508,8 +511,8 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       ww[i] = (VALS && act) ? bw[j] : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < kBItems; ++i) {
-      const bool act = w * (kBItems * 32) + i * 32 + lane < tcount;
+    for (int i = 0; i < ITEMS; ++i) {
+      const bool act = w * (ITEMS * 32) + i * 32 + lane < tcount;
       const uint32_t d = (key[i] >> a.shift) & mask;
       const uint32_t mm = match_digit(d, a.dbits, act);
       const uint32_t r = __popc(mm & lanemask_lt());
@@ -544,6 +547,7 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
 #pragma unroll
       for (int x = 0; x < kBWarps; ++x) before += (x < (int)w) ? wsum[x] : 0u;
       tile_start[tid] = before + inc - tot;
+      dst_base[tid] = run_off[tid] - (before + inc - tot);
     }
     __syncthreads();
     // back into the same buffer in (digit, rank) order
@@ -558,26 +562,27 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       }
     }
     __syncthreads();
+    auto put = [&](uint32_t j) {
+      const uint32_t k = bk[j];
+      const uint32_t d = (k >> a.shift) & mask;
+      const uint64_t pos = dst_base[d] + j;
+      a.out_key[pos] = k;
+      if (stores_batch(MODE)) {  // the last pass of a batch stores through the graph's descriptor
+        const uint32_t g = k >> a.batch.vbits;
+        const gt_graph_desc &gd = a.batch.descs[g];
+        const uint64_t lp = pos - a.batch.eoff[g];
+        gd.row_idx[lp] = bu[j];
+        if (VALS) gd.vals_out[lp] = __uint_as_float(bw[j]);
+      } else {
+        a.out_u[pos] = bu[j];
+        if (VALS) a.out_w[pos] = bw[j];
+      }
+    };
     if (tcount == kBTile) {
 #pragma unroll 4
-      for (int q = 0; q < kBItems; ++q) {
-        const uint32_t j = q * kBThreads + tid;
-        const uint32_t k = bk[j];
-        const uint32_t d = (k >> a.shift) & mask;
-        const uint64_t pos = run_off[d] + (j - tile_start[d]);
-        a.out_key[pos] = k;
-        a.out_u[pos] = bu[j];
-        if (VALS) a.out_w[pos] = bw[j];
-      }
+      for (int q = 0; q < kBItems; ++q) put(q * kBThreads + tid);
     } else {
-      for (uint32_t j = tid; j < tcount; j += kBThreads) {
-        const uint32_t k = bk[j];
-        const uint32_t d = (k >> a.shift) & mask;
-        const uint64_t pos = run_off[d] + (j - tile_start[d]);
-        a.out_key[pos] = k;
-        a.out_u[pos] = bu[j];
-        if (VALS) a.out_w[pos] = bw[j];
-      }
+      for (uint32_t j = tid; j < tcount; j += kBThreads) put(j);
     }
     __syncthreads();
     run_off[tid] += tot;
@@ -631,9 +636,22 @@ __device__ __forceinline__ void colptr_range(uint64_t a, uint64_t b, uint64_t va
   }
 }
 
+// Key -> position in the col_ptr space: the key itself (clamped to n), or,
+// for a batch, the compact union index voff[graph] + vertex (clamped to the
+// graph's vertex count), which is monotone in the key.
+template <bool BATCH>
+__device__ __forceinline__ uint32_t cp_index(uint32_t k, uint32_t n, const BatchView &bv) {
+  if (!BATCH) return min(k, n);
+  const uint32_t g = k >> bv.vbits;
+  if (g >= bv.ng) return n;
+  const uint32_t v = k & ((1u << bv.vbits) - 1u);
+  return (uint32_t)(bv.voff[g] + min(v, bv.descs[g].n_vertices));
+}
+
+template <bool BATCH>
 __global__ void __launch_bounds__(256) k_radix_colptr(const uint32_t *__restrict__ key, uint64_t m, uint32_t n,
                                                       uint64_t *col_ptr, unsigned long long *gaps, uint32_t gap_cap,
-                                                      uint32_t *status) {
+                                                      uint32_t *status, BatchView bv) {
   __shared__ uint32_t sk[8][kCpChunk];
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
   uint32_t *ck = sk[w];
@@ -643,10 +661,10 @@ __global__ void __launch_bounds__(256) k_radix_colptr(const uint32_t *__restrict
 #pragma unroll
     for (int i = 0; i < (int)(kCpChunk / 32); ++i) {
       const uint32_t j = i * 32 + lane;
-      ck[j] = j < cnt ? min(__ldcs(key + c + j), n) : 0xFFFFFFFFu;
+      ck[j] = j < cnt ? cp_index<BATCH>(__ldcs(key + c + j), n, bv) : 0xFFFFFFFFu;
     }
     __syncwarp();
-    const uint64_t lo = c == 0 ? 0 : (uint64_t)min(key[c - 1], n) + 1;
+    const uint64_t lo = c == 0 ? 0 : (uint64_t)cp_index<BATCH>(key[c - 1], n, bv) + 1;
     const uint64_t hi = (c + cnt == m) ? (uint64_t)n : (uint64_t)ck[cnt - 1];
     if (hi + 1 <= lo + kChunkRange) {
       for (uint64_t v = lo + lane; v <= hi; v += 32) {
@@ -697,17 +715,6 @@ __global__ void k_radix_gaps(const unsigned long long *__restrict__ gaps, uint32
   }
 }
 
-// Degrees from the runs of equal keys in the sorted key array:
-// deg[k] = (end of run) - (start of run), via two wrapping adds.
-__global__ void k_radix_runs(const uint32_t *__restrict__ key, uint64_t m, uint32_t n, uint32_t *deg) {
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = key[p];
-    if (k >= n) continue;
-    if (p == 0 || key[p - 1] != k) red_add_u32(&deg[k], (uint32_t)(0u - (uint32_t)p));
-    if (p + 1 == m || key[p + 1] != k) red_add_u32(&deg[k], (uint32_t)(p + 1));
-  }
-}
-
 // ---------------------------------------------------------------------------
 
 static uint32_t key_bits_of(uint32_t n) {
@@ -729,9 +736,13 @@ cudaError_t configure_radix() {
                       allow_down<8, kBatchOnly>(),   allow_down<16, kBatchOnly>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
-  cudaError_t b1 = allow_max_dynamic_smem(k_radix_down_bulk<true>);
-  cudaError_t b2 = allow_max_dynamic_smem(k_radix_down_bulk<false>);
-  return b1 != cudaSuccess ? b1 : b2;
+  cudaError_t b[4] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<false, kPlain>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<true, kBatchLast>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<false, kBatchLast>)};
+  for (cudaError_t x : b)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 
 template <int MODE>
@@ -794,8 +805,8 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G * sub, w.r_offsets);
     if (ev && ev->ndown + 2 <= 8) cudaEventRecord(ev->down[ev->ndown], s);
     if (bulk) {
-      if (vals) k_radix_down_bulk<true><<<G, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-      else k_radix_down_bulk<false><<<G, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+      if (vals) k_radix_down_bulk<true, kPlain><<<G, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else k_radix_down_bulk<false, kPlain><<<G, kBThreads, bulk_dyn_smem(false), s>>>(ra);
     } else {
       const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
       launch_down<kPlain>(vals, items, G, dsm, s, ra);
@@ -811,7 +822,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     in_w = ow;
   }
   uint32_t g = (uint32_t)min64((m + 255) / 256, (uint64_t)w.num_sms * 16);
-  k_radix_colptr<<<g, 256, 0, s>>>(w.r_b_key, m, n, pb.col_ptr, w.r_gaps, w.r_gap_cap, w.status);
+  k_radix_colptr<false><<<g, 256, 0, s>>>(w.r_b_key, m, n, pb.col_ptr, w.r_gaps, w.r_gap_cap, w.status, BatchView{});
   k_radix_gaps<<<w.num_sms * 4, 256, 0, s>>>(w.r_gaps, w.r_gap_cap, pb.col_ptr);
   nl += 2;
   if (launches) *launches += nl;
@@ -895,20 +906,7 @@ __global__ void k_b_expand_long(BatchView bv, const uint32_t *__restrict__ long_
   }
 }
 
-// Degrees of the union vertices from the runs of equal sorted keys.
-__global__ void k_b_runs(BatchView bv, const uint32_t *__restrict__ key, uint64_t m, uint32_t *deg) {
-  const uint32_t vmask = (1u << bv.vbits) - 1u;
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = key[p];
-    const uint32_t g = k >> bv.vbits, v = k & vmask;
-    if (g >= bv.ng || v >= bv.descs[g].n_vertices) continue;
-    uint32_t *dv = deg + bv.voff[g] + v;
-    if (p == 0 || key[p - 1] != k) red_add_u32(dv, (uint32_t)(0u - (uint32_t)p));
-    if (p + 1 == m || key[p + 1] != k) red_add_u32(dv, (uint32_t)(p + 1));
-  }
-}
-
-// col_ptr of every graph from the union exclusive scan (and the last entry).
+// col_ptr of every graph from the union col_ptr (and the last entry).
 __global__ void k_b_colptr(BatchView bv, const unsigned long long *__restrict__ ucp, uint64_t nv) {
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nv + bv.ng;
        x += (uint64_t)gridDim.x * blockDim.x) {
@@ -934,9 +932,6 @@ cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_
   const uint32_t G = bw.rG;
   const uint32_t tpc = ntiles ? (ntiles + G - 1) / G : 0;
   const uint32_t passes = sb.passes, dbits = sb.dbits;
-  const uint32_t stiles = (sb.nv + kScanTile - 1) / kScanTile;
-  if ((err = cudaMemsetAsync(bw.deg, 0, (size_t)sb.nv * 4, s)) != cudaSuccess) return err;
-  if ((err = cudaMemsetAsync(bw.scan_state, 0, (size_t)stiles * 8, s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(bw.meta, 0, kMetaCount * 4, s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(bw.n_long, 0, 4, s)) != cudaSuccess) return err;
   k_b_check<<<(sb.ng + 255) / 256, 256, 0, s>>>(bv, bw.status);
@@ -951,35 +946,47 @@ cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_
     k_b_expand_long<<<bw.num_sms * 4, 256, 0, s>>>(bv, bw.long_g, bw.long_r, bw.n_long, bw.long_cap, src_rows);
     nl += 2;
     const uint32_t *in_key = nullptr, *in_u = src_rows, *in_w = nullptr;
+    // the first pass reads through the descriptors (register tiles); later
+    // passes read the workspace with the bulk-staged downsweep
+    const uint32_t Gb = (uint32_t)bw.num_sms * kBCtasPerSm, subb = 2;
+    const uint32_t ntb = (uint32_t)((m + kBTile - 1) / kBTile), tpcb = (ntb + Gb - 1) / Gb;
     for (uint32_t p = 1; p <= passes; ++p) {
       const bool toB = ((passes - p) % 2) == 0;
       uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
+      const bool bulk = p > 1;
       RadixArgs ra{nullptr, nullptr, nullptr, 0, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
-                   (p - 1) * dbits, dbits, ntiles, tpc, tile, bw.table, bw.offsets, bw.status, bv};
+                   (p - 1) * dbits, dbits, bulk ? ntb : ntiles, bulk ? tpcb : tpc, bulk ? kBTile : tile,
+                   bw.table, bw.offsets, bw.status, bv, bulk ? subb : 1u};
+      const uint32_t Gp = bulk ? Gb : G, rows = bulk ? Gb * subb : G;
       if (p == 1) k_radix_up<true, kBatchFirst><<<G, kRThreads, 0, s>>>(ra);
-      else k_radix_up<false, kPlain><<<G, kRThreads, 0, s>>>(ra);
-      k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, G, bw.offsets);
+      else k_radix_up<false, kPlain><<<rows, kRThreads, 0, s>>>(ra);
+      k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, rows, bw.offsets);
       const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
       if (p == 1 && p == passes) launch_down<kBatchOnly>(vals, items, G, dsm, s, ra);
       else if (p == 1) launch_down<kBatchFirst>(vals, items, G, dsm, s, ra);
-      else if (p == passes) launch_down<kBatchLast>(vals, items, G, dsm, s, ra);
-      else launch_down<kPlain>(vals, items, G, dsm, s, ra);
+      else if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gp, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gp, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+      else if (vals) k_radix_down_bulk<true, kPlain><<<Gp, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else k_radix_down_bulk<false, kPlain><<<Gp, kBThreads, bulk_dyn_smem(false), s>>>(ra);
       nl += 3;
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       in_key = ok;
       in_u = ou;
       in_w = ow;
     }
+    // union col_ptr straight from the sorted keys (compact vertex space)
     uint32_t gr = (uint32_t)min64((m + 255) / 256, (uint64_t)bw.num_sms * 16);
-    k_b_runs<<<gr, 256, 0, s>>>(bv, bw.b_key, m, bw.deg);
-    ++nl;
-  }
-  if ((err = launch_scan(bw.deg, sb.nv, m, nullptr, (uint64_t *)bw.ucp, nullptr, bw.scan_state, stiles, bw.meta, bw.status, s)) !=
-      cudaSuccess)
+    if ((err = cudaMemsetAsync(bw.gaps, 0, 8, s)) != cudaSuccess) return err;
+    k_radix_colptr<true><<<gr, 256, 0, s>>>(bw.b_key, m, sb.nv, (uint64_t *)bw.ucp, bw.gaps, bw.gap_cap, bw.status,
+                                            bv);
+    k_radix_gaps<<<bw.num_sms * 4, 256, 0, s>>>(bw.gaps, bw.gap_cap, (uint64_t *)bw.ucp);
+    nl += 2;
+  } else if ((err = cudaMemsetAsync(bw.ucp, 0, ((size_t)sb.nv + 1) * 8, s)) != cudaSuccess) {
     return err;
+  }
   uint32_t gc = (uint32_t)min64((sb.nv + sb.ng + 255) / 256, (uint64_t)bw.num_sms * 16);
   k_b_colptr<<<gc, 256, 0, s>>>(bv, bw.ucp, sb.nv);
-  nl += 2;
+  ++nl;
   if (launches) *launches += nl;
   return cudaGetLastError();
 }

@@ -193,3 +193,37 @@ def test_tune_reports_bad_input():
         plan.tune(binding.TUNE_EXHAUSTIVE, rpd, cid, None, cp, ri, None, reps=1)
     assert e.value.code == 2
     plan.close()
+
+
+def _heldout():
+    import json
+    import paper_2501_06872_gb300 as pkg
+    root = os.path.dirname(pkg.__file__)
+    d = np.load(os.path.join(root, "selector_dataset.npz"), allow_pickle=False)
+    rep = json.load(open(os.path.join(root, "selector_report.json")))
+    meta = json.loads(str(d["meta"]))
+    n_train = rep["n_train"]
+    return d["features"][n_train:], d["times"][n_train:], meta[n_train:], rep
+
+
+def _regret(times, idx):
+    best = np.where(times > 0, times, np.inf).min(axis=1)
+    return times[np.arange(len(idx)), idx] / best
+
+
+def test_trained_selector_gains_over_the_method_without_it():
+    """On the 64 held-out graphs (timed by the exhaustive autotuner), the
+    trained network's picks, run through the library's forward kernels, have
+    a lower mean regret than the default configuration (the method without
+    the selector) and than the analytic model."""
+    from paper_2501_06872_gb300 import binding
+    feats, times, meta, rep = _heldout()
+    sel = binding.Selector.pretrained()
+    scores = sel.forward(torch.from_numpy(feats.astype(np.float32)).cuda()).cpu().numpy()
+    sel.close()
+    learned = _regret(times, scores.argmin(axis=1)).mean()
+    default = _regret(times, np.array([m["default"] for m in meta])).mean()
+    analytic = _regret(times, np.array([m["analytic"] for m in meta])).mean()
+    assert learned == pytest.approx(rep["test"]["learned"]["mean"], rel=1e-6)
+    assert learned < default
+    assert learned < analytic

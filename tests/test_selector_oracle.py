@@ -191,3 +191,22 @@ def test_adam_first_step_closed_form():
     assert np.allclose(p1, p - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
     p2, _, _ = so.adam(p, g, z, z, 1, lr, first=10)
     assert np.array_equal(p2[:10], p[:10])
+
+
+def test_shipped_selector_report_reproduces_in_fp64():
+    """The committed report's held-out regret follows from the committed
+    parameters and dataset through the fp64 oracle forward pass."""
+    import json
+    import paper_2501_06872_gb300 as pkg
+    root = os.path.dirname(pkg.__file__)
+    d = np.load(os.path.join(root, "selector_dataset.npz"), allow_pickle=False)
+    rep = json.load(open(os.path.join(root, "selector_report.json")))
+    p = np.fromfile(os.path.join(root, "selector_params.f32"), dtype="<f4").astype(np.float64)
+    assert p.size == so.layout()["total"]
+    n_train = rep["n_train"]
+    f, t = d["features"][n_train:].astype(np.float64), d["times"][n_train:]
+    y, _ = so.forward(p, f)
+    idx = y.argmin(axis=1)
+    best = np.where(t > 0, t, np.inf).min(axis=1)
+    reg = t[np.arange(len(idx)), idx] / best
+    assert reg.mean() == pytest.approx(rep["test"]["learned"]["mean"], rel=1e-6)
