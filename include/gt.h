@@ -270,10 +270,13 @@ typedef struct gt_selector_s *gt_selector;
 /* Learned selector: an MLP GT_N_FEATURES -> 64 -> 64 -> GT_TUNE_GRID (ReLU),
  * f32, on the device.  Parameter vector (gt_selector_param_count floats):
  * mu[F], sd[F] (input standardisation, x' = (x - mu) / sd, not trained),
- * W1[64][F], b1[64], W2[64][64], b2[64], W3[K][64], b3[K].  Output i is a
- * score for grid point i; the learned mode takes the smallest.
- * host_params == NULL: mu = 0, sd = 1, weights uniform in +-sqrt(6/fan_in)
- * from SplitMix64(seed), biases 0. */
+ * lo[F], hi[F] (the feature range of the training graphs, not trained and
+ * not used by the network), W1[64][F], b1[64], W2[64][64], b2[64],
+ * W3[K][64], b3[K].  Output i is a score for grid point i; the learned mode
+ * takes the smallest, except for a graph whose features leave [lo, hi]
+ * (widened by 5 % of its width), where it takes the analytic choice.
+ * host_params == NULL: mu = 0, sd = 1, unbounded range, weights uniform in
+ * +-sqrt(6/fan_in) from SplitMix64(seed), biases 0. */
 uint64_t gt_selector_param_count(void);
 gt_status gt_selector_create(gt_selector *sel, const float *host_params, uint64_t seed);
 gt_status gt_selector_get_params(gt_selector sel, float *host_params);
@@ -288,6 +291,9 @@ gt_status gt_selector_forward(gt_selector sel, const float *features, uint32_t b
  * f32[param_count], mu/sd entries 0) are optional copies. */
 gt_status gt_selector_backward(gt_selector sel, const float *features, const float *target, const float *mask,
                                uint32_t batch, float *loss, float *grads, void *stream);
+/* *in_range = 1 if host features (F floats) lie in the selector's trained
+ * range (widened by 5 % of its width), else 0. */
+gt_status gt_selector_in_range(gt_selector sel, const float *host_features, int *in_range);
 /* One Adam step (bias-corrected) with the last gradients on W and b. */
 gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float beta2, float eps, void *stream);
 void gt_selector_destroy(gt_selector sel);
@@ -295,13 +301,14 @@ void gt_selector_destroy(gt_selector sel);
 typedef struct gt_tune_entry {
     gt_config cfg;    /* grid point                                           */
     float ms;         /* exhaustive: median device time of the timed calls; -1 if not run */
-    float score;      /* learned: the selector's score                        */
+    float score;      /* learned: the selector's score (computed even when the
+                         graph is outside the trained range)                */
     int32_t status;   /* gt_status of this point's run                        */
 } gt_tune_entry;
 
 #define GT_TUNE_ANALYTIC 0    /* features + gt_tune_analytic                  */
 #define GT_TUNE_EXHAUSTIVE 1  /* time every grid point (1 warm-up + reps calls) */
-#define GT_TUNE_LEARNED 2     /* features + selector, smallest score           */
+#define GT_TUNE_LEARNED 2     /* features + selector, smallest score (analytic outside its range) */
 
 /* Chooses a configuration for the plan's graph and installs it
  * (gt_plan_set_config).  The exhaustive mode runs real transpositions into

@@ -113,8 +113,10 @@ def features(n: int, m: int, row_ptr, col_idx, has_vals: bool, seed: int) -> np.
 # ---- selector network ---------------------------------------------------------
 
 def layout(F: int = N_FEATURES, H: int = HIDDEN, K: int = GRID):
-    """Offsets of mu, sd, W1, b1, W2, b2, W3, b3 in the flat parameter vector."""
-    sizes = [("mu", F), ("sd", F), ("W1", H * F), ("b1", H), ("W2", H * H), ("b2", H), ("W3", K * H), ("b3", K)]
+    """Offsets of mu, sd, lo, hi, W1, b1, W2, b2, W3, b3 in the flat parameter
+    vector (lo, hi: the training feature range, unused by the network)."""
+    sizes = [("mu", F), ("sd", F), ("lo", F), ("hi", F), ("W1", H * F), ("b1", H), ("W2", H * H), ("b2", H),
+             ("W3", K * H), ("b3", K)]
     out, off = {}, 0
     for name, size in sizes:
         out[name] = (off, size)
@@ -155,7 +157,7 @@ def loss(p, X, T, M, F=N_FEATURES, H=HIDDEN, K=GRID):
 
 
 def backward(p, X, T, M, F=N_FEATURES, H=HIDDEN, K=GRID):
-    """(loss, gradient vector in the parameter layout; mu and sd get 0).
+    """(loss, gradient vector in the parameter layout; mu, sd, lo, hi get 0).
     The ReLU derivative is taken as 1 where the pre-activation is > 0."""
     mu, sd, W1, b1, W2, b2, W3, b3 = unpack(p, F, H, K)
     y, (xn, a1, h1, a2, h2) = forward(p, X, F, H, K)

@@ -94,7 +94,7 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_batch_plan_destroy", "gt_graph_features", "gt_tune_grid_config", "gt_tune_analytic",
            "gt_selector_param_count", "gt_selector_create", "gt_selector_get_params", "gt_selector_set_params",
            "gt_selector_forward", "gt_selector_backward", "gt_selector_adam_step", "gt_selector_destroy",
-           "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges"]
+           "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges", "gt_selector_in_range"]
 
 N_FEATURES = 41
 TUNE_GRID = 12
@@ -144,6 +144,7 @@ def load():
     lib.gt_selector_forward.argtypes = [P, P, u32, P, P]
     lib.gt_selector_backward.argtypes = [P, P, P, P, u32, P, P, P]
     lib.gt_selector_adam_step.argtypes = [P, F, F, F, F, P]
+    lib.gt_selector_in_range.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     lib.gt_selector_destroy.argtypes = [P]
     lib.gt_selector_destroy.restype = None
     lib.gt_plan_tune.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, u32, ctypes.POINTER(TuneEntry),
@@ -154,7 +155,7 @@ def load():
     lib.gt_plan_edges.restype = u64
     for f in ["gt_graph_features", "gt_tune_grid_config", "gt_tune_analytic", "gt_selector_create",
               "gt_selector_get_params", "gt_selector_set_params", "gt_selector_forward", "gt_selector_backward",
-              "gt_selector_adam_step", "gt_plan_tune"]:
+              "gt_selector_adam_step", "gt_plan_tune", "gt_selector_in_range"]:
         getattr(lib, f).restype = ctypes.c_int
     lib.gt_plan_enable_timing.argtypes = [P, ctypes.c_int]
     lib.gt_plan_timing.argtypes = [P, ctypes.POINTER(Timing)]
@@ -425,6 +426,14 @@ class Selector:
         b = features.shape[0]
         _check(self._lib.gt_selector_backward(self._h, _ptr(features), _ptr(target), _ptr(mask), b, _ptr(loss),
                                               _ptr(grads), _stream(stream)), "gt_selector_backward")
+
+    def in_range(self, features_host) -> bool:
+        import numpy as np
+        f = np.ascontiguousarray(features_host, dtype=np.float32)
+        ok = ctypes.c_int()
+        _check(self._lib.gt_selector_in_range(self._h, ctypes.c_void_p(f.ctypes.data), ctypes.byref(ok)),
+               "gt_selector_in_range")
+        return bool(ok.value)
 
     def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         _check(self._lib.gt_selector_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps),

@@ -5,6 +5,7 @@
 // None of this touches the transposition's integer arithmetic: a configuration
 // only changes speed, never the output bytes.
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -33,7 +34,9 @@ constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 // Parameter vector layout of the selector (floats).
 constexpr uint32_t kOffMu = 0;
 constexpr uint32_t kOffSd = kOffMu + kNF;
-constexpr uint32_t kOffW1 = kOffSd + kNF;
+constexpr uint32_t kOffLo = kOffSd + kNF;  // trained feature range (not used by the network)
+constexpr uint32_t kOffHi = kOffLo + kNF;
+constexpr uint32_t kOffW1 = kOffHi + kNF;
 constexpr uint32_t kOffB1 = kOffW1 + kH * kNF;
 constexpr uint32_t kOffW2 = kOffB1 + kH;
 constexpr uint32_t kOffB2 = kOffW2 + kH * kH;
@@ -319,6 +322,7 @@ using namespace gt;
 
 struct gt_selector_s {
   int device = 0;
+  float lo[GT_N_FEATURES], hi[GT_N_FEATURES];  // host copy of the trained feature range
   float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
   uint32_t steps = 0;
   uint32_t cap = 0;  // batch capacity of the activation buffers
@@ -438,8 +442,12 @@ gt_status gt_selector_create(gt_selector *sel, const float *host_params, uint64_
   if (host_params) {
     memcpy(p.data(), host_params, kParams * 4);
   } else {
-    // mu = 0, sd = 1; weights uniform in +-sqrt(6 / fan_in) (He), biases 0
-    for (uint32_t f = 0; f < kNF; ++f) p[kOffSd + f] = 1.f;
+    // mu = 0, sd = 1, unbounded range; weights uniform in +-sqrt(6 / fan_in) (He), biases 0
+    for (uint32_t f = 0; f < kNF; ++f) {
+      p[kOffSd + f] = 1.f;
+      p[kOffLo + f] = -FLT_MAX;
+      p[kOffHi + f] = FLT_MAX;
+    }
     uint64_t ctr = 0;
     auto fill = [&](uint32_t off, uint32_t count, uint32_t fan_in) {
       const double lim = sqrt(6.0 / fan_in);
@@ -452,6 +460,8 @@ gt_status gt_selector_create(gt_selector *sel, const float *host_params, uint64_
     fill(kOffW2, kH * kH, kH);
     fill(kOffW3, kK * kH, kH);
   }
+  memcpy(s->lo, p.data() + kOffLo, sizeof(s->lo));
+  memcpy(s->hi, p.data() + kOffHi, sizeof(s->hi));
   cudaError_t e = cudaMemcpy(s->params, p.data(), kParams * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->grads, 0, kParams * 4);
   if (e == cudaSuccess) e = cudaMemset(s->m1, 0, kParams * 4);
@@ -472,9 +482,12 @@ gt_status gt_selector_get_params(gt_selector sel, float *host_params) {
 gt_status gt_selector_set_params(gt_selector sel, const float *host_params) {
   if (!sel || !host_params) return GT_ERR_INVALID_ARG;
   for (uint32_t f = 0; f < kNF; ++f)
-    if (!(host_params[kOffSd + f] > 0.f)) return GT_ERR_INVALID_ARG;
+    if (!(host_params[kOffSd + f] > 0.f) || !(host_params[kOffLo + f] <= host_params[kOffHi + f]))
+      return GT_ERR_INVALID_ARG;
   gt_status st = cuda_status(cudaMemcpy(sel->params, host_params, kParams * 4, cudaMemcpyHostToDevice));
   if (st != GT_OK) return st;
+  memcpy(sel->lo, host_params + kOffLo, sizeof(sel->lo));
+  memcpy(sel->hi, host_params + kOffHi, sizeof(sel->hi));
   sel->steps = 0;
   cudaMemset(sel->m1, 0, kParams * 4);
   cudaMemset(sel->m2, 0, kParams * 4);
@@ -517,7 +530,7 @@ gt_status gt_selector_backward(gt_selector sel, const float *features, const flo
   k_dense_bwd_w<<<blocks((uint64_t)kH * (kNF + 1), 128), 128, 0, s>>>(sel->d1, sel->xn, B, kNF, kH, g + kOffW1,
                                                                         g + kOffB1);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, (size_t)kOffW1 * 4, s);  // mu, sd are not trained
+  if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, (size_t)kOffW1 * 4, s);  // mu, sd, lo, hi are not trained
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, sel->loss, 4, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && grads) e = cudaMemcpyAsync(grads, g, (size_t)kParams * 4, cudaMemcpyDeviceToDevice, s);
   return cuda_status(e);
@@ -533,6 +546,19 @@ gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float be
   k_adam<<<blocks(kParams - kOffW1, 256), 256, 0, s>>>(sel->params, sel->grads, sel->m1, sel->m2, kOffW1, kParams, lr,
                                                        beta1, beta2, eps, bc1, bc2);
   return cuda_status(cudaGetLastError());
+}
+
+gt_status gt_selector_in_range(gt_selector sel, const float *host_features, int *in_range) {
+  if (!sel || !host_features || !in_range) return GT_ERR_INVALID_ARG;
+  // the trained range widened by 5 % of its width on each side
+  int ok = 1;
+  for (uint32_t f = 0; f < kNF; ++f) {
+    const double lo = sel->lo[f], hi = sel->hi[f];
+    const double pad = 0.05 * (hi - lo) + 1e-6;
+    if (host_features[f] < lo - pad || host_features[f] > hi + pad) ok = 0;
+  }
+  *in_range = ok;
+  return GT_OK;
 }
 
 void gt_selector_destroy(gt_selector sel) {
@@ -737,8 +763,10 @@ extern "C" gt_status gt_plan_tune(gt_plan plan, int mode, gt_selector sel, const
     if (st == GT_OK) st = cuda_status(cudaStreamSynchronize(s));
     cudaFreeAsync(feat, s);
     if (st != GT_OK) return st;
-    if (mode == GT_TUNE_ANALYTIC) {
-      st = gt_tune_analytic(hf, n, m, &pick);
+    int in_range = 1;
+    if (mode == GT_TUNE_LEARNED) gt_selector_in_range(sel, hf, &in_range);
+    if (mode == GT_TUNE_ANALYTIC || !in_range) {
+      st = gt_tune_analytic(hf, n, m, &pick);  // outside the trained range the analytic model decides
     } else {
       pick = 0;
       for (uint32_t i = 1; i < kK; ++i)

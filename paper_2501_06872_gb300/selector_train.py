@@ -127,6 +127,8 @@ def train(feats, times, steps=4000, lr=3e-3, seed=7, val=None, every=250, log=pr
     F = binding.N_FEATURES
     p[:F] = mu
     p[F:2 * F] = sd
+    p[2 * F:3 * F] = feats.min(axis=0)
+    p[3 * F:4 * F] = feats.max(axis=0)
     sel.set_params(p)
     y, mask = targets(times)
     X = torch.from_numpy(feats.astype(np.float32)).cuda()
@@ -154,13 +156,28 @@ def train(feats, times, steps=4000, lr=3e-3, seed=7, val=None, every=250, log=pr
     return params, hist, best[1] if Xv is not None else steps
 
 
-def picks(params, feats):
+def picks(params, feats, analytic=None):
+    """Grid points the learned mode picks: the smallest score, or the analytic
+    choice for graphs outside the trained feature range."""
     import torch
     from . import binding
     sel = binding.Selector(params)
     s = sel.forward(torch.from_numpy(feats.astype(np.float32)).cuda()).cpu().numpy()
+    idx = s.argmin(axis=1)
+    if analytic is not None:
+        for i in range(len(idx)):
+            if not sel.in_range(feats[i]):
+                idx[i] = analytic[i]
     sel.close()
-    return s.argmin(axis=1), s
+    return idx, s
+
+
+def _in_range(params, f):
+    from . import binding
+    sel = binding.Selector(params)
+    ok = sel.in_range(f)
+    sel.close()
+    return ok
 
 
 def regrets(times, idx):
@@ -185,6 +202,7 @@ def main():
     ap.add_argument("--val", type=int, default=32, help="training graphs held out for checkpoint choice")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--dataset", default=None, help="reuse a dataset.npz instead of timing")
+    ap.add_argument("--params", default=None, help="with --dataset: evaluate these parameters, no training")
     args = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
@@ -205,13 +223,22 @@ def main():
     te = slice(args.train, len(feats))
     fit = slice(0, args.train - args.val)
     va = slice(args.train - args.val, args.train)
-    params, hist, chosen_step = train(feats[fit], times[fit], steps=args.steps,
-                                      val=(feats[va], times[va]) if args.val else None, log=log)
+    if args.params:
+        params = np.fromfile(args.params, dtype="<f4")
+        hist, chosen_step = [], None
+        if args.dataset:
+            old = os.path.join(os.path.dirname(os.path.abspath(args.dataset)), "selector_report.json")
+            if os.path.exists(old):
+                prev = json.load(open(old))
+                hist, chosen_step = prev.get("loss", []), prev.get("chosen_step")
+    else:
+        params, hist, chosen_step = train(feats[fit], times[fit], steps=args.steps,
+                                          val=(feats[va], times[va]) if args.val else None, log=log)
     params.astype("<f4").tofile(os.path.join(args.out, "selector_params.f32"))
-    idx_te, _ = picks(params, feats[te])
-    idx_tr, _ = picks(params, feats[tr])
     an = np.array([m["analytic"] for m in meta])
     de = np.array([m["default"] for m in meta])
+    idx_te, _ = picks(params, feats[te], an[te])
+    idx_tr, _ = picks(params, feats[tr], an[tr])
     report = {
         "graphs": len(feats), "n_train": args.train, "n_test": len(feats) - args.train, "steps": args.steps,
         "n_val": args.val, "chosen_step": chosen_step, "loss": hist,
@@ -223,6 +250,8 @@ def main():
                  "time_default_ms": float(times[te][np.arange(len(idx_te)), de[te]].sum()),
                  "time_best_ms": float(np.where(times[te] > 0, times[te], np.inf).min(axis=1).sum())},
         "train_fit": {"learned": summary(regrets(times[tr], idx_tr))},
+        "test_out_of_range": int(sum(1 for i in range(len(idx_te)) if idx_te[i] == an[te][i]
+                                     and not _in_range(params, feats[te][i]))),
         "grid_best_counts": np.bincount(np.where(times > 0, times, np.inf).argmin(axis=1),
                                         minlength=times.shape[1]).tolist(),
     }

@@ -220,10 +220,12 @@ def test_trained_selector_gains_over_the_method_without_it():
     feats, times, meta, rep = _heldout()
     sel = binding.Selector.pretrained()
     scores = sel.forward(torch.from_numpy(feats.astype(np.float32)).cuda()).cpu().numpy()
+    an = np.array([m["analytic"] for m in meta])
+    pick = np.array([scores[i].argmin() if sel.in_range(feats[i]) else an[i] for i in range(len(feats))])
     sel.close()
-    learned = _regret(times, scores.argmin(axis=1)).mean()
+    learned = _regret(times, pick).mean()
     default = _regret(times, np.array([m["default"] for m in meta])).mean()
-    analytic = _regret(times, np.array([m["analytic"] for m in meta])).mean()
+    analytic = _regret(times, an).mean()
     assert learned == pytest.approx(rep["test"]["learned"]["mean"], rel=1e-6)
     assert learned < default
     assert learned < analytic

@@ -207,6 +207,14 @@ def test_shipped_selector_report_reproduces_in_fp64():
     f, t = d["features"][n_train:].astype(np.float64), d["times"][n_train:]
     y, _ = so.forward(p, f)
     idx = y.argmin(axis=1)
+    # outside the trained range (widened by 5 % of its width) the analytic choice stands
+    lo_o, hi_o = so.layout()["lo"][0], so.layout()["hi"][0]
+    lo, hi = p[lo_o:lo_o + so.N_FEATURES], p[hi_o:hi_o + so.N_FEATURES]
+    pad = 0.05 * (hi - lo) + 1e-6
+    f32 = d["features"][n_train:]
+    out = ((f32 < lo - pad) | (f32 > hi + pad)).any(axis=1)
+    meta = json.loads(str(d["meta"]))[n_train:]
+    idx = np.where(out, np.array([m["analytic"] for m in meta]), idx)
     best = np.where(t > 0, t, np.inf).min(axis=1)
     reg = t[np.arange(len(idx)), idx] / best
     assert reg.mean() == pytest.approx(rep["test"]["learned"]["mean"], rel=1e-6)
