@@ -50,12 +50,21 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+# sources each timed kernel is built from (a committed DRAM-byte figure is
+# used only while these files are unchanged)
+KERNEL_SOURCES = {
+    "k_radix_down_bulk": ["gt_radix.cu", "gt_device.cuh", "gt_internal.h"],
+    "k_radix_down": ["gt_radix.cu", "gt_device.cuh", "gt_internal.h"],
+    "k_scatter": ["gt_steps.cu", "gt_device.cuh", "gt_internal.h"],
+}
+
+
+def kernel_source_sha(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_06872_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "gt.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -67,7 +76,7 @@ def load_traffic(kernel, workload):
     try:
         d = json.load(open(p))
         e = d.get(f"{kernel}@{workload}")
-        if e and e.get("source_sha") == kernel_source_sha():
+        if e and e.get("source_sha") == kernel_source_sha(kernel):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass

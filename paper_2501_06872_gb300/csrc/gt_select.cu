@@ -170,9 +170,72 @@ __global__ void k_feat_loc(const uint64_t *__restrict__ row_ptr, const uint32_t 
   }
 }
 
-// One thread: turns the integer summaries into the GT_N_FEATURES floats.
-__global__ void k_feat_final(FeatWs *ws, uint32_t n, uint64_t m, uint32_t ns, int has_vals, float *out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Turns the integer summaries into the GT_N_FEATURES floats (one CTA of
+// 1024 threads).  The coverage of the kTopK most frequent sampled
+// destinations takes the exactly listed large frequencies first, then walks
+// the frequency histogram downwards: thread t sums the 64 bins of its chunk,
+// a suffix scan over the chunks finds the chunk where kTopK is reached, and
+// that chunk's thread walks its bins.
+constexpr uint32_t kFinThreads = 1024;
+constexpr uint32_t kFinChunk = kFreqCap / kFinThreads;
+
+__global__ void __launch_bounds__(kFinThreads) k_feat_final(FeatWs *ws, uint32_t n, uint64_t m, uint32_t ns,
+                                                            int has_vals, float *out) {
+  __shared__ unsigned long long s_cnt[kFinThreads], s_sum[kFinThreads];
+  __shared__ unsigned long long s_left, s_cov;
+  const uint32_t t = threadIdx.x;
+  unsigned long long cnt = 0, sum = 0;
+  for (uint32_t c = max(t * kFinChunk, 1u); c < (t + 1) * kFinChunk; ++c) {
+    cnt += ws->fh[c];
+    sum += (unsigned long long)c * ws->fh[c];
+  }
+  s_cnt[t] = cnt;
+  s_sum[t] = sum;
+  if (t == 0) {
+    const uint32_t nb = ws->nbig < kBigCap ? ws->nbig : kBigCap;
+    for (uint32_t i = 1; i < nb; ++i) {  // insertion sort, descending (at most ns / 2^16 <= 16 entries)
+      const uint32_t x = ws->big[i];
+      uint32_t j = i;
+      while (j > 0 && ws->big[j - 1] < x) {
+        ws->big[j] = ws->big[j - 1];
+        --j;
+      }
+      ws->big[j] = x;
+    }
+    uint64_t left = kTopK, cov = 0;
+    for (uint32_t i = 0; i < nb && left; ++i, --left) cov += ws->big[i];
+    s_left = left;
+    s_cov = cov;
+  }
+  __syncthreads();
+  // inclusive suffix sums over chunks (Hillis-Steele)
+  for (uint32_t off = 1; off < kFinThreads; off <<= 1) {
+    const unsigned long long ac = t + off < kFinThreads ? s_cnt[t + off] : 0;
+    const unsigned long long as = t + off < kFinThreads ? s_sum[t + off] : 0;
+    __syncthreads();
+    s_cnt[t] += ac;
+    s_sum[t] += as;
+    __syncthreads();
+  }
+  const unsigned long long left = s_left;
+  const unsigned long long above_c = t + 1 < kFinThreads ? s_cnt[t + 1] : 0;
+  const unsigned long long above_s = t + 1 < kFinThreads ? s_sum[t + 1] : 0;
+  __syncthreads();
+  if (left > 0) {
+    if (t == 0 && s_cnt[0] < left) {
+      s_cov += s_sum[0];  // fewer than kTopK distinct destinations left: all of them
+    } else if (above_c < left && s_cnt[t] >= left) {
+      unsigned long long need = left - above_c, cov = above_s;
+      for (uint32_t c = (t + 1) * kFinChunk - 1; c >= max(t * kFinChunk, 1u) && need; --c) {
+        const unsigned long long k = min((unsigned long long)ws->fh[c], need);
+        cov += k * c;
+        need -= k;
+      }
+      s_cov += cov;  // exactly one thread gets here
+    }
+  }
+  __syncthreads();
+  if (t != 0) return;
   const double dn = (double)n;
   for (uint32_t b = 0; b < kDegBins; ++b) out[b] = (float)((double)ws->vcnt[b] / dn);
   out[32] = (float)(log2(dn) / 32.0);
@@ -193,25 +256,7 @@ __global__ void k_feat_final(FeatWs *ws, uint32_t n, uint64_t m, uint32_t ns, in
     }
   }
   out[35] = m ? (float)(got / (double)m) : 0.f;
-  // coverage of the kTopK most frequent sampled destinations
-  uint32_t nb = ws->nbig < kBigCap ? ws->nbig : kBigCap;
-  for (uint32_t i = 1; i < nb; ++i) {  // insertion sort, descending
-    uint32_t x = ws->big[i];
-    uint32_t j = i;
-    while (j > 0 && ws->big[j - 1] < x) {
-      ws->big[j] = ws->big[j - 1];
-      --j;
-    }
-    ws->big[j] = x;
-  }
-  uint64_t left = kTopK, cov = 0;
-  for (uint32_t i = 0; i < nb && left; ++i, --left) cov += ws->big[i];
-  for (uint32_t c = kFreqCap - 1; c >= 1 && left; --c) {
-    const uint64_t k = min64(left, (uint64_t)ws->fh[c]);
-    cov += k * c;
-    left -= k;
-  }
-  out[36] = ns ? (float)((double)cov / (double)ns) : 0.f;
+  out[36] = ns ? (float)((double)s_cov / (double)ns) : 0.f;
   out[37] = ns ? (float)(log2((double)ws->maxfreq * (double)m / (double)ns + 1.0) / 32.0) : 0.f;
   const double lp = (double)ws->loc_pairs;
   out[38] = lp > 0 ? (float)(ws->loc_sum / lp / 32.0) : 0.f;
@@ -416,7 +461,7 @@ gt_status gt_graph_features(uint32_t n, uint64_t m, int has_vals, const uint64_t
       k_feat_freq<<<std::min<uint32_t>(blocks(ts, 256), sms * 8), 256, 0, s>>>(keys, cnt, (uint32_t)ts, ws);
       k_feat_loc<<<blocks((uint64_t)kLocRows * 32, 256), 256, 0, s>>>(row_ptr, col_idx, n, m, kLocRows, seed, ws);
     }
-    k_feat_final<<<1, 32, 0, s>>>(ws, n, m, ns, has_vals, features);
+    k_feat_final<<<1, kFinThreads, 0, s>>>(ws, n, m, ns, has_vals, features);
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(blk, s);

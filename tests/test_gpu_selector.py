@@ -48,10 +48,14 @@ def graphs():
     rp[1:] = np.cumsum([len(r) for r in rows])
     out.append(("consecutive", n, rp, np.array([v for r in rows for v in r], dtype=np.uint32), None))
     out.append(("empty", 7, np.zeros(8, dtype=np.uint64), np.zeros(0, dtype=np.uint32), None))
+    # 7 M vertices: ~70,000 samples all on vertex 0 (a frequency >= 2^16, listed exactly)
+    n = 7_000_000
+    rp = np.minimum(np.arange(n + 1, dtype=np.uint64), 1000).astype(np.uint64)
+    out.append(("hub-7M", n, rp, np.zeros(1000, dtype=np.uint32), None))
     return out
 
 
-@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("idx", range(7))
 def test_features_match_oracle(idx):
     from paper_2501_06872_gb300 import binding
     name, n, rp, ci, vv = graphs()[idx]
