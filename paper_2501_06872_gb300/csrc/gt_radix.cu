@@ -32,8 +32,12 @@ constexpr int kRBins = 256;
 // Lanes holding the same dbits-bit digit (and active): AND of one ballot per
 // bit -- cheaper than __match_any_sync for digits of a few bits.
 __device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t dbits, bool act) {
+  // digits have at most 8 bits; the bits above dbits are 0 in every lane, so
+  // their ballots change nothing and the loop unrolls at compile time
+  (void)dbits;
   uint32_t mm = __ballot_sync(kFull, act);
-  for (uint32_t b = 0; b < dbits; ++b) {
+#pragma unroll
+  for (uint32_t b = 0; b < 8; ++b) {
     const bool bit = (d >> b) & 1u;
     const uint32_t bb = __ballot_sync(kFull, bit);
     mm &= bit ? bb : ~bb;
@@ -439,8 +443,7 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t wcnt[kBWarps][kRBins];
   __shared__ unsigned long long run_off[kRBins];
-  __shared__ unsigned long long dst_base[kRBins];  // run_off[d] - tile_start[d] of the current tile
-  __shared__ uint32_t tile_start[kRBins];
+  __shared__ unsigned long long dst_base[kRBins];  // run_off[d] - (tile-local start of d) for the current tile
   __shared__ uint32_t wsum[kBWarps];
   __shared__ uint32_t s_abort;
   const uint32_t tid = threadIdx.x, w = tid >> 5, lane = tid & 31u;
@@ -546,19 +549,22 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       uint32_t before = 0;
 #pragma unroll
       for (int x = 0; x < kBWarps; ++x) before += (x < (int)w) ? wsum[x] : 0u;
-      tile_start[tid] = before + inc - tot;
-      dst_base[tid] = run_off[tid] - (before + inc - tot);
+      const uint32_t ts = before + inc - tot;  // tile-local start of digit tid
+      dst_base[tid] = run_off[tid] - ts;
+#pragma unroll
+      for (int x = 0; x < kBWarps; ++x) wcnt[x][tid] += ts;  // per-warp bases, tile-local
     }
     __syncthreads();
-    // back into the same buffer in (digit, rank) order
+    // back into the same buffer in (digit, rank) order; weighted tiles keep
+    // (source, value) pairs interleaved in the source and value arrays' space
 #pragma unroll
     for (int i = 0; i < kBItems; ++i) {
       if (rk[i] != 0xFFFFFFFFu) {
         const uint32_t d = (key[i] >> a.shift) & mask;
-        const uint32_t lp = tile_start[d] + wcnt[w][d] + rk[i];
+        const uint32_t lp = wcnt[w][d] + rk[i];
         bk[lp] = key[i];
-        bu[lp] = uu[i];
-        if (VALS) bw[lp] = ww[i];
+        if (VALS) reinterpret_cast<uint2 *>(bu)[lp] = make_uint2(uu[i], ww[i]);
+        else bu[lp] = uu[i];
       }
     }
     __syncthreads();
@@ -566,16 +572,24 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       const uint32_t k = bk[j];
       const uint32_t d = (k >> a.shift) & mask;
       const uint64_t pos = dst_base[d] + j;
+      uint32_t u, wv = 0;
+      if (VALS) {
+        const uint2 uw = reinterpret_cast<const uint2 *>(bu)[j];
+        u = uw.x;
+        wv = uw.y;
+      } else {
+        u = bu[j];
+      }
       a.out_key[pos] = k;
       if (stores_batch(MODE)) {  // the last pass of a batch stores through the graph's descriptor
         const uint32_t g = k >> a.batch.vbits;
         const gt_graph_desc &gd = a.batch.descs[g];
         const uint64_t lp = pos - a.batch.eoff[g];
-        gd.row_idx[lp] = bu[j];
-        if (VALS) gd.vals_out[lp] = __uint_as_float(bw[j]);
+        gd.row_idx[lp] = u;
+        if (VALS) gd.vals_out[lp] = __uint_as_float(wv);
       } else {
-        a.out_u[pos] = bu[j];
-        if (VALS) a.out_w[pos] = bw[j];
+        a.out_u[pos] = u;
+        if (VALS) a.out_w[pos] = wv;
       }
     };
     if (tcount == kBTile) {

@@ -407,19 +407,179 @@ __device__ void cta_sort_run(uint32_t *a, uint32_t *tmp, uint32_t len, uint32_t 
   __syncthreads();
 }
 
+// Sorts one LDV list [s0, s0 + L) stably by its (tag-masked) source ID and
+// writes row_idx / vals_out: an LSD radix sort over the bits of a vertex ID
+// with per-(digit, warp) offsets, the list cut into 32 contiguous warp ranges
+// (1024 threads); every warp scatters its range in order and counts the next
+// pass's digits per destination warp range as it writes.  The first pass
+// reads `src`; the passes then alternate between the views x and y.  Tagged
+// runs (split rows) are then ordered by their position in the row: a run of
+// <= 64 entries by the thread at its start, longer ones by the whole CTA.
+// words: the hist / next tables, [256][32] words each.
+struct SortShared {
+  uint32_t tagged, nlong;
+  uint32_t long_i[kRadixThreads], long_n[kRadixThreads];
+};
+
 template <bool VALS>
-__global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  if (cta_status_set(a.status)) return;
-  __shared__ uint32_t s_item, s_tagged, s_nlong;
-  __shared__ uint32_t s_long_i[kRadixThreads], s_long_n[kRadixThreads];
+__device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, const Buf x, const Buf y,
+                          uint32_t *words, SortShared &sh) {
   const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t umask = umask_of(a);
-  const uint32_t nlarge = min(a.meta[kMetaLargeN], a.large_cap);
   const uint32_t bits = a.key_bits ? a.key_bits : 1u;
   const uint32_t passes = (bits + 7) / 8;
   const uint32_t dbits = (bits + passes - 1) / passes;
   const uint32_t nb = 1u << dbits;
+  const uint32_t chunk = (L + 31) / 32;
+  uint32_t *hist = words;             // [256][32]
+  uint32_t *next = words + 256 * 32;  // [256][32]
+  // first pass's per-warp counts; notes whether any entry is tagged
+  for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) sh.tagged = 0;
+  __syncthreads();
+  {
+    const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
+    uint32_t anytag = 0;
+    for (uint32_t i = r0 + lane; i < r1; i += 32) {
+      const uint32_t u = src.getu(i);
+      anytag |= u & ~umask;
+      atomicAdd(&hist[(u & umask & (nb - 1)) * 32 + w], 1u);
+    }
+    if (anytag) sh.tagged = 1;
+  }
+  __syncthreads();
+  Buf dst = x;
+  for (uint32_t ps = 0; ps < passes; ++ps) {
+    const uint32_t shift = ps * dbits;
+    // exclusive scan over (digit, warp), digit-major: per-digit prefix over
+    // warps, per-digit totals, prefix over digits, then combine
+    for (uint32_t d = w; d < nb; d += 32) {
+      uint32_t xv = hist[d * 32 + lane];
+      uint32_t inc = xv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t yv = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += yv;
+      }
+      hist[d * 32 + lane] = inc - xv;
+      if (lane == 31) next[d] = inc;  // digit total (next[] is cleared below)
+    }
+    __syncthreads();
+    if (w == 0) {
+      uint32_t run = 0;
+      for (uint32_t d0 = 0; d0 < nb; d0 += 32) {
+        uint32_t t = (d0 + lane < nb) ? next[d0 + lane] : 0u;
+        uint32_t inc = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t yv = __shfl_up_sync(kFull, inc, o);
+          if (lane >= (uint32_t)o) inc += yv;
+        }
+        if (d0 + lane < nb) next[d0 + lane] = run + inc - t;
+        run += __shfl_sync(kFull, inc, 31);
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nb * 32; i += blockDim.x) hist[i] += next[i >> 5];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) next[i] = 0;
+    __syncthreads();
+    const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
+    const uint32_t nshift = shift + dbits;
+    const bool more = ps + 1 < passes;
+    for (uint32_t c = r0; c < r1; c += 32) {
+      const uint32_t i = c + lane;
+      const bool act = i < r1;
+      const uint32_t u = act ? src.getu(i) : 0u;
+      const uint32_t wv = (VALS && act) ? src.getw(i) : 0u;
+      const uint32_t d = act ? (((u & umask) >> shift) & (nb - 1)) : nb;
+      const uint32_t mm = __match_any_sync(kFull, d);
+      const uint32_t rank = __popc(mm & lanemask_lt());
+      uint32_t base = 0;
+      if (act) base = hist[d * 32 + w];
+      __syncwarp();
+      if (act && rank == 0) hist[d * 32 + w] = base + __popc(mm);
+      __syncwarp();
+      if (act) {
+        const uint32_t pos = base + rank;
+        dst.u[pos] = u;
+        if (VALS) dst.w[pos] = wv;
+        if (more) atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * 32 + min(pos / chunk, 31u)], 1u);
+      }
+    }
+    __syncthreads();
+    uint32_t *t = hist;
+    hist = next;
+    next = t;
+    src = dst;
+    dst = (dst.u == x.u) ? y : x;
+  }
+  // src holds the sorted list (SoA)
+  if (VALS && a.flag_mode && sh.tagged) {
+    const Buf other = (src.u == x.u) ? y : x;
+    for (uint32_t base = 0; base < L; base += blockDim.x) {
+      if (threadIdx.x == 0) sh.nlong = 0;
+      __syncthreads();
+      const uint32_t i = base + threadIdx.x;
+      if (i < L) {
+        const uint32_t u = src.u[i];
+        if ((u & kSplitFlag) && (i == 0 || src.u[i - 1] != u)) {
+          uint32_t lo = i, hi = L;  // end of the run: first index past i with another source
+          while (hi - lo > 1) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if (src.u[mid] == u) lo = mid;
+            else hi = mid;
+          }
+          const uint32_t j = hi;
+          if (j - i <= 64) {
+            for (uint32_t xi = i + 1; xi < j; ++xi) {
+              const uint32_t tpos = src.w[xi];
+              uint32_t yi = xi;
+              while (yi > i && src.w[yi - 1] > tpos) {
+                src.w[yi] = src.w[yi - 1];
+                --yi;
+              }
+              src.w[yi] = tpos;
+            }
+          } else {
+            const uint32_t q = atomicAdd(&sh.nlong, 1u);
+            sh.long_i[q] = i;
+            sh.long_n[q] = j - i;
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t nl = sh.nlong;
+      for (uint32_t q = 0; q < nl; ++q) cta_sort_run(src.w + sh.long_i[q], other.w + sh.long_i[q], sh.long_n[q], words);
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
+    uint32_t u = src.u[i];
+    if (VALS) {
+      uint32_t wb = src.w[i];
+      if (a.flag_mode && (u & kSplitFlag)) {
+        u &= ~kSplitFlag;
+        wb = __float_as_uint(a.vals[a.row_ptr[u] + wb]);
+      }
+      a.row_idx[s0 + i] = u;
+      a.vals_out[s0 + i] = __uint_as_float(wb);
+    } else if (src.u != a.row_idx + s0) {
+      a.row_idx[s0 + i] = u;
+    }
+  }
+  __syncthreads();
+}
+
+// > kSortSmemCap: one CTA per list, through global memory: the outputs and
+// the list's scratch alternate (weighted lists start in the packed scratch).
+template <bool VALS>
+__global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (cta_status_set(a.status)) return;
+  __shared__ uint32_t s_item;
+  __shared__ SortShared sh;
+  const uint32_t nlarge = min(a.meta[kMetaLargeN], a.large_cap);
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaLargeTicket], 1u);
     __syncthreads();
@@ -429,160 +589,14 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
     const uint32_t v = a.largelist[it];
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
-    const uint32_t chunk = (L + 31) / 32;
-    uint32_t *hist = (uint32_t *)smem;  // [256][32]
-    uint32_t *next = hist + 256 * 32;   // [256][32]
-    Buf out{a.row_idx + s0, VALS ? (uint32_t *)(a.vals_out + s0) : nullptr, nullptr};
-    Buf scr;
-    Buf src;
+    const Buf out{a.row_idx + s0, VALS ? (uint32_t *)(a.vals_out + s0) : nullptr, nullptr};
     if (VALS) {
       uint32_t *base32 = (uint32_t *)(a.ldv64 + s0);  // the list's 8L scratch bytes as u[L], w[L]
-      scr = Buf{base32, base32 + L, nullptr};
-      src = Buf{nullptr, nullptr, a.ldv64 + s0};
+      sort_list<VALS>(a, s0, L, Buf{nullptr, nullptr, a.ldv64 + s0}, out, Buf{base32, base32 + L, nullptr},
+                      (uint32_t *)smem, sh);
     } else {
-      scr = Buf{a.scr32 + s0, nullptr, nullptr};
-      src = out;
+      sort_list<VALS>(a, s0, L, out, Buf{a.scr32 + s0, nullptr, nullptr}, out, (uint32_t *)smem, sh);
     }
-    // first pass's per-warp counts; notes whether any entry is tagged
-    for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) hist[i] = 0;
-    if (threadIdx.x == 0) s_tagged = 0;
-    __syncthreads();
-    {
-      const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
-      uint32_t anytag = 0;
-      for (uint32_t i = r0 + lane; i < r1; i += 32) {
-        const uint32_t u = src.getu(i);
-        anytag |= u & ~umask;
-        atomicAdd(&hist[(u & umask & (nb - 1)) * 32 + w], 1u);
-      }
-      if (anytag) s_tagged = 1;
-    }
-    __syncthreads();
-    Buf dst = VALS ? out : scr;
-    for (uint32_t ps = 0; ps < passes; ++ps) {
-      const uint32_t shift = ps * dbits;
-      // exclusive scan over (digit, warp), digit-major: per-digit prefix over
-      // warps, per-digit totals, prefix over digits, then combine
-      for (uint32_t d = w; d < nb; d += 32) {
-        uint32_t x = hist[d * 32 + lane];
-        uint32_t inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          uint32_t y = __shfl_up_sync(kFull, inc, o);
-          if (lane >= (uint32_t)o) inc += y;
-        }
-        hist[d * 32 + lane] = inc - x;
-        if (lane == 31) next[d] = inc;  // digit total (next[] is cleared below)
-      }
-      __syncthreads();
-      if (w == 0) {
-        uint32_t run = 0;
-        for (uint32_t d0 = 0; d0 < nb; d0 += 32) {
-          uint32_t t = (d0 + lane < nb) ? next[d0 + lane] : 0u;
-          uint32_t inc = t;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, inc, o);
-            if (lane >= (uint32_t)o) inc += y;
-          }
-          if (d0 + lane < nb) next[d0 + lane] = run + inc - t;
-          run += __shfl_sync(kFull, inc, 31);
-        }
-      }
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < nb * 32; i += blockDim.x) hist[i] += next[i >> 5];
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) next[i] = 0;
-      __syncthreads();
-      const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
-      const uint32_t nshift = shift + dbits;
-      const bool more = ps + 1 < passes;
-      for (uint32_t c = r0; c < r1; c += 32) {
-        const uint32_t i = c + lane;
-        const bool act = i < r1;
-        const uint32_t u = act ? src.getu(i) : 0u;
-        const uint32_t wv = (VALS && act) ? src.getw(i) : 0u;
-        const uint32_t d = act ? (((u & umask) >> shift) & (nb - 1)) : nb;
-        const uint32_t mm = __match_any_sync(kFull, d);
-        const uint32_t rank = __popc(mm & lanemask_lt());
-        uint32_t base = 0;
-        if (act) base = hist[d * 32 + w];
-        __syncwarp();
-        if (act && rank == 0) hist[d * 32 + w] = base + __popc(mm);
-        __syncwarp();
-        if (act) {
-          const uint32_t pos = base + rank;
-          dst.u[pos] = u;
-          if (VALS) dst.w[pos] = wv;
-          if (more) atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * 32 + min(pos / chunk, 31u)], 1u);
-        }
-      }
-      __syncthreads();
-      uint32_t *t = hist;
-      hist = next;
-      next = t;
-      src = dst;
-      dst = (dst.u == out.u) ? scr : out;
-    }
-    // src holds the sorted list (SoA): order tagged runs (split rows) by
-    // their position in the row, then write the outputs (in place when src
-    // is the output buffer).  A run of <= 64 entries is sorted by the thread
-    // at its start; longer ones by the whole CTA, window by window.
-    if (VALS && a.flag_mode && s_tagged) {
-      Buf other = (src.u == out.u) ? scr : out;
-      for (uint32_t base = 0; base < L; base += blockDim.x) {
-        if (threadIdx.x == 0) s_nlong = 0;
-        __syncthreads();
-        const uint32_t i = base + threadIdx.x;
-        if (i < L) {
-          const uint32_t u = src.u[i];
-          if ((u & kSplitFlag) && (i == 0 || src.u[i - 1] != u)) {
-            uint32_t lo = i, hi = L;  // end of the run: first index past i with another source
-            while (hi - lo > 1) {
-              const uint32_t mid = lo + (hi - lo) / 2;
-              if (src.u[mid] == u) lo = mid;
-              else hi = mid;
-            }
-            const uint32_t j = hi;
-            if (j - i <= 64) {
-              for (uint32_t x = i + 1; x < j; ++x) {
-                const uint32_t tpos = src.w[x];
-                uint32_t y = x;
-                while (y > i && src.w[y - 1] > tpos) {
-                  src.w[y] = src.w[y - 1];
-                  --y;
-                }
-                src.w[y] = tpos;
-              }
-            } else {
-              const uint32_t q = atomicAdd(&s_nlong, 1u);
-              s_long_i[q] = i;
-              s_long_n[q] = j - i;
-            }
-          }
-        }
-        __syncthreads();
-        const uint32_t nl = s_nlong;
-        for (uint32_t q = 0; q < nl; ++q)
-          cta_sort_run(src.w + s_long_i[q], other.w + s_long_i[q], s_long_n[q], (uint32_t *)smem);
-        __syncthreads();
-      }
-    }
-    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-      uint32_t u = src.u[i];
-      if (VALS) {
-        uint32_t wb = src.w[i];
-        if (a.flag_mode && (u & kSplitFlag)) {
-          u &= ~kSplitFlag;
-          wb = __float_as_uint(a.vals[a.row_ptr[u] + wb]);
-        }
-        a.row_idx[s0 + i] = u;
-        a.vals_out[s0 + i] = __uint_as_float(wb);
-      } else if (src.u != out.u) {
-        a.row_idx[s0 + i] = u;
-      }
-    }
-    __syncthreads();
   }
 }
 
