@@ -159,6 +159,20 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
                             const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
                             float *vals_out, void *stream);
 
+/* Asynchronous gt_transpose_host: enqueues the input copies and the
+ * transposition on `stream` and the output copies on a stream the plan owns,
+ * and returns without waiting.  The next call's input copies overlap this
+ * call's output copies (the next transposition waits for them), so a loop of
+ * calls keeps both copy directions busy.  Host buffers must stay untouched
+ * (inputs) and unread (outputs) until gt_plan_host_wait returns; calls that
+ * overwrite one pair of host output buffers leave the last call's CSC there.
+ * gt_plan_host_wait waits for all outstanding calls and returns the device
+ * status. */
+gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx,
+                                  const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out,
+                                  void *stream);
+gt_status gt_plan_host_wait(gt_plan plan);
+
 /* Allocation-free variant of gt_transpose (no counterpart in the paper).
  * For callers that must not allocate device memory on the call path, e.g. a
  * host program whose pool already owns all device memory, or a latency-

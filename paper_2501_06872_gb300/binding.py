@@ -94,7 +94,8 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_batch_plan_destroy", "gt_graph_features", "gt_tune_grid_config", "gt_tune_analytic",
            "gt_selector_param_count", "gt_selector_create", "gt_selector_get_params", "gt_selector_set_params",
            "gt_selector_forward", "gt_selector_backward", "gt_selector_adam_step", "gt_selector_destroy",
-           "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges", "gt_selector_in_range"]
+           "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges", "gt_selector_in_range", "gt_transpose_host_async",
+           "gt_plan_host_wait"]
 
 N_FEATURES = 41
 TUNE_GRID = 12
@@ -118,6 +119,10 @@ def load():
     lib.gt_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
     lib.gt_transpose.argtypes = [P, P, P, P, P, P, P, P]
     lib.gt_transpose_host.argtypes = [P, P, P, P, P, P, P, P]
+    lib.gt_transpose_host_async.argtypes = [P, P, P, P, P, P, P, P]
+    lib.gt_transpose_host_async.restype = ctypes.c_int
+    lib.gt_plan_host_wait.argtypes = [P]
+    lib.gt_plan_host_wait.restype = ctypes.c_int
     lib.gt_transpose_sub.argtypes = [P, u32, u64, P, P, P, P, P, P, P]
     lib.gt_transpose_sub.restype = ctypes.c_int
     lib.gt_plan_status.argtypes = [P]
@@ -251,6 +256,15 @@ class Plan:
         rc = self._lib.gt_transpose_host(self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
                                          _ptr(row_idx), _ptr(vals_out), _stream(stream))
         _check(rc, "gt_transpose_host")
+
+    def transpose_host_async(self, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
+        """Enqueue CSR -> CSC on pinned host arrays without waiting (see host_wait)."""
+        rc = self._lib.gt_transpose_host_async(self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
+                                               _ptr(row_idx), _ptr(vals_out), _stream(stream))
+        _check(rc, "gt_transpose_host_async")
+
+    def host_wait(self):
+        _check(self._lib.gt_plan_host_wait(self._h), "gt_plan_host_wait")
 
     def status(self) -> int:
         return self._lib.gt_plan_status(self._h)

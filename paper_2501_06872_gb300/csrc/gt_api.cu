@@ -31,6 +31,10 @@ struct gt_plan_s {
   float *h_vals = nullptr, *h_vals_out = nullptr;
   void *host_allocs[6] = {};
   int nhost = 0;
+  // gt_transpose_host_async: output copies on their own stream, ordered by events
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_computed = nullptr, ev_copied = nullptr;
+  cudaStream_t async_stream = nullptr;
   // per-step timing
   bool timing = false;
   std::vector<gt::StepEvents> events;
@@ -503,14 +507,8 @@ uint32_t gt_plan_vertices(gt_plan plan) { return plan ? plan->w.n : 0; }
 
 uint64_t gt_plan_edges(gt_plan plan) { return plan ? plan->w.m : 0; }
 
-gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
-                            uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
-  if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
+static gt_status host_staging(gt_plan plan) {
   const size_t n = plan->w.n, m = plan->w.m;
-  if (m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
-  if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
-  if (vals && !plan->w.has_vals) return GT_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
   if (!plan->h_row_ptr) {
     void *q;
 #define GT_HA(field, bytes)                                              \
@@ -532,6 +530,26 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
     }
 #undef GT_HA
   }
+  return GT_OK;
+}
+
+static gt_status host_args(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                           uint64_t *col_ptr, uint32_t *row_idx, float *vals_out) {
+  if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
+  if (plan->w.m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
+  if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
+  if (vals && !plan->w.has_vals) return GT_ERR_INVALID_ARG;
+  return GT_OK;
+}
+
+gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                            uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+  gt_status ast = host_args(plan, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out);
+  if (ast != GT_OK) return ast;
+  const size_t n = plan->w.n, m = plan->w.m;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((ast = host_staging(plan)) != GT_OK) return ast;
+  if (plan->copy_stream && cudaStreamSynchronize(plan->copy_stream) != cudaSuccess) return GT_ERR_CUDA;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
@@ -552,9 +570,66 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
   return gt_plan_status(plan);
 }
 
+gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                                  uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+  gt_status ast = host_args(plan, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out);
+  if (ast != GT_OK) return ast;
+  const size_t n = plan->w.n, m = plan->w.m;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((ast = host_staging(plan)) != GT_OK) return ast;
+  if (!plan->copy_stream) {
+    if (cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return GT_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&plan->ev_computed, cudaEventDisableTiming) != cudaSuccess) return GT_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&plan->ev_copied, cudaEventDisableTiming) != cudaSuccess) return GT_ERR_CUDA;
+    if (cudaEventRecord(plan->ev_copied, plan->copy_stream) != cudaSuccess) return GT_ERR_CUDA;
+  }
+  plan->async_stream = s;
+  cudaError_t e;
+  // inputs: on the caller's stream (after the previous transposition read them)
+  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return from_cuda(e);
+  if (m && (e = cudaMemcpyAsync(plan->h_col_idx, col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return from_cuda(e);
+  if (vals && m && (e = cudaMemcpyAsync(plan->h_vals, vals, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return from_cuda(e);
+  // the transposition overwrites the device outputs: wait for the previous call's output copies
+  if ((e = cudaStreamWaitEvent(s, plan->ev_copied, 0)) != cudaSuccess) return from_cuda(e);
+  gt_status st = gt_transpose(plan, plan->h_row_ptr, plan->h_col_idx, vals ? plan->h_vals : nullptr,
+                              plan->h_col_ptr, plan->h_row_idx, vals ? plan->h_vals_out : nullptr, stream);
+  if (st != GT_OK) return st;
+  // outputs: on the plan's copy stream, after the transposition
+  cudaStream_t c = plan->copy_stream;
+  if ((e = cudaEventRecord(plan->ev_computed, s)) != cudaSuccess) return from_cuda(e);
+  if ((e = cudaStreamWaitEvent(c, plan->ev_computed, 0)) != cudaSuccess) return from_cuda(e);
+  if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
+    return from_cuda(e);
+  if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx, m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
+    return from_cuda(e);
+  if (vals && m &&
+      (e = cudaMemcpyAsync(vals_out, plan->h_vals_out, m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
+    return from_cuda(e);
+  if ((e = cudaEventRecord(plan->ev_copied, c)) != cudaSuccess) return from_cuda(e);
+  return GT_OK;
+}
+
+gt_status gt_plan_host_wait(gt_plan plan) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  if (plan->copy_stream) {
+    cudaError_t e = cudaStreamSynchronize(plan->copy_stream);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return gt_plan_status(plan);
+}
+
 void gt_plan_destroy(gt_plan plan) {
   if (!plan) return;
   if (plan->last) cudaStreamSynchronize(plan->last);
+  if (plan->copy_stream) {
+    cudaStreamSynchronize(plan->copy_stream);
+    cudaEventDestroy(plan->ev_computed);
+    cudaEventDestroy(plan->ev_copied);
+    cudaStreamDestroy(plan->copy_stream);
+  }
   drop_events(plan);
   plan_free_ws(plan);
   for (int i = 0; i < plan->nhost; ++i) cudaFree(plan->host_allocs[i]);

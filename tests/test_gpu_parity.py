@@ -254,6 +254,29 @@ def test_host_path_matches_device_path():
     plan.close()
 
 
+def test_host_async_pipeline():
+    """Three overlapped host calls with different values, each into its own
+    pinned output buffers, all equal to the oracle."""
+    from paper_2501_06872_gb300 import binding
+    n, rp, ci, vv = inputs.rmat_csr(13, 16, seed=7, order="random", weighted=True)
+    m = len(ci)
+    plan = binding.Plan(n, m, True, config(**CONFIGS["radix"]))
+    h_rp = torch.from_numpy(rp.view(np.int64)).pin_memory()
+    h_ci = torch.from_numpy(ci.view(np.int32)).pin_memory()
+    vals = [vv, vv * 2 + 1, -vv]
+    h_vv = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory() for x in vals]
+    outs = [(torch.empty(n + 1, dtype=torch.int64).pin_memory(), torch.empty(m, dtype=torch.int32).pin_memory(),
+             torch.empty(m, dtype=torch.float32).pin_memory()) for _ in vals]
+    for k in range(3):
+        plan.transpose_host_async(h_rp, h_ci, h_vv[k], *outs[k])
+    plan.host_wait()
+    for k in range(3):
+        exp = oracle.transpose(rp, ci, vals[k].astype(np.float32))
+        got = (outs[k][0].numpy().view(np.uint64), outs[k][1].numpy().view(np.uint32), outs[k][2].numpy())
+        assert_same(got, exp)
+    plan.close()
+
+
 def test_plan_reuse_and_stats():
     from paper_2501_06872_gb300 import binding
     n, rp, ci, vv = inputs.rmat_csr(13, 16, seed=2, order="degree", weighted=True)
