@@ -222,8 +222,9 @@ typedef struct gt_batch_plan_s *gt_batch_plan;
 /* descs: HOST array of n_graphs descriptors (copied; the pointers inside are
  * used by every later gt_transpose_batched).  Graphs may be empty; every
  * graph needs n_vertices >= 1.  cfg: method must be GT_METHOD_RADIX (or cfg
- * NULL); radix_tile and ctas_per_sm apply; flags bit GT_FLAG_NO_GRAPH runs
- * the kernels directly instead of through a CUDA graph. */
+ * NULL); the digit passes always use the bulk-copy staged downsweep; flags
+ * bit GT_FLAG_NO_GRAPH runs the kernels directly instead of through a CUDA
+ * graph. */
 gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_graph_desc *descs, int has_vals,
                                const gt_config *cfg, void *stream);
 

@@ -84,6 +84,7 @@ struct RadixArgs {
   uint32_t *status;
   BatchView batch;
   uint32_t sub = 1;  // upsweep CTAs per downsweep CTA (table rows = G * sub)
+  uint32_t *g_key = nullptr, *g_w = nullptr;  // batch first upsweep: gathered union keys / values
 };
 
 // Pass modes: plain arrays, or a batch whose first pass loads through the
@@ -183,9 +184,14 @@ __global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
         if (e < e1) {
           while (e >= a.batch.eoff[g + 1]) ++g;
           const gt_graph_desc &d = a.batch.descs[g];
-          const uint32_t v = __ldcs(d.col_idx + (e - a.batch.eoff[g]));
+          const uint64_t le = e - a.batch.eoff[g];
+          const uint32_t v = __ldcs(d.col_idx + le);
           if (v >= d.n_vertices) bad = 1;
           key[i] = (g << a.batch.vbits) | (v & ((1u << a.batch.vbits) - 1u));
+          if (a.g_key) {  // gather the union key (and value) for a plain first pass
+            a.g_key[e] = key[i];
+            if (a.g_w) a.g_w[e] = __float_as_uint(__ldcs(d.vals + le));
+          }
         }
       }
     } else {
@@ -745,9 +751,7 @@ static cudaError_t allow_down() {
 }
 
 cudaError_t configure_radix() {
-  cudaError_t e[8] = {allow_down<8, kPlain>(),      allow_down<16, kPlain>(),     allow_down<8, kBatchFirst>(),
-                      allow_down<16, kBatchFirst>(), allow_down<8, kBatchLast>(),  allow_down<16, kBatchLast>(),
-                      allow_down<8, kBatchOnly>(),   allow_down<16, kBatchOnly>()};
+  cudaError_t e[2] = {allow_down<8, kPlain>(), allow_down<16, kPlain>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   cudaError_t b[4] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
@@ -941,10 +945,6 @@ cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_
   BatchView bv{sb.descs, sb.eoff, sb.voff, sb.ng, sb.vbits};
   const bool vals = bw.has_vals != 0;
   const uint64_t m = sb.m;
-  const uint32_t items = bw.r_items, tile = kRThreads * items;
-  const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
-  const uint32_t G = bw.rG;
-  const uint32_t tpc = ntiles ? (ntiles + G - 1) / G : 0;
   const uint32_t passes = sb.passes, dbits = sb.dbits;
   if ((err = cudaMemsetAsync(bw.meta, 0, kMetaCount * 4, s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(bw.n_long, 0, 4, s)) != cudaSuccess) return err;
@@ -959,29 +959,28 @@ cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_
                                  bw.status);
     k_b_expand_long<<<bw.num_sms * 4, 256, 0, s>>>(bv, bw.long_g, bw.long_r, bw.n_long, bw.long_cap, src_rows);
     nl += 2;
-    const uint32_t *in_key = nullptr, *in_u = src_rows, *in_w = nullptr;
-    // the first pass reads through the descriptors (register tiles); later
-    // passes read the workspace with the bulk-staged downsweep
+    // The first upsweep reads through the descriptors and gathers the union
+    // keys and values into the buffers the first pass does not write; every
+    // pass then runs the bulk-staged downsweep on plain arrays, the last one
+    // storing through the descriptors.
     const uint32_t Gb = (uint32_t)bw.num_sms * kBCtasPerSm, subb = 2;
     const uint32_t ntb = (uint32_t)((m + kBTile - 1) / kBTile), tpcb = (ntb + Gb - 1) / Gb;
+    uint32_t *gk = first_to_b ? bw.a_key : bw.b_key, *gw = vals ? (first_to_b ? bw.a_w : bw.b_w) : nullptr;
+    const uint32_t *in_key = gk, *in_u = src_rows, *in_w = gw;
     for (uint32_t p = 1; p <= passes; ++p) {
       const bool toB = ((passes - p) % 2) == 0;
       uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
-      const bool bulk = p > 1;
       RadixArgs ra{nullptr, nullptr, nullptr, 0, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
-                   (p - 1) * dbits, dbits, bulk ? ntb : ntiles, bulk ? tpcb : tpc, bulk ? kBTile : tile,
-                   bw.table, bw.offsets, bw.status, bv, bulk ? subb : 1u};
-      const uint32_t Gp = bulk ? Gb : G, rows = bulk ? Gb * subb : G;
-      if (p == 1) k_radix_up<true, kBatchFirst><<<G, kRThreads, 0, s>>>(ra);
+                   (p - 1) * dbits, dbits, ntb, tpcb, kBTile, bw.table, bw.offsets, bw.status, bv, subb,
+                   p == 1 ? gk : nullptr, p == 1 ? gw : nullptr};
+      const uint32_t rows = Gb * subb;
+      if (p == 1) k_radix_up<true, kBatchFirst><<<rows, kRThreads, 0, s>>>(ra);
       else k_radix_up<false, kPlain><<<rows, kRThreads, 0, s>>>(ra);
       k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, rows, bw.offsets);
-      const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
-      if (p == 1 && p == passes) launch_down<kBatchOnly>(vals, items, G, dsm, s, ra);
-      else if (p == 1) launch_down<kBatchFirst>(vals, items, G, dsm, s, ra);
-      else if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gp, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-      else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gp, kBThreads, bulk_dyn_smem(false), s>>>(ra);
-      else if (vals) k_radix_down_bulk<true, kPlain><<<Gp, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-      else k_radix_down_bulk<false, kPlain><<<Gp, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+      if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+      else if (vals) k_radix_down_bulk<true, kPlain><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else k_radix_down_bulk<false, kPlain><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
       nl += 3;
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       in_key = ok;
