@@ -443,7 +443,6 @@ __host__ constexpr size_t bulk_dyn_smem(bool vals) { return (size_t)2 * bulk_arr
 template <bool VALS, int MODE>
 __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(RadixArgs a) {
   static_assert(!loads_batch(MODE), "the bulk downsweep reads plain arrays");
-  constexpr int ITEMS = kBItems;
   constexpr uint32_t NA = bulk_arrays(VALS);
   extern __shared__ __align__(128) uint32_t dsm[];  // buf[2][NA][TILE]
   __shared__ __align__(8) uint64_t bar[2];
@@ -474,40 +473,33 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
     bulk_g2s(dst + kBTile, a.in_u + e, kBTile * 4u, &bar[b]);
     if (VALS) bulk_g2s(dst + 2 * kBTile, a.in_w + e, kBTile * 4u, &bar[b]);
   };
-  if (tid == 0) {
-    if (full(t0)) issue(t0, 0);
-    if (t0 + 1 < t1 && full(t0 + 1)) issue(t0 + 1, 1);
-  }
-  // bit b: a copy into buffer b is in flight / parity of its next phase
-  uint32_t pending = (full(t0) ? 1u : 0u) | ((t0 + 1 < t1 && full(t0 + 1)) ? 2u : 0u);
+  if (tid == 0 && full(t0)) issue(t0, 0);
+  // bit b: parity of buffer b's next phase
   uint32_t par = 0u;
+  // Per tile: every warp ranks its items as soon as it has written its part
+  // of the previous tile (the digit counters are per-warp rows); barriers
+  // separate only the steps that read other warps' data.
   for (uint64_t t = t0; t < t1; ++t) {
     const uint32_t b = (uint32_t)((t - t0) & 1u);
     uint32_t *bk = dsm + b * NA * kBTile, *bu = bk + kBTile, *bw = bk + 2 * kBTile;
     const uint64_t tbase = t * kBTile;
     const uint32_t tcount = (uint32_t)min64(kBTile, a.m - tbase);
-#pragma unroll
-    for (int x = 0; x < kBWarps; ++x) wcnt[x][tid] = 0;
+    const uint32_t wpar = (par >> b) & 1u;  // parity of this tile's copy
     if (tcount == kBTile) {
-      if (!mbar_wait(&bar[b], (par >> b) & 1u)) s_abort = 1;
+      if (!mbar_wait(&bar[b], wpar)) s_abort = 1;
       par ^= 1u << b;
-      pending &= ~(1u << b);
-    } else {
+    } else {  // the ragged last tile: plain loads (its buffer held tile t - 2, written out long ago)
       for (uint32_t j = tid; j < tcount; j += kBThreads) {
         bk[j] = __ldcs(a.in_key + tbase + j);
         bu[j] = __ldcs(a.in_u + tbase + j);
         if (VALS) bw[j] = __ldcs(a.in_w + tbase + j);
       }
+      __syncthreads();
     }
-    __syncthreads();
-    if (s_abort) {
-      if (tid == 0) {
-        set_status(a.status, GT_ERR_TIMEOUT);
-        for (uint32_t q = 0; q < 2; ++q)
-          if ((pending >> q) & 1u) mbar_wait(&bar[q], (par >> q) & 1u);
-      }
-      return;
-    }
+    // this warp's counter row (no other warp touches it until the barrier below)
+#pragma unroll
+    for (int x = 0; x < kRBins / 32; ++x) wcnt[w][x * 32 + lane] = 0;
+    __syncwarp();
     // stable rank within the warp (items in order, lanes in order); the
     // tile moves into registers
     uint32_t key[kBItems], uu[kBItems], ww[kBItems], rk[kBItems];
@@ -520,8 +512,8 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       ww[i] = (VALS && act) ? bw[j] : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const bool act = w * (ITEMS * 32) + i * 32 + lane < tcount;
+    for (int i = 0; i < kBItems; ++i) {
+      const bool act = w * (kBItems * 32) + i * 32 + lane < tcount;
       const uint32_t d = (key[i] >> a.shift) & mask;
       const uint32_t mm = match_digit(d, a.dbits, act);
       const uint32_t r = __popc(mm & lanemask_lt());
@@ -532,7 +524,19 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       __syncwarp();
       rk[i] = act ? (c + r) : 0xFFFFFFFFu;
     }
-    __syncthreads();
+    __syncthreads();  // (A) every warp ranked this tile and wrote out the previous one
+    if (s_abort) {
+      if (tid == 0) {
+        set_status(a.status, GT_ERR_TIMEOUT);
+        if (tcount == kBTile) mbar_wait(&bar[b], wpar);  // the only copy that can be in flight
+      }
+      return;
+    }
+    // the other buffer (the previous tile) is free: copy the next tile into it
+    if (t + 1 < t1 && full(t + 1) && tid == 0) {
+      fence_proxy_async();
+      issue(t + 1, b ^ 1u);
+    }
     // per digit (one thread each): exclusive prefix over warps, tile total,
     // then the tile-local start of every digit
     uint32_t run = 0;
@@ -550,17 +554,18 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       if (lane >= (uint32_t)o) inc += y;
     }
     if (lane == 31) wsum[w] = inc;
-    __syncthreads();
+    __syncthreads();  // (B)
     {
       uint32_t before = 0;
 #pragma unroll
       for (int x = 0; x < kBWarps; ++x) before += (x < (int)w) ? wsum[x] : 0u;
       const uint32_t ts = before + inc - tot;  // tile-local start of digit tid
       dst_base[tid] = run_off[tid] - ts;
+      run_off[tid] += tot;
 #pragma unroll
       for (int x = 0; x < kBWarps; ++x) wcnt[x][tid] += ts;  // per-warp bases, tile-local
     }
-    __syncthreads();
+    __syncthreads();  // (C)
     // back into the same buffer in (digit, rank) order; weighted tiles keep
     // (source, value) pairs interleaved in the source and value arrays' space
 #pragma unroll
@@ -573,7 +578,7 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
         else bu[lp] = uu[i];
       }
     }
-    __syncthreads();
+    __syncthreads();  // (D)
     auto put = [&](uint32_t j) {
       const uint32_t k = bk[j];
       const uint32_t d = (k >> a.shift) & mask;
@@ -604,16 +609,7 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
     } else {
       for (uint32_t j = tid; j < tcount; j += kBThreads) put(j);
     }
-    __syncthreads();
-    run_off[tid] += tot;
-    // the buffer is free: prefetch tile t + 2 into it
-    if (t + 2 < t1 && full(t + 2)) {
-      if (tid == 0) {
-        fence_proxy_async();
-        issue(t + 2, b);
-      }
-      pending |= 1u << b;
-    }
+    // no barrier: the next tile's ranking overlaps this write phase
   }
 }
 
