@@ -4,19 +4,21 @@
 // every in-list in ascending source order with parallel edges in CSR order
 // (Gustavson's sort-based transposition, Sec. VI, done as a counting sort
 // per digit).  Every pass streams the data once, so the method is bound by
-// HBM bandwidth whatever the vertex order; it is the method the selector
-// picks for graphs whose working set is far larger than L2.
+// HBM bandwidth whatever the vertex order; it is the method chosen for
+// graphs whose working set is far larger than L2.
 //
-// Per digit pass (8-bit digits, passes = ceil(bits(n-1) / 8)):
-//   upsweep    each persistent CTA counts the digits of its contiguous tile
-//              range -> table[cta][digit]
-//   offsets    exclusive scan of the table in (digit, cta) order
-//   downsweep  each CTA re-reads its tiles in order, ranks every tile stably
-//              in shared memory and scatters with running per-digit offsets
-// The first pass reads the CSR (rows found with the warp window search);
-// the last one writes row_idx / vals_out and the sorted keys.  Degrees come
-// from the run boundaries of the sorted keys, then the look-back scan builds
-// col_ptr.
+// Per call: the row expansion writes the source of every edge; then per
+// digit pass (passes = ceil(bits(n-1) / 8), digits split evenly):
+//   upsweep    per-CTA digit counts of the CTA's contiguous tile range
+//              (with the bulk downsweep, two upsweep CTAs per range)
+//   offsets    exclusive scan of the table in (digit, CTA) order
+//   downsweep  each persistent CTA walks its tiles in order, ranks every tile
+//              stably in shared memory and writes coalesced digit runs from
+//              running per-digit offsets (k_radix_down_bulk: bulk-copy staged
+//              4096-edge tiles, 2 CTAs per SM; k_radix_down: register tiles)
+// The last pass writes row_idx / vals_out and the sorted keys; col_ptr then
+// comes straight from the sorted keys (k_radix_colptr).  Batches run the
+// same passes over the union of their graphs (key = graph, destination).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,7 +74,6 @@ struct RadixArgs {
   const float *vals;
   uint32_t n;
   uint64_t m;
-  const uint32_t *unused_rows;
   // this pass
   const uint32_t *in_key, *in_u, *in_w;
   uint32_t *out_key, *out_u, *out_w;
@@ -87,11 +88,12 @@ struct RadixArgs {
   uint32_t *g_key = nullptr, *g_w = nullptr;  // batch first upsweep: gathered union keys / values
 };
 
-// Pass modes: plain arrays, or a batch whose first pass loads through the
-// descriptors and whose last pass stores through them.
-enum RadixMode : int { kPlain = 0, kBatchFirst = 1, kBatchLast = 2, kBatchOnly = 3 };
-__host__ __device__ constexpr bool loads_batch(int mode) { return mode == kBatchFirst || mode == kBatchOnly; }
-__host__ __device__ constexpr bool stores_batch(int mode) { return mode == kBatchLast || mode == kBatchOnly; }
+// Pass modes: plain arrays; a batch's first upsweep, which reads through the
+// descriptors (and gathers the union keys); a batch's last downsweep, which
+// stores through them.
+enum RadixMode : int { kPlain = 0, kBatchFirst = 1, kBatchLast = 2 };
+__host__ __device__ constexpr bool loads_batch(int mode) { return mode == kBatchFirst; }
+__host__ __device__ constexpr bool stores_batch(int mode) { return mode == kBatchLast; }
 
 // Writes the source row of every edge (src[e] = u for e in row u).  Rows of
 // at most kLongRow edges: 32 rows per warp step, whose edges form one
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_radix_offsets(const uint32_t *__restri
   }
 }
 
-template <bool VALS, int ITEMS, int MODE>
+template <bool VALS, int ITEMS>
 __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
   constexpr uint32_t TILE = kRThreads * ITEMS;
   extern __shared__ __align__(16) uint32_t stage[];  // [TILE] keys | [TILE] sources | [TILE] values
@@ -310,36 +312,17 @@ __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
     const uint32_t tcount = (uint32_t)min64(TILE, a.m - tbase);
     uint32_t key[ITEMS], uu[ITEMS], ww[ITEMS], rk[ITEMS];
     // all of this warp's loads are in flight before any ranking
-    if (loads_batch(MODE)) {
-      uint32_t g = upper_graph(a.batch.eoff, a.batch.ng, base < a.m ? base : a.m - 1);
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const uint64_t e = base + (uint64_t)i * 32 + lane;
+    for (int i = 0; i < ITEMS; ++i) {
+      const uint64_t e = base + (uint64_t)i * 32 + lane;
+      if (e < a.m) {
+        key[i] = __ldcs(a.in_key + e);
+        uu[i] = __ldcs(a.in_u + e);
+        ww[i] = VALS ? __ldcs(a.in_w + e) : 0u;
+      } else {
         key[i] = 0u;
         uu[i] = 0u;
         ww[i] = 0u;
-        if (e < a.m) {
-          while (e >= a.batch.eoff[g + 1]) ++g;
-          const gt_graph_desc &d = a.batch.descs[g];
-          const uint64_t le = e - a.batch.eoff[g];
-          key[i] = (g << a.batch.vbits) | (__ldcs(d.col_idx + le) & ((1u << a.batch.vbits) - 1u));
-          uu[i] = __ldcs(a.in_u + e);
-          if (VALS) ww[i] = __float_as_uint(__ldcs(d.vals + le));
-        }
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const uint64_t e = base + (uint64_t)i * 32 + lane;
-        if (e < a.m) {
-          key[i] = __ldcs(a.in_key + e);
-          uu[i] = __ldcs(a.in_u + e);
-          ww[i] = VALS ? __ldcs(a.in_w + e) : 0u;
-        } else {
-          key[i] = 0u;
-          uu[i] = 0u;
-          ww[i] = 0u;
-        }
       }
     }
     __syncthreads();
@@ -403,16 +386,8 @@ __global__ void __launch_bounds__(kRThreads) k_radix_down(RadixArgs a) {
       const uint32_t d = (k >> a.shift) & mask;
       const uint64_t pos = run_off[d] + (j - tile_start[d]);
       a.out_key[pos] = k;
-      if (stores_batch(MODE)) {
-        const uint32_t g = k >> a.batch.vbits;
-        const gt_graph_desc &gd = a.batch.descs[g];
-        const uint64_t lp = pos - a.batch.eoff[g];
-        gd.row_idx[lp] = su[j];
-        if (VALS) gd.vals_out[lp] = __uint_as_float(sw[j]);
-      } else {
-        a.out_u[pos] = su[j];
-        if (VALS) a.out_w[pos] = sw[j];
-      }
+      a.out_u[pos] = su[j];
+      if (VALS) a.out_w[pos] = sw[j];
     }
     __syncthreads();
     run_off[threadIdx.x] += tot;
@@ -739,15 +714,15 @@ static uint32_t key_bits_of(uint32_t n) {
   return bits ? bits : 1u;
 }
 
-template <int ITEMS, int MODE>
+template <int ITEMS>
 static cudaError_t allow_down() {
-  cudaError_t e1 = allow_max_dynamic_smem(k_radix_down<true, ITEMS, MODE>);
-  cudaError_t e2 = allow_max_dynamic_smem(k_radix_down<false, ITEMS, MODE>);
+  cudaError_t e1 = allow_max_dynamic_smem(k_radix_down<true, ITEMS>);
+  cudaError_t e2 = allow_max_dynamic_smem(k_radix_down<false, ITEMS>);
   return e1 != cudaSuccess ? e1 : e2;
 }
 
 cudaError_t configure_radix() {
-  cudaError_t e[2] = {allow_down<8, kPlain>(), allow_down<16, kPlain>()};
+  cudaError_t e[2] = {allow_down<8>(), allow_down<16>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   cudaError_t b[4] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
@@ -759,14 +734,13 @@ cudaError_t configure_radix() {
   return cudaSuccess;
 }
 
-template <int MODE>
 static void launch_down(bool vals, uint32_t items, uint32_t G, size_t dsm, cudaStream_t s, const RadixArgs &ra) {
   if (items == 8) {
-    if (vals) k_radix_down<true, 8, MODE><<<G, kRThreads, dsm, s>>>(ra);
-    else k_radix_down<false, 8, MODE><<<G, kRThreads, dsm, s>>>(ra);
+    if (vals) k_radix_down<true, 8><<<G, kRThreads, dsm, s>>>(ra);
+    else k_radix_down<false, 8><<<G, kRThreads, dsm, s>>>(ra);
   } else {
-    if (vals) k_radix_down<true, 16, MODE><<<G, kRThreads, dsm, s>>>(ra);
-    else k_radix_down<false, 16, MODE><<<G, kRThreads, dsm, s>>>(ra);
+    if (vals) k_radix_down<true, 16><<<G, kRThreads, dsm, s>>>(ra);
+    else k_radix_down<false, 16><<<G, kRThreads, dsm, s>>>(ra);
   }
 }
 
@@ -812,7 +786,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   for (uint32_t p = 1; p <= passes; ++p) {
     const bool toB = ((passes - p) % 2) == 0;
     uint32_t *ok = toB ? w.r_b_key : w.r_a_key, *ou = toB ? b_u : w.r_a_u, *ow = toB ? b_w : w.r_a_w;
-    RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
+    RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, in_key, in_u, in_w, ok, ou, ow,
                  (p - 1) * dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status, BatchView{}, sub};
     if (p == 1) k_radix_up<true, kPlain><<<G * sub, kRThreads, 0, s>>>(ra);
     else k_radix_up<false, kPlain><<<G * sub, kRThreads, 0, s>>>(ra);
@@ -823,7 +797,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
       else k_radix_down_bulk<false, kPlain><<<G, kBThreads, bulk_dyn_smem(false), s>>>(ra);
     } else {
       const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
-      launch_down<kPlain>(vals, items, G, dsm, s, ra);
+      launch_down(vals, items, G, dsm, s, ra);
     }
     if (ev && ev->ndown + 2 <= 8) {
       cudaEventRecord(ev->down[ev->ndown + 1], s);
@@ -966,7 +940,7 @@ cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_
     for (uint32_t p = 1; p <= passes; ++p) {
       const bool toB = ((passes - p) % 2) == 0;
       uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
-      RadixArgs ra{nullptr, nullptr, nullptr, 0, m, nullptr, in_key, in_u, in_w, ok, ou, ow,
+      RadixArgs ra{nullptr, nullptr, nullptr, 0, m, in_key, in_u, in_w, ok, ou, ow,
                    (p - 1) * dbits, dbits, ntb, tpcb, kBTile, bw.table, bw.offsets, bw.status, bv, subb,
                    p == 1 ? gk : nullptr, p == 1 ? gw : nullptr};
       const uint32_t rows = Gb * subb;
