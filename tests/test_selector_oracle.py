@@ -218,3 +218,31 @@ def test_shipped_selector_report_reproduces_in_fp64():
     best = np.where(t > 0, t, np.inf).min(axis=1)
     reg = t[np.arange(len(idx)), idx] / best
     assert reg.mean() == pytest.approx(rep["test"]["learned"]["mean"], rel=1e-6)
+
+
+def test_trainer_targets_and_regret_helpers():
+    """Log-regret targets are 0 at the best grid point and ln(t/t_best)
+    elsewhere, masked where a point was not timed; regret is t_pick/t_best."""
+    from paper_2501_06872_gb300 import selector_train as st
+    times = np.array([[2.0, 1.0, 4.0, -1.0], [3.0, 6.0, 3.0, 1.5]])
+    y, m = st.targets(times)
+    assert np.allclose(y[0], [math.log(2.0), 0.0, math.log(4.0), 0.0])
+    assert np.allclose(m, [[1, 1, 1, 0], [1, 1, 1, 1]])
+    assert np.allclose(y[1], [math.log(2.0), math.log(4.0), math.log(2.0), 0.0])
+    r = st.regrets(times, np.array([2, 3]))
+    assert np.allclose(r, [4.0, 1.0])
+    s = st.summary(r)
+    assert s["mean"] == pytest.approx(2.5) and s["max"] == 4.0 and s["optimal_share"] == 0.5
+    mu, sd = st.standardise(np.array([[1.0, 5.0], [3.0, 5.0]]))
+    assert np.allclose(mu, [2.0, 5.0]) and np.allclose(sd, [1.001, 0.001])
+
+
+def test_trainer_graph_specs_follow_the_stated_ranges():
+    from paper_2501_06872_gb300 import selector_train as st
+    specs = [st.graph_spec(i) for i in range(256)]
+    assert all(0.25 <= s["a"] <= 0.70 for s in specs)
+    assert all(abs(s["b"] - (1 - s["a"] - 0.05) / 2) < 1e-12 and s["b"] == s["c"] for s in specs)
+    assert {s["scale"] for s in specs} <= set(range(18, 27))
+    assert all(8 <= s["edge_factor"] <= 32 for s in specs)
+    assert {s["order"] for s in specs} == {"degree", "random"}
+    assert specs[3] == st.graph_spec(3)  # seeded
