@@ -88,8 +88,9 @@ typedef struct gt_config {
 /* GT_METHOD_HLH: PoTra's hash-based LDV-HDV method (Algorithm 2; hdv_k = 0 is
  *   Atomic GT, Algorithm 1) with the LDV list sort.
  * GT_METHOD_RADIX: stable LSD radix sort of the CSR edge sequence by
- *   destination (8-bit digits); streams the data once per digit, independent
- *   of vertex order.  Uses 12-16 bytes per edge of extra workspace. */
+ *   destination (ceil(bits / 8) passes of equal digits of at most 8 bits);
+ *   streams the data once per digit, independent of vertex order.  Uses
+ *   12-16 bytes per edge of extra workspace. */
 #define GT_METHOD_HLH 0u
 #define GT_METHOD_RADIX 1u
 

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -15,6 +16,20 @@ namespace gt {
 cudaError_t configure_steps();
 cudaError_t configure_sort();
 cudaError_t configure_radix();
+
+// Raises the kernels' shared-memory limits, once per device (thread-safe).
+cudaError_t configure_kernels(int device) {
+  static std::mutex mu;
+  static std::vector<char> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((size_t)device >= done.size()) done.resize((size_t)device + 1, 0);
+  if (done[(size_t)device]) return cudaSuccess;
+  cudaError_t e = configure_steps();
+  if (e == cudaSuccess) e = configure_sort();
+  if (e == cudaSuccess) e = configure_radix();
+  if (e == cudaSuccess) done[(size_t)device] = 1;
+  return e;
+}
 }  // namespace gt
 
 struct gt_plan_s {
@@ -289,18 +304,14 @@ gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, i
     delete p;
     return GT_ERR_CUDA;
   }
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e1 = gt::configure_steps();
-    cudaError_t e2 = gt::configure_sort();
-    if (e2 == cudaSuccess) e2 = gt::configure_radix();
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
-      from_cuda(e1 != cudaSuccess ? e1 : e2);
+  {
+    cudaError_t ce = gt::configure_kernels(p->device);
+    if (ce != cudaSuccess) {
+      from_cuda(ce);
       cudaGetLastError();
       delete p;
       return GT_ERR_CUDA;
     }
-    configured = true;
   }
   p->w.n = n_vertices;
   p->w.m = n_edges;

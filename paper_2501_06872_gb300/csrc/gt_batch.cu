@@ -15,9 +15,6 @@
 #include "gt_internal.h"
 
 namespace gt {
-cudaError_t configure_steps();
-cudaError_t configure_sort();
-cudaError_t configure_radix();
 }  // namespace gt
 
 struct gt_batch_plan_s {
@@ -121,15 +118,10 @@ gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_
     delete p;
     return GT_ERR_CUDA;
   }
-  static bool configured = false;
-  if (!configured) {
-    if (gt::configure_steps() != cudaSuccess || gt::configure_sort() != cudaSuccess ||
-        gt::configure_radix() != cudaSuccess) {
-      cudaGetLastError();
-      delete p;
-      return GT_ERR_CUDA;
-    }
-    configured = true;
+  if (gt::configure_kernels(p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return GT_ERR_CUDA;
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);

@@ -138,7 +138,8 @@ uint32_t smem_count_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged,
 uint32_t smem_scatter_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged, uint32_t stage_edges,
                             int has_vals);
 
-// Raises the dynamic shared-memory limits of the kernels once per process.
-cudaError_t configure_kernels();
+// Raises the dynamic shared-memory limits of the kernels, once per device
+// (the current device must be `device`; thread-safe).
+cudaError_t configure_kernels(int device);
 
 }  // namespace gt
