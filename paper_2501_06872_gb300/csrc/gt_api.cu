@@ -166,18 +166,14 @@ gt_status plan_alloc_ws(gt_plan p) {
   do {                                                                         \
     if ((st = plan_alloc(p, (void **)&w.field, (bytes))) != GT_OK) return st; \
   } while (0)
-  GT_AL(deg, n * 4);
-  GT_AL(scan_state, (size_t)w.ntiles * 8);
   GT_AL(status, 4);
   GT_AL(meta, gt::kMetaCount * 4);
   GT_AL(meta64, 4 * 8);
-  if (w.method == GT_METHOD_RADIX) {
-    const size_t tiles = (m + 4095) / 4096;
+  if (w.method == GT_METHOD_RADIX) {  // col_ptr comes from the sorted keys: no degree array, no scan state
     GT_AL(r_a_key, m * 4);
     GT_AL(r_a_u, m * 4);
     if (w.has_vals) GT_AL(r_a_w, m * 4);
     GT_AL(r_b_key, m * 4);
-    (void)tiles;
     GT_AL(r_long, (m / 2049 + 1) * 4);
     w.r_gap_cap = (uint32_t)(n / 1024 + 2);
     GT_AL(r_gaps, (1 + 2 * (size_t)w.r_gap_cap) * 8);
@@ -191,6 +187,8 @@ gt_status plan_alloc_ws(gt_plan p) {
     if (cudaMemset(w.meta64, 0, 32) != cudaSuccess) return GT_ERR_CUDA;
     return GT_OK;
   }
+  GT_AL(deg, n * 4);
+  GT_AL(scan_state, (size_t)w.ntiles * 8);
   GT_AL(cursor, n * 8);
   GT_AL(hdv_cnt, (size_t)w.P * (w.kmax ? w.kmax : 1) * 4);
   GT_AL(hdv_ids, (w.kmax ? w.kmax : 1) * 4);
