@@ -368,10 +368,13 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    import __graft_entry__
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import __graft_entry__
+        if local == 0:  # one build per node; the other ranks wait for it
+            __graft_entry__.build()
+        dist.barrier()
     __graft_entry__.build()
     from paper_2501_06872_gb300 import binding
     from paper_2501_06872_gb300.inputs import gpu as ggen
