@@ -9,7 +9,8 @@
  * bit-for-bit).  Every CSC list comes out in ascending source order, and
  * parallel edges with the same (source, destination) keep their CSR order:
  * the result is the stable sort of the CSR edge sequence by destination.
- * The result never depends on the gt_config used.
+ * The result never depends on the gt_config used (except with
+ * GT_FLAG_UNSORTED, which drops the order within lists).
  *
  * Method (all steps run in CUDA kernels for sm_103a; there is no CPU path):
  *   Step 0  (Sec. IV-C, Step 0)  sample ceil(n * sample_permille / 1000)
@@ -84,6 +85,13 @@ typedef struct gt_config {
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
 #define GT_FLAG_NO_GRAPH 2u   /* batches: launch kernels directly, no CUDA graph        */
+/* GT_METHOD_HLH only: skip the LDV list sort; the scatter writes LDV entries
+ * straight to the outputs, so the lists of low-degree destinations come out in
+ * arbitrary order (each holds the right multiset of (source, value) pairs;
+ * HDV lists stay in edge order).  This is the output of PoTra and Atomic GT as
+ * the paper times them (Sec. V excludes the sort).  The radix method ignores
+ * it: its lists are always sorted. */
+#define GT_FLAG_UNSORTED 4u
 
 /* GT_METHOD_HLH: PoTra's hash-based LDV-HDV method (Algorithm 2; hdv_k = 0 is
  *   Atomic GT, Algorithm 1) with the LDV list sort.

@@ -641,7 +641,7 @@ struct ScatterArgs {
   const uint64_t *col_ptr;
   uint32_t *row_idx;
   float *vals_out;
-  unsigned long long *ldv64;  // weighted: LDV entries go here (one 8-byte store)
+  unsigned long long *ldv64;  // weighted, sorted output: LDV entries go here (one 8-byte store); null = outputs
   uint32_t *status;
   int flag_mode;
   uint32_t stage_edges;
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
           wbits = (uint32_t)(e - (my_u == row_first ? rs_first : rs_last));
         }
       }
-      if (VALS && ldv) {
+      if (VALS && ldv && a.ldv64) {  // sorted output: LDV entries wait in the scratch for the list sort
         a.ldv64[slot] = ((unsigned long long)wbits << 32) | uu;
       } else {
         a.row_idx[slot] = uu;
@@ -940,7 +940,11 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   mark(1);
 
   // partitions
-  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n, w.m, w.P, w.psize, w.flag_mode || !w.has_vals,
+  // unsorted output (GT_FLAG_UNSORTED): no LDV sort, no split-row tags
+  const bool unsorted = (cfg.flags & GT_FLAG_UNSORTED) != 0;
+  const int flag_mode = unsorted ? 0 : w.flag_mode;
+  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n, w.m, w.P, w.psize,
+                                                    unsorted || w.flag_mode || !w.has_vals,
                                                      w.part, w.status);
   nl += 2;  // partition + count
 
@@ -983,8 +987,8 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // Step 3
   ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n,         w.m,       w.part,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
-                 pb.col_ptr, pb.row_idx, pb.vals_out, (unsigned long long *)w.scratch, w.status, w.flag_mode,
-                 w.stage_edges};
+                 pb.col_ptr, pb.row_idx, pb.vals_out, unsorted ? nullptr : (unsigned long long *)w.scratch,
+                 w.status, flag_mode, w.stage_edges};
   const bool vals = pb.vals != nullptr;
 #define GT_SC(H, V, ST) k_scatter<H, V, ST><<<w.G, threads, w.smem_scatter, s>>>(sa)
   if (hdv) {
@@ -1010,8 +1014,10 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   mark(4);
 
   // LDV sort
-  err = launch_sort(w, cfg, pb, s);
-  nl += 4;
+  if (!unsorted) {
+    err = launch_sort(w, cfg, pb, s);
+    nl += 4;
+  }
   mark(5);
   if (launches) *launches = nl;
   return err;

@@ -254,6 +254,50 @@ def test_host_path_matches_device_path():
     plan.close()
 
 
+def _column_multisets(cp, ri, vo, n):
+    """(destination, source, value bits) triples sorted: the CSC as a multiset per list."""
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(cp.astype(np.int64)))
+    vb = np.zeros_like(ri) if vo is None else vo.view(np.uint32)
+    o = np.lexsort((vb, ri, cols))
+    return cols[o], ri[o], vb[o]
+
+
+@pytest.mark.parametrize("name", ["atomic", "hdv64", "hdv512_staged", "noagg_staged"])
+def test_unsorted_mode_keeps_every_list_as_a_multiset(name):
+    """GT_FLAG_UNSORTED (the paper's output, no LDV sort): col_ptr is exact and
+    every list holds the oracle's (source, value) multiset."""
+    from paper_2501_06872_gb300 import binding
+    graphs = [inputs.rmat_csr(13, 16, seed=5, order="random", weighted=True),
+              inputs.random_csr(4000, 90001, seed=3, weighted=True, hot=7, hot_frac=0.5)]
+    for n, rp, ci, vv in graphs:
+        for vals in (vv, None):
+            exp = oracle.transpose(rp, ci, vals)
+            c = dict(CONFIGS[name])
+            c["flags"] = c.get("flags", 1) | binding.FLAG_UNSORTED
+            got = gpu_transpose(rp, ci, vals, config(**c))
+            assert np.array_equal(got[0], exp[0])
+            for x, y in zip(_column_multisets(got[0], got[1], got[2], n), _column_multisets(exp[0], exp[1], exp[2], n)):
+                assert np.array_equal(x, y)
+
+
+def test_unsorted_mode_split_hub_rows():
+    """Hub rows split over partitions with many parallel edges: still the right multisets."""
+    from paper_2501_06872_gb300 import binding
+    rng = np.random.default_rng(31)
+    n = 3000
+    rows = [np.concatenate([np.full(20000, 7), rng.integers(0, n, 30000)])] + \
+           [rng.integers(0, n, rng.integers(0, 30)) for _ in range(n - 1)]
+    rp = np.zeros(n + 1, np.uint64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate(rows).astype(np.uint32)
+    vv = rng.standard_normal(len(ci)).astype(np.float32)
+    exp = oracle.transpose(rp, ci, vv)
+    got = gpu_transpose(rp, ci, vv, config(hdv_k=0, warp_edges=2048, flags=1 | binding.FLAG_UNSORTED))
+    assert np.array_equal(got[0], exp[0])
+    for x, y in zip(_column_multisets(got[0], got[1], got[2], n), _column_multisets(exp[0], exp[1], exp[2], n)):
+        assert np.array_equal(x, y)
+
+
 def test_host_async_pipeline():
     """Three overlapped host calls with different values, each into its own
     pinned output buffers, all equal to the oracle."""
