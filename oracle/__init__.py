@@ -10,6 +10,8 @@ other.
 thread, which turns it into a stable counting sort of the CSR edge sequence by
 destination (see ``gt_oracle.c``).  The result is the CSC of Sec. II-A with
 every in-list in ascending source order and duplicate edges in CSR order.
+Rectangular matrices (``n_cols`` columns, ``len(row_ptr) - 1`` rows) follow
+the same definition; the default is the square case of a graph.
 """
 from __future__ import annotations
 
@@ -56,12 +58,17 @@ def _load():
     P = ctypes.c_void_p
     lib.oracle_transpose.argtypes = [ctypes.c_uint32, ctypes.c_uint64, P, P, P, P, P, P]
     lib.oracle_transpose.restype = ctypes.c_int
+    lib.oracle_transpose_rect.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P, P, P, P, P, P]
+    lib.oracle_transpose_rect.restype = ctypes.c_int
     lib.oracle_transpose_range.argtypes = [ctypes.c_uint32, ctypes.c_uint64, P, P, P,
                                            ctypes.c_uint32, ctypes.c_uint32, P, P, P]
     lib.oracle_transpose_range.restype = ctypes.c_int
     lib.oracle_columns.argtypes = [ctypes.c_uint32, ctypes.c_uint64, P, P, P, P, ctypes.c_uint64,
                                    P, P, P, P, ctypes.c_uint64]
     lib.oracle_columns.restype = ctypes.c_int
+    lib.oracle_columns_rect.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P, P, P, P,
+                                        ctypes.c_uint64, P, P, P, P, ctypes.c_uint64]
+    lib.oracle_columns_rect.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -83,15 +90,24 @@ def _inputs(row_ptr, col_idx, vals):
     return n, row_ptr, col_idx, vals
 
 
-def transpose(row_ptr, col_idx, vals=None):
-    """CSR -> CSC.  Returns (col_ptr u64[n+1], row_idx u32[m], vals_out f32[m] or None)."""
+def _cols(n, n_cols):
+    n_cols = n if n_cols is None else int(n_cols)
+    if n_cols < 0 or n_cols > 0xFFFFFFFF:
+        raise ValueError("n_cols must lie in [0, 2^32)")
+    return n_cols
+
+
+def transpose(row_ptr, col_idx, vals=None, n_cols=None):
+    """CSR -> CSC.  Returns (col_ptr u64[n_cols+1], row_idx u32[m], vals_out
+    f32[m] or None); n_cols defaults to the row count (a graph)."""
     n, row_ptr, col_idx, vals = _inputs(row_ptr, col_idx, vals)
+    nc = _cols(n, n_cols)
     m = col_idx.shape[0]
-    col_ptr = np.empty(n + 1, dtype=np.uint64)
+    col_ptr = np.empty(nc + 1, dtype=np.uint64)
     row_idx = np.empty(m, dtype=np.uint32)
     vals_out = np.empty(m, dtype=np.float32) if vals is not None else None
-    rc = _load().oracle_transpose(n, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
-                                  _ptr(col_ptr), _ptr(row_idx), _ptr(vals_out))
+    rc = _load().oracle_transpose_rect(n, nc, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                       _ptr(col_ptr), _ptr(row_idx), _ptr(vals_out))
     if rc:
         raise OracleError(rc)
     return col_ptr, row_idx, vals_out
@@ -113,31 +129,32 @@ def transpose_range(row_ptr, col_idx, vals, v_lo, v_hi):
     return col_ptr, rows, vo
 
 
-def columns(row_ptr, col_idx, vals, cols):
+def columns(row_ptr, col_idx, vals, cols, n_cols=None):
     """Sampled columns: (col_start u64[k], deg u64[k], rows concat u32, vals concat f32|None)."""
     n, row_ptr, col_idx, vals = _inputs(row_ptr, col_idx, vals)
+    nc = _cols(n, n_cols)
     m = col_idx.shape[0]
     cols = np.ascontiguousarray(np.unique(np.asarray(cols, dtype=np.uint32)))
     k = cols.shape[0]
     start = np.empty(k, dtype=np.uint64)
     deg = np.empty(k, dtype=np.uint64)
     lib = _load()
-    rc = lib.oracle_columns(n, m, _ptr(row_ptr), _ptr(col_idx), None, _ptr(cols), k,
-                            _ptr(start), _ptr(deg), None, None, 0)
+    rc = lib.oracle_columns_rect(n, nc, m, _ptr(row_ptr), _ptr(col_idx), None, _ptr(cols), k,
+                                 _ptr(start), _ptr(deg), None, None, 0)
     if rc:
         raise OracleError(rc)
     cap = int(deg.sum())
     rows = np.empty(max(cap, 1), dtype=np.uint32)
     vo = np.empty(max(cap, 1), dtype=np.float32) if vals is not None else None
-    rc = lib.oracle_columns(n, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(cols), k,
-                                _ptr(start), _ptr(deg), _ptr(rows), _ptr(vo), cap)
+    rc = lib.oracle_columns_rect(n, nc, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(cols), k,
+                                 _ptr(start), _ptr(deg), _ptr(rows), _ptr(vo), cap)
     if rc:
         raise OracleError(rc)
     return cols, start, deg, rows[:cap], (vo[:cap] if vo is not None else None)
 
 
-def timed_transpose(row_ptr, col_idx, vals=None):
+def timed_transpose(row_ptr, col_idx, vals=None, n_cols=None):
     """Run ``transpose`` once and return (outputs, wall seconds)."""
     t0 = time.perf_counter()
-    out = transpose(row_ptr, col_idx, vals)
+    out = transpose(row_ptr, col_idx, vals, n_cols)
     return out, time.perf_counter() - t0

@@ -15,6 +15,11 @@
  * same (source, destination) keep their CSR order.  That is exactly a stable
  * sort of the CSR edge sequence by destination.
  *
+ * Rectangular matrices (a sparse n_rows x n_cols matrix in CSR: row_ptr has
+ * n_rows + 1 entries, col_idx values lie in [0, n_cols)) follow the same
+ * definition: the CSC has n_cols + 1 offsets and lists row IDs.  A graph is
+ * the square case n_rows = n_cols = n.
+ *
  * Algorithm: the three steps of Atomic GT (Algorithm 1) run by ONE thread, so
  * every fetch_and_add becomes a plain increment and the edge visit order is
  * the CSR order -- a sequential counting sort, stable by construction:
@@ -28,49 +33,52 @@
 
 #define OR_OK 0
 #define OR_ERR_ARG 1
-#define OR_ERR_RANGE 2   /* some col_idx[e] >= n */
-#define OR_ERR_ROWPTR 3  /* row_ptr[0] != 0, not monotone, or row_ptr[n] != m */
+#define OR_ERR_RANGE 2   /* some col_idx[e] >= n_cols */
+#define OR_ERR_ROWPTR 3  /* row_ptr[0] != 0, not monotone, or row_ptr[n_rows] != m */
 #define OR_ERR_NOMEM 4
 #define OR_ERR_DEGREE 5  /* an in-degree does not fit 32 bits (not reachable for m <= 2^32 - 1) */
 
-static int check_csr(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx) {
+static int check_csr(uint32_t n_rows, uint32_t n_cols, uint64_t m, const uint64_t *row_ptr,
+                     const uint32_t *col_idx) {
     if (!row_ptr) return OR_ERR_ARG;
     if (m > 0 && !col_idx) return OR_ERR_ARG;
-    if (row_ptr[0] != 0 || row_ptr[n] != m) return OR_ERR_ROWPTR;
-    for (uint64_t u = 0; u < n; ++u)
+    if (row_ptr[0] != 0 || row_ptr[n_rows] != m) return OR_ERR_ROWPTR;
+    for (uint64_t u = 0; u < n_rows; ++u)
         if (row_ptr[u] > row_ptr[u + 1]) return OR_ERR_ROWPTR;
     for (uint64_t e = 0; e < m; ++e)
-        if (col_idx[e] >= n) return OR_ERR_RANGE;
+        if (col_idx[e] >= n_cols) return OR_ERR_RANGE;
     return OR_OK;
 }
 
 /*
- * Full transposition, Algorithm 1 run serially.  col_ptr has n+1 entries,
- * row_idx m entries, vals_out m entries when vals != NULL.
+ * Full transposition of an n_rows x n_cols matrix, Algorithm 1 run serially.
+ * col_ptr has n_cols + 1 entries, row_idx m entries, vals_out m entries when
+ * vals != NULL.
  */
-int oracle_transpose(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx,
-                     const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out) {
-    int st = check_csr(n, m, row_ptr, col_idx);
+int oracle_transpose_rect(uint32_t n_rows, uint32_t n_cols, uint64_t m, const uint64_t *row_ptr,
+                          const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
+                          float *vals_out) {
+    int st = check_csr(n_rows, n_cols, m, row_ptr, col_idx);
     if (st) return st;
     if (!col_ptr || (m > 0 && !row_idx) || (vals && m > 0 && !vals_out)) return OR_ERR_ARG;
 
-    /* Step 1: in-degrees (counters). */
-    uint64_t *ip = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    /* Step 1: in-degrees (counters), one per column. */
+    uint64_t *ip = (uint64_t *)calloc((size_t)n_cols + 1, sizeof(uint64_t));
     if (!ip) return OR_ERR_NOMEM;
     for (uint64_t e = 0; e < m; ++e) ip[col_idx[e]] += 1;
 
     /* Step 2: t_offsets = exclusive prefix sum; IP starts as a copy. */
     uint64_t run = 0;
-    for (uint64_t v = 0; v < n; ++v) {
+    for (uint64_t v = 0; v < n_cols; ++v) {
         uint64_t d = ip[v];
         col_ptr[v] = run;
         ip[v] = run;
         run += d;
     }
-    col_ptr[n] = run;
+    col_ptr[n_cols] = run;
 
-    /* Step 3: visit edges in CSR order and append u to the list of v. */
-    for (uint64_t u = 0; u < n; ++u) {
+    /* Step 3: visit edges in CSR order (rows ascending) and append u to the list of v. */
+    for (uint64_t u = 0; u < n_rows; ++u) {
         for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
             uint64_t slot = ip[col_idx[e]]++;
             row_idx[slot] = (uint32_t)u;
@@ -79,6 +87,12 @@ int oracle_transpose(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint
     }
     free(ip);
     return OR_OK;
+}
+
+/* The square case: a graph with n vertices. */
+int oracle_transpose(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx,
+                     const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out) {
+    return oracle_transpose_rect(n, n, m, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out);
 }
 
 /*
@@ -91,7 +105,7 @@ int oracle_transpose(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint
 int oracle_transpose_range(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx,
                            const float *vals, uint32_t v_lo, uint32_t v_hi, uint64_t *col_ptr_part,
                            uint32_t *row_idx_part, float *vals_out_part) {
-    int st = check_csr(n, m, row_ptr, col_idx);
+    int st = check_csr(n, n, m, row_ptr, col_idx);
     if (st) return st;
     if (v_lo > v_hi || v_hi > n || !col_ptr_part) return OR_ERR_ARG;
     uint32_t w = v_hi - v_lo;
@@ -143,13 +157,14 @@ static size_t lower_bound_u32(const uint32_t *a, size_t len, uint32_t x) {
  * call fails with OR_ERR_ARG if the lists do not fit).  With out_rows == NULL
  * only col_start and col_deg are produced.
  */
-int oracle_columns(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx,
-                   const float *vals, const uint32_t *cols, uint64_t ncols, uint64_t *col_start,
-                   uint64_t *col_deg, uint32_t *out_rows, float *out_vals, uint64_t out_cap) {
-    int st = check_csr(n, m, row_ptr, col_idx);
+int oracle_columns_rect(uint32_t n_rows, uint32_t n_cols, uint64_t m, const uint64_t *row_ptr,
+                        const uint32_t *col_idx, const float *vals, const uint32_t *cols, uint64_t ncols,
+                        uint64_t *col_start, uint64_t *col_deg, uint32_t *out_rows, float *out_vals,
+                        uint64_t out_cap) {
+    int st = check_csr(n_rows, n_cols, m, row_ptr, col_idx);
     if (st) return st;
     for (uint64_t i = 0; i < ncols; ++i) {
-        if (cols[i] >= n || (i > 0 && cols[i] <= cols[i - 1])) return OR_ERR_ARG;
+        if (cols[i] >= n_cols || (i > 0 && cols[i] <= cols[i - 1])) return OR_ERR_ARG;
     }
     /* below[i] = number of edges whose destination lies in [cols[i-1], cols[i]) ... counted
        by bucketing every destination at its lower-bound position among cols. */
@@ -176,7 +191,7 @@ int oracle_columns(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32
     /* Write cursor for each sampled column inside the concatenated output. */
     uint64_t acc = 0;
     for (uint64_t i = 0; i < ncols; ++i) { uint64_t d = deg[i]; deg[i] = acc; acc += d; }
-    for (uint64_t u = 0; u < n; ++u) {
+    for (uint64_t u = 0; u < n_rows; ++u) {
         for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
             uint32_t v = col_idx[e];
             size_t pos = lower_bound_u32(cols, (size_t)ncols, v);
@@ -190,4 +205,11 @@ int oracle_columns(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32
     free(bucket);
     free(deg);
     return OR_OK;
+}
+
+int oracle_columns(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx,
+                   const float *vals, const uint32_t *cols, uint64_t ncols, uint64_t *col_start,
+                   uint64_t *col_deg, uint32_t *out_rows, float *out_vals, uint64_t out_cap) {
+    return oracle_columns_rect(n, n, m, row_ptr, col_idx, vals, cols, ncols, col_start, col_deg, out_rows,
+                               out_vals, out_cap);
 }

@@ -220,18 +220,35 @@ def er_csr(n, m, seed=1, weighted=False, order="random"):
     return (n,) + csr_from_edges(n, src, dst, vals)
 
 
-def random_csr(n, m, seed=1, weighted=True, hot=0, hot_frac=0.0):
+def random_csr(n, m, seed=1, weighted=True, hot=0, hot_frac=0.0, n_cols=None):
     """Small uniform graph for edge-case tests; optionally a fraction of the
-    edges goes to ``hot`` distinct high-in-degree vertices."""
+    edges goes to ``hot`` distinct high-in-degree vertices.  With n_cols, an
+    n x n_cols matrix (destinations drawn from [0, n_cols))."""
+    nc = n if n_cols is None else n_cols
     key = stream_key(seed, 99)
     r = draw(key, np.arange(2 * m + 1, dtype=np.uint64))
     src = ((r[:m] >> np.uint64(32)) * np.uint64(n)) >> np.uint64(32)
-    dst = ((r[m:2 * m] >> np.uint64(32)) * np.uint64(n)) >> np.uint64(32)
+    dst = ((r[m:2 * m] >> np.uint64(32)) * np.uint64(nc)) >> np.uint64(32)
     if hot and hot_frac > 0:
         pick = (r[m:2 * m] & np.uint64(0xFFFF)) < np.uint64(int(hot_frac * 65536))
-        dst = np.where(pick, (r[m:2 * m] >> np.uint64(16)) % np.uint64(min(hot, n)), dst)
+        dst = np.where(pick, (r[m:2 * m] >> np.uint64(16)) % np.uint64(min(hot, nc)), dst)
     vals = uniform_vals(m, seed, -1.0, 1.0) if weighted else None
     return (n,) + csr_from_edges(n, src.astype(np.uint32), dst.astype(np.uint32), vals)
+
+
+def fold_rect(row_ptr, col_idx, row_shift: int, col_shift: int):
+    """Rectangular matrix from a square CSR by relabelling: rows u become
+    u >> row_shift (2^row_shift consecutive rows merge, keeping their edges in
+    CSR order) and columns v become v >> col_shift.  For a graph with
+    n = 2^s vertices the result is 2^(s - row_shift) x 2^(s - col_shift).
+    Returns (n_rows, n_cols, row_ptr, col_idx)."""
+    row_ptr = np.asarray(row_ptr, dtype=np.uint64)
+    n = row_ptr.shape[0] - 1
+    if n & ((1 << row_shift) - 1) or n & ((1 << col_shift) - 1):
+        raise ValueError("the vertex count must be a multiple of both folds")
+    rp = np.ascontiguousarray(row_ptr[::1 << row_shift])
+    ci = (np.asarray(col_idx, dtype=np.uint32) >> np.uint32(col_shift)).astype(np.uint32)
+    return n >> row_shift, n >> col_shift, rp, ci
 
 
 # ----------------------------------------------------------------------------

@@ -40,3 +40,13 @@ def test_zipf_matrix_shape():
     assert col_idx.max() < n and np.all(np.diff(row_ptr.astype(np.int64)) >= 1)
     assert -1.0 <= vals.min() and vals.max() < 1.0
     assert 8.0 < col_idx.size / n < 16.0
+
+
+def test_fold_rect_relabels_rows_and_columns():
+    n, row_ptr, col_idx, _ = inputs.rmat_csr(8, 4, seed=3)
+    nr, nc, rp, ci = inputs.fold_rect(row_ptr, col_idx, 2, 5)
+    assert (nr, nc) == (64, 8) and rp.shape == (65,) and ci.shape == col_idx.shape
+    src = np.repeat(np.arange(n), np.diff(row_ptr.astype(np.int64)))
+    src_f = np.repeat(np.arange(nr), np.diff(rp.astype(np.int64)))
+    assert np.array_equal(src_f, src >> 2)  # same edge sequence, rows merged by 4
+    assert np.array_equal(ci, col_idx >> 5)

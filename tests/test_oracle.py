@@ -7,7 +7,12 @@
 * Degree preservation and offsets semantics (Algorithm 1 Steps 1-2).
 * Undirected graphs have identical CSR and CSC (Sec. II-A).
 * Weights ride along unchanged (Sec. II-A).
+* Rectangular n_rows x n_cols matrices: the same definition with n_cols + 1
+  offsets, pinned by brute force (exhaustively on tiny shapes), by scipy's
+  CSR -> CSC conversion (a library routine), by the involution with the
+  shapes swapped, and by the range check against n_cols, not n_rows.
 """
+import math
 import os
 
 import numpy as np
@@ -15,7 +20,7 @@ import pytest
 
 import oracle
 from paper_2501_06872_gb300 import inputs
-from tests._graphs import all_tiny_graphs, brute_transpose, csr_from_rows
+from tests._graphs import all_tiny_graphs, all_tiny_rect, brute_transpose, csr_from_rows
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fig1_pins.txt")
 
@@ -202,3 +207,93 @@ def test_brute_force_detects_planted_mistakes():
     j = int(np.argmax(np.diff(bad_rows.astype(np.int64)) > 0))
     bad_rows[j], bad_rows[j + 1] = bad_rows[j + 1], bad_rows[j]
     assert not np.array_equal(bad_rows, exp[1])
+
+
+# ---- rectangular matrices ------------------------------------------------------
+
+def test_rect_exhaustive_tiny_vs_definition():
+    count = 0
+    for nr, nc, rows in all_tiny_rect(3, 3, 3):
+        row_ptr, col_idx = csr_from_rows(nr, rows)
+        m = col_idx.shape[0]
+        vals = np.arange(m, dtype=np.float32) + 0.25
+        got = oracle.transpose(row_ptr, col_idx, vals, n_cols=nc)
+        exp = brute_transpose(row_ptr, col_idx, vals, n_cols=nc)
+        assert got[0].shape == (nc + 1,)
+        for a, b in zip(got, exp):
+            assert np.array_equal(a, b)
+        count += 1
+    # per shape: C(m + r - 1, r - 1) ways to split m entries over r rows, c^m destination sequences
+    assert count == sum(math.comb(m + r - 1, r - 1) * c ** m for r in range(1, 4) for c in range(1, 4) if r != c
+                        for m in range(4)) == 338
+
+
+@pytest.mark.parametrize("nr,nc,m", [(1, 50, 200), (50, 1, 200), (300, 7, 4000), (7, 300, 4000),
+                                     (1000, 3, 777), (3, 1000, 777)])
+def test_rect_random_vs_definition(nr, nc, m):
+    n, row_ptr, col_idx, vals = inputs.random_csr(nr, m, seed=nr + nc, hot=2, hot_frac=0.3, n_cols=nc)
+    assert int(col_idx.max()) < nc
+    got = oracle.transpose(row_ptr, col_idx, vals, n_cols=nc)
+    exp = brute_transpose(row_ptr, col_idx, vals, n_cols=nc)
+    for a, b in zip(got, exp):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("rs,cs", [(0, 3), (3, 0), (2, 5)])
+def test_rect_matches_scipy(rs, cs):
+    sp = pytest.importorskip("scipy.sparse")
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(10, 8, seed=21, order="random", weighted=True)
+    nr, nc, rp, ci = inputs.fold_rect(row_ptr, col_idx, rs, cs)
+    a = sp.csr_matrix((vals, ci.astype(np.int64), rp.astype(np.int64)), shape=(nr, nc))
+    t = a.tocsc()  # scipy's conversion: a stable counting sort by column, duplicates kept
+    cp, ri, vo = oracle.transpose(rp, ci, vals, n_cols=nc)
+    assert np.array_equal(cp.astype(np.int64), t.indptr.astype(np.int64))
+    assert np.array_equal(ri.astype(np.int64), t.indices.astype(np.int64))
+    assert np.array_equal(vo.view(np.uint32), np.asarray(t.data, dtype=np.float32).view(np.uint32))
+
+
+def test_rect_involution_swaps_shape():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(9, 8, seed=13, weighted=True, sorted_rows=True)
+    nr, nc, rp, ci = inputs.fold_rect(row_ptr, col_idx, 3, 0)  # 64 x 512; merged rows stay sorted per source
+    o = np.lexsort((ci, np.repeat(np.arange(nr), np.diff(rp.astype(np.int64)))))
+    ci, vals = ci[o], vals[o]
+    c1 = oracle.transpose(rp, ci, vals, n_cols=nc)
+    assert c1[0].shape == (nc + 1,) and int(c1[1].max()) < nr
+    c2 = oracle.transpose(c1[0], c1[1], c1[2], n_cols=nr)
+    assert np.array_equal(c2[0], rp)
+    assert np.array_equal(c2[1], ci)
+    assert np.array_equal(c2[2].view(np.uint32), vals.view(np.uint32))
+
+
+def test_rect_degenerate_and_errors():
+    # one row: every column holds that row once per entry, values in CSR order
+    cp, ri, vo = oracle.transpose(np.array([0, 4], np.uint64), np.array([2, 0, 2, 5], np.uint32),
+                                  np.array([1.0, 2.0, 3.0, 4.0], np.float32), n_cols=6)
+    assert list(cp) == [0, 1, 1, 3, 3, 3, 4] and list(ri) == [0, 0, 0, 0] and list(vo) == [2.0, 1.0, 3.0, 4.0]
+    # one column: the rows of the entries in CSR order
+    cp, ri, _ = oracle.transpose(np.array([0, 2, 2, 3], np.uint64), np.zeros(3, np.uint32), n_cols=1)
+    assert list(cp) == [0, 3] and list(ri) == [0, 0, 2]
+    # zero columns and no entries
+    cp, ri, _ = oracle.transpose(np.zeros(4, np.uint64), np.zeros(0, np.uint32), n_cols=0)
+    assert list(cp) == [0] and ri.size == 0
+    # a tall matrix: a column index below n_rows but not below n_cols is out of range
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.transpose(np.array([0, 1, 1, 1], np.uint64), np.array([1], np.uint32), n_cols=1)
+    assert ei.value.code == 2
+    # a wide matrix: a column index above n_rows is fine
+    cp, ri, _ = oracle.transpose(np.array([0, 1], np.uint64), np.array([9], np.uint32), n_cols=10)
+    assert cp[9] == 0 and cp[10] == 1
+
+
+def test_rect_sampled_columns_match_full():
+    n, row_ptr, col_idx, vals = inputs.rmat_csr(10, 16, seed=6, order="degree", weighted=True)
+    nr, nc, rp, ci = inputs.fold_rect(row_ptr, col_idx, 4, 1)
+    full = oracle.transpose(rp, ci, vals, n_cols=nc)
+    cols = np.array([0, 3, 100, nc - 1], dtype=np.uint32)
+    c, start, deg, rows, vo = oracle.columns(rp, ci, vals, cols, n_cols=nc)
+    off = 0
+    for i, v in enumerate(c):
+        assert start[i] == full[0][v] and deg[i] == full[0][v + 1] - full[0][v]
+        d = int(deg[i])
+        assert np.array_equal(rows[off:off + d], full[1][full[0][v]:full[0][v + 1]])
+        off += d
