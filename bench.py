@@ -38,8 +38,25 @@ WORKLOADS = {
     "rmat25-degree": ("rmat", 25, 16, "degree", True),
     "rmat26-degree": ("rmat", 26, 16, "degree", True),
     "rmat27-degree": ("rmat", 27, 16, "degree", True),
+    # rectangular sparse matrices from the scale-28 graph: rows merged by 2^r, columns by 2^c
+    "rmat28-tall": ("rmat", 28, 16, "degree", True),   # 2^28 rows x 2^20 columns
+    "rmat28-wide": ("rmat", 28, 16, "degree", True),   # 2^20 rows x 2^28 columns
+    "rmat24-tall": ("rmat", 24, 16, "degree", True),   # 2^24 rows x 2^16 columns
 }
+FOLDS = {"rmat28-tall": (0, 8), "rmat28-wide": (8, 0), "rmat24-tall": (0, 8)}
 SEED = 0x5EED0003
+
+
+def make_workload(name, seed):
+    """(n_rows, n_cols, row_ptr, col_idx, vals) of a workload, on the GPU."""
+    from paper_2501_06872_gb300.inputs import gpu as ggen
+    kind, scale, ef, order, weighted = WORKLOADS[name]
+    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=seed, order=order, weighted=weighted)
+    rs, cs = FOLDS.get(name, (0, 0))
+    if rs or cs:
+        nr, nc, rp, ci = ggen.fold_rect(rp, ci, rs, cs)
+        return nr, nc, rp, ci, vv
+    return n, n, rp, ci, vv
 
 
 def load_peaks():
@@ -134,11 +151,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def algorithmic_bytes(n, m, weighted):
+def algorithmic_bytes(n, m, weighted, n_cols=None):
     """Bytes the transposition must move (formula of the metric): 2 x col_idx read +
     row_ptr read + row_idx (+ vals_out) write + col_ptr write; plus, separately,
-    the vals read."""
-    literal = 2 * 4 * m + 8 * (n + 1) + 4 * m + (4 * m if weighted else 0) + 8 * (n + 1)
+    the vals read.  n: rows (row_ptr), n_cols: columns (col_ptr), default n."""
+    nc = n if n_cols is None else n_cols
+    literal = 2 * 4 * m + 8 * (n + 1) + 4 * m + (4 * m if weighted else 0) + 8 * (nc + 1)
     with_vals = literal + (4 * m if weighted else 0)
     return literal, with_vals
 
@@ -168,7 +186,7 @@ def radix_down_bytes_per_edge(weighted, passes):
     return (first + later * (passes - 1)) / passes
 
 
-def cpu_baseline_sample(rp_h, ci_h, vv_h, target_edges):
+def cpu_baseline_sample(rp_h, ci_h, vv_h, target_edges, n_cols=None):
     """Rows [0, R) of the workload, R chosen so the prefix holds about target_edges."""
     import oracle
     n = rp_h.size - 1
@@ -178,7 +196,7 @@ def cpu_baseline_sample(rp_h, ci_h, vv_h, target_edges):
     rp_s = rp_h.copy()
     rp_s[R:] = mS
     t0 = time.perf_counter()
-    oracle.transpose(rp_s, ci_h[:mS], None if vv_h is None else vv_h[:mS])
+    oracle.transpose(rp_s, ci_h[:mS], None if vv_h is None else vv_h[:mS], n_cols=n_cols)
     dt = time.perf_counter() - t0
     return mS, R, dt
 
@@ -188,12 +206,11 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import torch
-    from paper_2501_06872_gb300.inputs import gpu as ggen
     import __graft_entry__
     __graft_entry__.build()
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
     torch.cuda.set_device(0)
-    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=SEED, order=order, weighted=weighted)
+    n, n_cols, rp, ci, vv = make_workload(args.workload, SEED)
     m_full = ci.numel()
     target = min(args.ref_sample_edges, ci.numel())
     R = int(torch.searchsorted(rp, torch.tensor([target], device=rp.device)).item())
@@ -207,19 +224,19 @@ def run_reference(args, rank, world):
     torch.cuda.empty_cache()
     import oracle
     for _ in range(args.warmup):
-        oracle.transpose(rp_h, ci_h, vv_h)
+        oracle.transpose(rp_h, ci_h, vv_h, n_cols=n_cols)
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.transpose(rp_h, ci_h, vv_h)
+        oracle.transpose(rp_h, ci_h, vv_h, n_cols=n_cols)
         ts.append(time.perf_counter() - t0)
     total = sum(ts)
     value = mS * args.steps / total
-    sample = f"rows [0,{R}) of the workload ({mS} edges, all {n} vertices)"
+    sample = f"rows [0,{R}) of the workload ({mS} edges, all {n} rows, {n_cols} columns)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": workload_config(args.workload, n, m_full, weighted),
+            "data": "synthetic", "config": workload_config(args.workload, n, m_full, weighted, n_cols),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -243,11 +260,15 @@ def replica_seed(rank):
     return SEED + rank
 
 
-def workload_config(name, n, m, weighted):
+def workload_config(name, n, m, weighted, n_cols=None):
     kind, scale, ef, order, _ = WORKLOADS[name]
-    return {"workload": f"{name}{'-weighted' if weighted else ''}", "graph": kind, "scale": scale,
-            "edge_factor": ef, "n_vertices": n, "n_edges": m, "vertex_order": order, "weighted": weighted,
-            "seed": SEED, "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"}
+    c = {"workload": f"{name}{'-weighted' if weighted else ''}", "graph": kind, "scale": scale,
+         "edge_factor": ef, "n_vertices": n, "n_edges": m, "vertex_order": order, "weighted": weighted,
+         "seed": SEED, "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"}
+    if n_cols is not None and n_cols != n:
+        rs, cs = FOLDS.get(name, (0, 0))
+        c.update({"n_rows": n, "n_cols": n_cols, "fold": f"rows merged by 2^{rs}, columns by 2^{cs}"})
+    return c
 
 
 def run_batched(args):
@@ -377,17 +398,16 @@ def main():
         dist.barrier()
     __graft_entry__.build()
     from paper_2501_06872_gb300 import binding
-    from paper_2501_06872_gb300.inputs import gpu as ggen
 
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
-    n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=replica_seed(rank), order=order, weighted=weighted)
+    n, n_cols, rp, ci, vv = make_workload(args.workload, replica_seed(rank))
     m = ci.numel()
-    cfg = binding.default_config(n, m)
+    cfg = binding.default_config(n_cols, m)
     if args.config:
         for k, v in json.loads(args.config).items():
             setattr(cfg, k, int(v))
-    plan = binding.Plan(n, m, weighted, cfg)
-    cp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    plan = binding.Plan(n, m, weighted, cfg, n_cols=n_cols)
+    cp = torch.empty(n_cols + 1, dtype=torch.int64, device="cuda")
     ri = torch.empty(m, dtype=torch.int32, device="cuda")
     vo = torch.empty(m, dtype=torch.float32, device="cuda") if weighted else None
     stream = torch.cuda.current_stream()
@@ -423,15 +443,15 @@ def main():
     if method == 1:
         # the bulk-staged downsweep runs when radix_tile is 0 and every array is 16-byte aligned (torch's are)
         kname = "k_radix_down_bulk" if plan.config().radix_tile == 0 else "k_radix_down"
-        passes = radix_passes(n)
+        passes = radix_passes(n_cols)
         per_edge = radix_down_bytes_per_edge(weighted, passes)
-        dom_bytes = int(per_edge * m + 8 * (n + 1) / passes)
+        dom_bytes = int(per_edge * m + 8 * (n_cols + 1) / passes)
     else:
         kname = "k_scatter"
-        dom_bytes = stage_bytes(n, m, weighted)["scatter"]
+        dom_bytes = stage_bytes(n, m, weighted)["scatter"]  # graphs only (HLH is not the default above 4 M edges)
     dom_ms = timing["dominant_ms"]
     ach = dom_bytes / (dom_ms * 1e-3) / 1e9
-    lit, withv = algorithmic_bytes(n, m, weighted)
+    lit, withv = algorithmic_bytes(n, m, weighted, n_cols)
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": load_traffic(kname, args.workload), "kernel": kname,
             "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": dom_ms,
@@ -440,11 +460,11 @@ def main():
 
     learned = None
     if rank == 0:
-        learned = selector_summary(plan, rp, ci, vv, cp, ri, vo, n, m)
+        learned = selector_summary(plan, rp, ci, vv, cp, ri, vo, n_cols, m)
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        e2e = run_e2e(plan, rp, ci, vv, n, m, weighted, args)
+        e2e = run_e2e(plan, rp, ci, vv, n, m, weighted, args, n_cols)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -454,15 +474,16 @@ def main():
         mS = int(rp_h[max(1, min(R, n))])
         ci_h = ci[:mS].cpu().numpy().view(np.uint32)
         vv_h = None if vv is None else vv[:mS].cpu().numpy()
-        mS, R, dt = cpu_baseline_sample(rp_h, ci_h, vv_h, target)
+        mS, R, dt = cpu_baseline_sample(rp_h, ci_h, vv_h, target, n_cols)
         cpu = {"value": mS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"rows [0,{R}) of the workload: {mS} edges, all {n} vertices, {dt:.1f} s"}
+               "sample": f"rows [0,{R}) of the workload: {mS} edges, all {n} rows, {n_cols} columns, {dt:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": dict(workload_config(args.workload, n, m, weighted), gt_config=plan.config().as_dict()),
+                "config": dict(workload_config(args.workload, n, m, weighted, n_cols),
+                               gt_config=plan.config().as_dict()),
                 "roofline": roof,
                 "step_hbm": {"gbs_formula": step_gbs, "frac_of_peak": step_gbs / peak,
                              "frac_of_8tbs": step_gbs / 8000.0, "bytes_formula": lit, "bytes_with_vals_read": withv,
@@ -496,12 +517,13 @@ def selector_summary(plan, rp, ci, vv, cp, ri, vo, n, m):
             "heldout_graphs": rep["n_test"]}
 
 
-def run_e2e(plan, rp, ci, vv, n, m, weighted, args):
+def run_e2e(plan, rp, ci, vv, n, m, weighted, args, n_cols=None):
     """Same metric through the host entry point (gt_transpose_host_async, then
     gt_plan_host_wait): pinned host inputs copied in and outputs copied out
     inside the timed region, every step."""
     import torch
-    need = (8 * (n + 1) + 4 * m + (4 * m if weighted else 0)) * 2
+    nc = n if n_cols is None else n_cols
+    need = 8 * (n + 1) + 8 * (nc + 1) + (4 * m + (4 * m if weighted else 0)) * 2
     avail = 0
     try:
         for line in open("/proc/meminfo"):
@@ -515,7 +537,7 @@ def run_e2e(plan, rp, ci, vv, n, m, weighted, args):
     h_rp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
     h_ci = torch.empty(m, dtype=torch.int32, pin_memory=True)
     h_vv = torch.empty(m, dtype=torch.float32, pin_memory=True) if weighted else None
-    h_cp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+    h_cp = torch.empty(nc + 1, dtype=torch.int64, pin_memory=True)
     h_ri = torch.empty(m, dtype=torch.int32, pin_memory=True)
     h_vo = torch.empty(m, dtype=torch.float32, pin_memory=True) if weighted else None
     h_rp.copy_(rp)
@@ -533,7 +555,7 @@ def run_e2e(plan, rp, ci, vv, n, m, weighted, args):
     plan.host_wait()
     dt = (time.perf_counter() - t0) / steps
     h2d = 8 * (n + 1) + 4 * m + (4 * m if weighted else 0)
-    d2h = h2d
+    d2h = 8 * (nc + 1) + 4 * m + (4 * m if weighted else 0)
     return {"value": m / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": dt * 1e3, "steps": steps}
 

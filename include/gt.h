@@ -43,6 +43,10 @@
  *     Outputs are unspecified when any error is reported.
  *   - Vertex IDs are u32 (n <= 2^32 - 1); edge offsets are u64
  *     (m <= 2^32 for weighted graphs, see gt_plan_create).
+ *   - Rectangular sparse matrices (n_rows x n_cols, gt_plan_create_rect)
+ *     follow the same definition: row_ptr has n_rows + 1 entries, col_idx
+ *     values lie in [0, n_cols), col_ptr has n_cols + 1 entries and row_idx
+ *     holds row IDs.  A graph is the square case n_rows = n_cols = n.
  *   - A plan may be used by one stream at a time.
  */
 #ifndef GT_H_
@@ -77,9 +81,10 @@ typedef struct gt_config {
     uint32_t sample_permille; /* sample size in 1/1000 of n (Sec. IV-C uses 10 = 1 %)     */
     uint32_t flags;           /* GT_FLAG_* bits                                            */
     uint32_t method;          /* GT_METHOD_*                                               */
-    uint32_t radix_tile;      /* GT_METHOD_RADIX: 0 = bulk-copy staged 4096-edge tiles, one 512-thread
-                                 CTA per SM (needs 16-byte aligned arrays, else as 4096); 2048 or 4096 =
-                                 register tiles of 256 threads, ctas_per_sm CTAs per SM */
+    uint32_t radix_tile;      /* GT_METHOD_RADIX: 0 = bulk-copy staged 4096-edge tiles, two 256-thread
+                                 CTAs per SM whatever ctas_per_sm says (needs 16-byte aligned arrays,
+                                 else as 4096); 2048 or 4096 = register tiles of 256 threads,
+                                 ctas_per_sm CTAs per SM */
     uint64_t seed;            /* seed of the sampling positions                            */
 } gt_config;
 
@@ -141,13 +146,24 @@ gt_status gt_default_config(gt_config *cfg, uint32_t n_vertices, uint64_t n_edge
 gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, int has_vals,
                          const gt_config *cfg, void *stream);
 
+/* Plan for an n_rows x n_cols sparse matrix with n_edges entries (CSR in,
+ * CSC out; gt_plan_create(n) is gt_plan_create_rect(n, n)).  cfg == NULL
+ * takes gt_default_config(cfg, n_cols, n_edges).  When n_rows or n_cols is
+ * 0, n_edges must be 0; gt_transpose then zero-fills col_ptr and does not
+ * read row_ptr.  Weighted matrices with the HLH method order split rows by a
+ * tag bit in row_idx, which needs n_rows <= 2^31 (larger matrices fall back
+ * to the untagged order, which is still stable). */
+gt_status gt_plan_create_rect(gt_plan *plan, uint32_t n_rows, uint32_t n_cols, uint64_t n_edges, int has_vals,
+                              const gt_config *cfg, void *stream);
+
 /* Replaces the configuration (reallocating workspace if needed). Synchronous. */
 gt_status gt_plan_set_config(gt_plan plan, const gt_config *cfg);
 gt_status gt_plan_get_config(gt_plan plan, gt_config *cfg);
 
 /* Enqueues the transposition (Steps 0-3 and the LDV sort) on `stream`.
- * row_ptr: u64[n+1]; col_idx: u32[m]; vals: f32[m] or NULL;
- * col_ptr: u64[n+1]; row_idx: u32[m]; vals_out: f32[m], NULL iff vals is NULL.
+ * row_ptr: u64[n_rows+1]; col_idx: u32[m]; vals: f32[m] or NULL;
+ * col_ptr: u64[n_cols+1]; row_idx: u32[m]; vals_out: f32[m], NULL iff vals is NULL.
+ * (n_rows = n_cols = n for a plan made by gt_plan_create.)
  * Output arrays must not overlap inputs.  Row pointers are validated on the
  * device (GT_ERR_BAD_ROW_PTR) and destinations range-checked (GT_ERR_OUT_OF_RANGE). */
 gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx,
@@ -160,6 +176,12 @@ gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *co
 gt_status gt_transpose_sub(gt_plan plan, uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
                            const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
                            float *vals_out, void *stream);
+
+/* gt_transpose_sub for an n_rows x n_cols matrix no larger than the plan's
+ * in each of the three sizes. */
+gt_status gt_transpose_sub_rect(gt_plan plan, uint32_t n_rows, uint32_t n_cols, uint64_t n_edges,
+                                const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                                uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream);
 
 /* Same as gt_transpose on HOST arrays (pinned memory recommended): copies the
  * inputs to plan-owned device buffers, transposes, copies the outputs back and
@@ -206,13 +228,13 @@ gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint
  * is captured once into a CUDA graph and replayed by gt_transpose_batched.
  * The output of every graph equals gt_transpose's. */
 typedef struct gt_graph_desc {
-    uint32_t n_vertices;
-    uint32_t reserved;        /* must be 0 */
+    uint32_t n_vertices;      /* rows (the vertices of a graph), >= 1                */
+    uint32_t n_cols;          /* columns of a rectangular matrix; 0 = n_vertices    */
     uint64_t n_edges;
     const uint64_t *row_ptr;  /* device, n_vertices + 1 */
-    const uint32_t *col_idx;  /* device, n_edges */
+    const uint32_t *col_idx;  /* device, n_edges, values < columns */
     const float *vals;        /* device, n_edges, or NULL (all graphs alike) */
-    uint64_t *col_ptr;        /* device, n_vertices + 1 (output) */
+    uint64_t *col_ptr;        /* device, columns + 1 (output) */
     uint32_t *row_idx;        /* device, n_edges (output) */
     float *vals_out;          /* device, n_edges, NULL iff vals is NULL */
 } gt_graph_desc;
@@ -275,18 +297,28 @@ void gt_batch_plan_destroy(gt_batch_plan plan);
 gt_status gt_graph_features(uint32_t n_vertices, uint64_t n_edges, int has_vals, const uint64_t *row_ptr,
                             const uint32_t *col_idx, uint64_t seed, float *features, void *stream);
 
-/* Grid point `index` (0..GT_TUNE_GRID-1) for a graph of this size:
+/* The same features for an n_rows x n_cols matrix: "vertices" in [0..31],
+ * [35], [38] and [39] are rows (out-degrees, sampled rows u_j over n_rows);
+ * [32] is log2(n_cols)/32 and ns = clamp(ceil(n_cols/100), 1024, 2^20).
+ * gt_graph_features(n) is gt_graph_features_rect(n, n). */
+gt_status gt_graph_features_rect(uint32_t n_rows, uint32_t n_cols, uint64_t n_edges, int has_vals,
+                                 const uint64_t *row_ptr, const uint32_t *col_idx, uint64_t seed, float *features,
+                                 void *stream);
+
+/* Grid point `index` (0..GT_TUNE_GRID-1) for a graph of this size
+ * (n_vertices: the column count of a rectangular matrix):
  *   0 Atomic GT (hdv_k = 0, Algorithm 1)   1 same without warp aggregation
  *   2 HLH k=64   3 HLH k=512 (Eq. 1)   4 k=512, 1024-edge bulk-copy stages
  *   5 k=2048   6 k=512, 1024-edge partitions   7 k=512, 512 threads x 2 CTAs/SM
- *   8 radix, bulk-copy staged 4096-edge tiles, one 512-thread CTA per SM
+ *   8 radix, bulk-copy staged 4096-edge tiles, two 256-thread CTAs per SM
  *   9 radix, register tiles of 4096 edges, 2 CTAs/SM   10 same, 4/SM   11 2048-edge tiles, 4/SM
  * An HDV count above n/2 becomes 0 (the point then equals Atomic GT). */
 gt_status gt_tune_grid_config(uint32_t index, uint32_t n_vertices, uint64_t n_edges, gt_config *cfg);
 
 /* Analytic choice (the Sec. IV-B cost model, Eqs. 2-3, with GB300 rates and a
  * streaming term for the radix method) from host copies of the features:
- * writes the grid index (0, 3 or 8). */
+ * writes the grid index (0, 3 or 8).  n_vertices: the column count of a
+ * rectangular matrix. */
 gt_status gt_tune_analytic(const float *features, uint32_t n_vertices, uint64_t n_edges, uint32_t *index);
 
 typedef struct gt_selector_s *gt_selector;
@@ -342,9 +374,11 @@ gt_status gt_plan_tune(gt_plan plan, int mode, gt_selector sel, const uint64_t *
                        const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, uint32_t reps,
                        gt_tune_entry *table, uint32_t *chosen, void *stream);
 
-/* Sizes the plan was created for. */
+/* Sizes the plan was created for (gt_plan_vertices: the row count, which is
+ * the vertex count of a graph).  gt_plan_shape: any pointer may be NULL. */
 uint32_t gt_plan_vertices(gt_plan plan);
 uint64_t gt_plan_edges(gt_plan plan);
+gt_status gt_plan_shape(gt_plan plan, uint32_t *n_rows, uint32_t *n_cols, uint64_t *n_edges);
 
 /* Synchronises the plan's last stream and returns (then clears) the latched
  * device status. */

@@ -53,9 +53,12 @@ def sample_count(n: int, m: int) -> int:
     return min(max((n + 99) // 100, 1024), 1 << 20)
 
 
-def features(n: int, m: int, row_ptr, col_idx, has_vals: bool, seed: int) -> np.ndarray:
+def features(n: int, m: int, row_ptr, col_idx, has_vals: bool, seed: int, n_cols=None) -> np.ndarray:
     """The GT_N_FEATURES graph features, by their definitions (float64, then
-    rounded to float32 as the library stores them)."""
+    rounded to float32 as the library stores them).  For an n x n_cols
+    matrix, n counts rows (degree bins, top rows, sampled rows) and n_cols
+    sets feature 32 and the sample count; n_cols defaults to n."""
+    nc = n if n_cols is None else int(n_cols)
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     col_idx = np.asarray(col_idx, dtype=np.int64)
     f = np.zeros(N_FEATURES, dtype=np.float64)
@@ -67,7 +70,7 @@ def features(n: int, m: int, row_ptr, col_idx, has_vals: bool, seed: int) -> np.
     vcnt = np.bincount(bins, minlength=32)[:32]
     esum = np.bincount(bins, weights=deg.astype(np.float64), minlength=32)[:32]
     f[:32] = vcnt / float(n)
-    f[32] = math.log2(n) / 32.0
+    f[32] = math.log2(nc) / 32.0
     f[33] = math.log2(m + 1.0) / 32.0
     f[34] = math.log2(float(deg.max() if n else 0) + 1.0) / 32.0
     take, got = float((n + 99) // 100), 0.0
@@ -84,7 +87,7 @@ def features(n: int, m: int, row_ptr, col_idx, has_vals: bool, seed: int) -> np.
             got += float(esum[b]) * (take / c)
             take = 0.0
     f[35] = got / m if m else 0.0
-    ns = sample_count(n, m)
+    ns = sample_count(nc, m)
     if ns:
         pos = [scaled(r, m) for r in stream(seed, ns)]
         dst = col_idx[np.array(pos, dtype=np.int64)]

@@ -66,7 +66,7 @@ class Timing(ctypes.Structure):
 
 
 class GraphDesc(ctypes.Structure):
-    _fields_ = [("n_vertices", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
+    _fields_ = [("n_vertices", ctypes.c_uint32), ("n_cols", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
                 ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p), ("vals_out", ctypes.c_void_p)]
 
@@ -95,7 +95,8 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_selector_param_count", "gt_selector_create", "gt_selector_get_params", "gt_selector_set_params",
            "gt_selector_forward", "gt_selector_backward", "gt_selector_adam_step", "gt_selector_destroy",
            "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges", "gt_selector_in_range", "gt_transpose_host_async",
-           "gt_plan_host_wait"]
+           "gt_plan_host_wait", "gt_plan_create_rect", "gt_transpose_sub_rect", "gt_plan_shape",
+           "gt_graph_features_rect"]
 
 N_FEATURES = 41
 TUNE_GRID = 12
@@ -115,6 +116,10 @@ def load():
     P, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
     lib.gt_default_config.argtypes = [ctypes.POINTER(Config), u32, u64]
     lib.gt_plan_create.argtypes = [ctypes.POINTER(P), u32, u64, ctypes.c_int, ctypes.POINTER(Config), P]
+    lib.gt_plan_create_rect.argtypes = [ctypes.POINTER(P), u32, u32, u64, ctypes.c_int, ctypes.POINTER(Config), P]
+    lib.gt_plan_create_rect.restype = ctypes.c_int
+    lib.gt_plan_shape.argtypes = [P, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u64)]
+    lib.gt_plan_shape.restype = ctypes.c_int
     lib.gt_plan_set_config.argtypes = [P, ctypes.POINTER(Config)]
     lib.gt_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
     lib.gt_transpose.argtypes = [P, P, P, P, P, P, P, P]
@@ -125,6 +130,8 @@ def load():
     lib.gt_plan_host_wait.restype = ctypes.c_int
     lib.gt_transpose_sub.argtypes = [P, u32, u64, P, P, P, P, P, P, P]
     lib.gt_transpose_sub.restype = ctypes.c_int
+    lib.gt_transpose_sub_rect.argtypes = [P, u32, u32, u64, P, P, P, P, P, P, P]
+    lib.gt_transpose_sub_rect.restype = ctypes.c_int
     lib.gt_plan_status.argtypes = [P]
     lib.gt_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.gt_transpose_noalloc.argtypes = [u32, u64, P, P, P, P, P, P, P]
@@ -140,6 +147,8 @@ def load():
         getattr(lib, f).restype = ctypes.c_int
     F = ctypes.c_float
     lib.gt_graph_features.argtypes = [u32, u64, ctypes.c_int, P, P, u64, P, P]
+    lib.gt_graph_features_rect.argtypes = [u32, u32, u64, ctypes.c_int, P, P, u64, P, P]
+    lib.gt_graph_features_rect.restype = ctypes.c_int
     lib.gt_tune_grid_config.argtypes = [u32, u32, u64, ctypes.POINTER(Config)]
     lib.gt_tune_analytic.argtypes = [P, u32, u64, ctypes.POINTER(u32)]
     lib.gt_selector_param_count.restype = u64
@@ -211,19 +220,28 @@ def _stream(stream):
 
 
 class Plan:
-    """Owns a gt_plan (workspace for graphs with exactly n vertices, m edges)."""
+    """Owns a gt_plan: workspace for graphs with exactly n vertices and m
+    edges, or, with n_cols, for n x n_cols sparse matrices with m entries."""
 
-    def __init__(self, n: int, m: int, weighted: bool, config: Config | dict | None = None, stream=None):
+    def __init__(self, n: int, m: int, weighted: bool, config: Config | dict | None = None, stream=None,
+                 n_cols: int | None = None):
         lib = load()
         self._lib = lib
         self.n, self.m, self.weighted = int(n), int(m), bool(weighted)
+        self.n_cols = self.n if n_cols is None else int(n_cols)
         h = ctypes.c_void_p()
         if isinstance(config, dict):
             config = Config.from_dict(config)
         cfgp = ctypes.byref(config) if config is not None else None
-        _check(lib.gt_plan_create(ctypes.byref(h), self.n, self.m, int(self.weighted), cfgp,
-                                  _stream(stream) if stream is not None else None), "gt_plan_create")
+        _check(lib.gt_plan_create_rect(ctypes.byref(h), self.n, self.n_cols, self.m, int(self.weighted), cfgp,
+                                       _stream(stream) if stream is not None else None), "gt_plan_create_rect")
         self._h = h
+
+    def shape(self):
+        """(rows, columns, entries) the plan was made for."""
+        r, c, e = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        _check(self._lib.gt_plan_shape(self._h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(e)), "gt_plan_shape")
+        return int(r.value), int(c.value), int(e.value)
 
     @property
     def handle(self):
@@ -245,11 +263,13 @@ class Plan:
                                     _ptr(row_idx), _ptr(vals_out), _stream(stream))
         _check(rc, "gt_transpose")
 
-    def transpose_sub(self, n, m, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
-        """Enqueue a graph no larger than the plan's on the plan's workspace."""
-        rc = self._lib.gt_transpose_sub(self._h, int(n), int(m), _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
-                                        _ptr(col_ptr), _ptr(row_idx), _ptr(vals_out), _stream(stream))
-        _check(rc, "gt_transpose_sub")
+    def transpose_sub(self, n, m, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None, n_cols=None):
+        """Enqueue a graph (or, with n_cols, an n x n_cols matrix) no larger
+        than the plan's on the plan's workspace."""
+        nc = int(n) if n_cols is None else int(n_cols)
+        rc = self._lib.gt_transpose_sub_rect(self._h, int(n), nc, int(m), _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                             _ptr(col_ptr), _ptr(row_idx), _ptr(vals_out), _stream(stream))
+        _check(rc, "gt_transpose_sub_rect")
 
     def transpose_host(self, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):
         """CSR -> CSC on host arrays (pinned recommended); synchronous, returns status."""
@@ -316,7 +336,8 @@ class BatchPlan:
     """Owns a gt_batch_plan over a fixed list of graphs (device pointers).
 
     graphs: sequence of dicts with n, m, row_ptr, col_idx, vals, col_ptr,
-    row_idx, vals_out (torch tensors or raw device addresses)."""
+    row_idx, vals_out (torch tensors or raw device addresses) and, for an
+    n x n_cols matrix, n_cols."""
 
     def __init__(self, graphs, weighted: bool, config: Config | dict | None = None, stream=None):
         lib = load()
@@ -328,7 +349,7 @@ class BatchPlan:
                 return None
             return x if isinstance(x, int) else x.data_ptr()
         for i, g in enumerate(graphs):
-            arr[i] = GraphDesc(int(g["n"]), 0, int(g["m"]), addr(g["row_ptr"]), addr(g["col_idx"]),
+            arr[i] = GraphDesc(int(g["n"]), int(g.get("n_cols", 0)), int(g["m"]), addr(g["row_ptr"]), addr(g["col_idx"]),
                                addr(g.get("vals")), addr(g["col_ptr"]), addr(g["row_idx"]), addr(g.get("vals_out")))
         if isinstance(config, dict):
             config = Config.from_dict(config)
@@ -370,15 +391,17 @@ def grid_config(index: int, n: int, m: int) -> Config:
     return c
 
 
-def graph_features(row_ptr, col_idx, weighted: bool, seed: int = 0x5EED0001, out=None, stream=None):
-    """gt_graph_features into a device f32 tensor of N_FEATURES (allocated if out is None)."""
+def graph_features(row_ptr, col_idx, weighted: bool, seed: int = 0x5EED0001, out=None, stream=None, n_cols=None):
+    """gt_graph_features_rect into a device f32 tensor of N_FEATURES
+    (allocated if out is None); n_cols defaults to the row count."""
     import torch
     n = row_ptr.numel() - 1
+    nc = n if n_cols is None else int(n_cols)
     m = col_idx.numel()
     if out is None:
         out = torch.empty(N_FEATURES, dtype=torch.float32, device=row_ptr.device)
-    _check(load().gt_graph_features(n, m, int(weighted), _ptr(row_ptr), _ptr(col_idx), int(seed), _ptr(out),
-                                    _stream(stream)), "gt_graph_features")
+    _check(load().gt_graph_features_rect(n, nc, m, int(weighted), _ptr(row_ptr), _ptr(col_idx), int(seed),
+                                         _ptr(out), _stream(stream)), "gt_graph_features_rect")
     return out
 
 
@@ -483,16 +506,18 @@ def transpose_noalloc(row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream
     _check(rc, "gt_transpose_noalloc")
 
 
-def transpose(row_ptr, col_idx, vals=None, config=None, stream=None, check=True):
-    """Convenience: allocate outputs (torch, same device) and transpose once."""
+def transpose(row_ptr, col_idx, vals=None, config=None, stream=None, check=True, n_cols=None):
+    """Convenience: allocate outputs (torch, same device) and transpose once
+    (an n x n_cols matrix when n_cols is given, else a graph)."""
     import torch
     n = row_ptr.numel() - 1
+    nc = n if n_cols is None else int(n_cols)
     m = col_idx.numel()
     dev = col_idx.device if m else row_ptr.device
-    col_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col_ptr = torch.empty(nc + 1, dtype=torch.int64, device=dev)
     row_idx = torch.empty(m, dtype=torch.int32, device=dev)
     vals_out = torch.empty(m, dtype=torch.float32, device=dev) if vals is not None else None
-    plan = Plan(n, m, vals is not None, config, stream)
+    plan = Plan(n, m, vals is not None, config, stream, n_cols=nc)
     try:
         plan.transpose(row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream)
         if check:

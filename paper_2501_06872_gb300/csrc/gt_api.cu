@@ -114,10 +114,12 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   if (w.m == 0) ns = 0;
   w.ns = (uint32_t)ns;
   w.ts_log2 = ceil_log2_u64(ns * 2 < 1024 ? 1024 : ns * 2);
-  w.ntiles = (uint32_t)((w.n + gt::kScanTile - 1) / gt::kScanTile);
+  // the look-back scan covers the columns and, in the same grid, validates the rows
+  const uint64_t span = w.n > w.n_rows ? w.n : w.n_rows;
+  w.ntiles = (uint32_t)((span + gt::kScanTile - 1) / gt::kScanTile);
   if (w.ntiles == 0) w.ntiles = 1;
   w.big_cap = (uint32_t)gt::worklist_entries(w.m);
-  w.flag_mode = (w.has_vals && w.n <= 0x80000000u) ? 1 : 0;
+  w.flag_mode = (w.has_vals && w.n_rows <= 0x80000000u) ? 1 : 0;
   w.method = (int)c.method;
   // radix method: radix_tile selects the tile (256 threads x 8 or 16 items),
   // ctas_per_sm the persistent grid
@@ -152,6 +154,7 @@ void plan_free_ws(gt_plan p) {
   gt::DevWork keep = p->w;
   p->w = gt::DevWork();
   p->w.n = keep.n;
+  p->w.n_rows = keep.n_rows;
   p->w.m = keep.m;
   p->w.has_vals = keep.has_vals;
 }
@@ -216,6 +219,7 @@ gt_status apply_config(gt_plan p, const gt_config &c) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) return GT_ERR_CUDA;
   gt::DevWork w;
   w.n = p->w.n;
+  w.n_rows = p->w.n_rows;
   w.m = p->w.m;
   w.has_vals = p->w.has_vals;
   gt_status st = derive_shape(w, c, sms);
@@ -285,14 +289,14 @@ gt_status gt_default_config(gt_config *cfg, uint32_t n_vertices, uint64_t n_edge
   return GT_OK;
 }
 
-gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, int has_vals, const gt_config *cfg,
-                         void *stream) {
+gt_status gt_plan_create_rect(gt_plan *plan, uint32_t n_rows, uint32_t n_cols, uint64_t n_edges, int has_vals,
+                              const gt_config *cfg, void *stream) {
   (void)stream;
   if (!plan) return GT_ERR_INVALID_ARG;
   *plan = nullptr;
   if (has_vals && n_edges > (1ull << 32)) return GT_ERR_UNSUPPORTED;
   if (n_edges >= (1ull << 62)) return GT_ERR_UNSUPPORTED;
-  if (n_vertices == 0 && n_edges != 0) return GT_ERR_INVALID_ARG;
+  if ((n_rows == 0 || n_cols == 0) && n_edges != 0) return GT_ERR_INVALID_ARG;
   gt_plan p = new (std::nothrow) gt_plan_s();
   if (!p) return GT_ERR_NO_MEMORY;
   cudaError_t ge = cudaGetDevice(&p->device);
@@ -311,12 +315,13 @@ gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, i
       return GT_ERR_CUDA;
     }
   }
-  p->w.n = n_vertices;
+  p->w.n = n_cols;
+  p->w.n_rows = n_rows;
   p->w.m = n_edges;
   p->w.has_vals = has_vals ? 1 : 0;
   gt_config c;
   if (cfg) c = *cfg;
-  else gt_default_config(&c, n_vertices, n_edges);
+  else gt_default_config(&c, n_cols, n_edges);
   gt_status st = apply_config(p, c);
   if (st != GT_OK) {
     plan_free_ws(p);
@@ -325,6 +330,11 @@ gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, i
   }
   *plan = p;
   return GT_OK;
+}
+
+gt_status gt_plan_create(gt_plan *plan, uint32_t n_vertices, uint64_t n_edges, int has_vals, const gt_config *cfg,
+                         void *stream) {
+  return gt_plan_create_rect(plan, n_vertices, n_vertices, n_edges, has_vals, cfg, stream);
 }
 
 gt_status gt_plan_set_config(gt_plan plan, const gt_config *cfg) {
@@ -340,18 +350,21 @@ gt_status gt_plan_get_config(gt_plan plan, gt_config *cfg) {
   return GT_OK;
 }
 
-// Launch shape of a smaller graph on a plan's buffers (every buffer size is
-// monotone in n and m for a fixed configuration).
-static gt_status shape_for(gt_plan plan, uint32_t n, uint64_t m, gt::DevWork &w) {
+// Launch shape of a smaller matrix on a plan's buffers (every buffer size is
+// monotone in the column count and m for a fixed configuration; none depends
+// on the row count).
+static gt_status shape_for(gt_plan plan, uint32_t n_rows, uint32_t n, uint64_t m, gt::DevWork &w) {
   w = plan->w;
-  if (n == w.n && m == w.m) return GT_OK;
+  if (n == w.n && n_rows == w.n_rows && m == w.m) return GT_OK;
   gt::DevWork t;
   t.n = n;
+  t.n_rows = n_rows;
   t.m = m;
   t.has_vals = w.has_vals;
   gt_status st = derive_shape(t, plan->cfg, w.num_sms);
   if (st != GT_OK) return st;
   w.n = t.n;
+  w.n_rows = t.n_rows;
   w.m = t.m;
   w.kmax = t.kmax;
   w.tlog2 = t.tlog2;
@@ -376,19 +389,20 @@ static gt_status shape_for(gt_plan plan, uint32_t n, uint64_t m, gt::DevWork &w)
   return GT_OK;
 }
 
-static gt_status transpose_impl(gt_plan plan, uint32_t n, uint64_t m, const uint64_t *row_ptr,
+static gt_status transpose_impl(gt_plan plan, uint32_t n_rows, uint32_t n, uint64_t m, const uint64_t *row_ptr,
                                 const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
                                 float *vals_out, void *stream) {
   if (!plan || !row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
   if (m > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
   if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
   if (vals && !plan->w.has_vals) return GT_ERR_INVALID_ARG;
-  if (n == 0 && m != 0) return GT_ERR_INVALID_ARG;
+  if ((n == 0 || n_rows == 0) && m != 0) return GT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   plan->last = s;
-  if (n == 0) return from_cuda(cudaMemsetAsync(col_ptr, 0, 8, s));
+  // no rows or no columns (and no entries): every offset is 0; row_ptr is not read
+  if (n == 0 || n_rows == 0) return from_cuda(cudaMemsetAsync(col_ptr, 0, ((size_t)n + 1) * 8, s));
   gt::DevWork w;
-  gt_status sst = shape_for(plan, n, m, w);
+  gt_status sst = shape_for(plan, n_rows, n, m, w);
   if (sst != GT_OK) return sst;
   // bulk copies need 16-byte aligned sources; fall back to direct loads otherwise
   if (w.staged && ((((uintptr_t)col_idx) & 15u) || (vals && (((uintptr_t)vals) & 15u)))) {
@@ -414,15 +428,23 @@ static gt_status transpose_impl(gt_plan plan, uint32_t n, uint64_t m, const uint
 gt_status gt_transpose(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
                        uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
   if (!plan) return GT_ERR_INVALID_ARG;
-  return transpose_impl(plan, plan->w.n, plan->w.m, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream);
+  return transpose_impl(plan, plan->w.n_rows, plan->w.n, plan->w.m, row_ptr, col_idx, vals, col_ptr, row_idx,
+                        vals_out, stream);
+}
+
+gt_status gt_transpose_sub_rect(gt_plan plan, uint32_t n_rows, uint32_t n_cols, uint64_t n_edges,
+                                const uint64_t *row_ptr, const uint32_t *col_idx, const float *vals,
+                                uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  if (n_rows > plan->w.n_rows || n_cols > plan->w.n || n_edges > plan->w.m) return GT_ERR_INVALID_ARG;
+  return transpose_impl(plan, n_rows, n_cols, n_edges, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream);
 }
 
 gt_status gt_transpose_sub(gt_plan plan, uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
                            const uint32_t *col_idx, const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
                            float *vals_out, void *stream) {
-  if (!plan) return GT_ERR_INVALID_ARG;
-  if (n_vertices > plan->w.n || n_edges > plan->w.m) return GT_ERR_INVALID_ARG;
-  return transpose_impl(plan, n_vertices, n_edges, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream);
+  return gt_transpose_sub_rect(plan, n_vertices, n_vertices, n_edges, row_ptr, col_idx, vals, col_ptr, row_idx,
+                               vals_out, stream);
 }
 
 gt_status gt_plan_enable_timing(gt_plan plan, int enable) {
@@ -512,12 +534,20 @@ gt_status gt_plan_stats(gt_plan plan, gt_stats *stats) {
 
 uint64_t gt_plan_workspace_bytes(gt_plan plan) { return plan ? plan->ws_bytes : 0; }
 
-uint32_t gt_plan_vertices(gt_plan plan) { return plan ? plan->w.n : 0; }
+uint32_t gt_plan_vertices(gt_plan plan) { return plan ? plan->w.n_rows : 0; }
+
+gt_status gt_plan_shape(gt_plan plan, uint32_t *n_rows, uint32_t *n_cols, uint64_t *n_edges) {
+  if (!plan) return GT_ERR_INVALID_ARG;
+  if (n_rows) *n_rows = plan->w.n_rows;
+  if (n_cols) *n_cols = plan->w.n;
+  if (n_edges) *n_edges = plan->w.m;
+  return GT_OK;
+}
 
 uint64_t gt_plan_edges(gt_plan plan) { return plan ? plan->w.m : 0; }
 
 static gt_status host_staging(gt_plan plan) {
-  const size_t n = plan->w.n, m = plan->w.m;
+  const size_t n = plan->w.n, nr = plan->w.n_rows, m = plan->w.m;
   if (!plan->h_row_ptr) {
     void *q;
 #define GT_HA(field, bytes)                                              \
@@ -529,7 +559,7 @@ static gt_status host_staging(gt_plan plan) {
     plan->host_allocs[plan->nhost++] = q;                                \
     plan->field = (decltype(plan->field))q;                              \
   } while (0)
-    GT_HA(h_row_ptr, (n + 1) * 8);
+    GT_HA(h_row_ptr, (nr + 1) * 8);
     GT_HA(h_col_ptr, (n + 1) * 8);
     GT_HA(h_col_idx, m * 4);
     GT_HA(h_row_idx, m * 4);
@@ -555,12 +585,12 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
                             uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
   gt_status ast = host_args(plan, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out);
   if (ast != GT_OK) return ast;
-  const size_t n = plan->w.n, m = plan->w.m;
+  const size_t n = plan->w.n, nr = plan->w.n_rows, m = plan->w.m;
   cudaStream_t s = (cudaStream_t)stream;
   if ((ast = host_staging(plan)) != GT_OK) return ast;
   if (plan->copy_stream && cudaStreamSynchronize(plan->copy_stream) != cudaSuccess) return GT_ERR_CUDA;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
   if (m && (e = cudaMemcpyAsync(plan->h_col_idx, col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
@@ -583,7 +613,7 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
                                   uint64_t *col_ptr, uint32_t *row_idx, float *vals_out, void *stream) {
   gt_status ast = host_args(plan, row_ptr, col_idx, vals, col_ptr, row_idx, vals_out);
   if (ast != GT_OK) return ast;
-  const size_t n = plan->w.n, m = plan->w.m;
+  const size_t n = plan->w.n, nr = plan->w.n_rows, m = plan->w.m;
   cudaStream_t s = (cudaStream_t)stream;
   if ((ast = host_staging(plan)) != GT_OK) return ast;
   if (!plan->copy_stream) {
@@ -595,7 +625,7 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
   plan->async_stream = s;
   cudaError_t e;
   // inputs: on the caller's stream (after the previous transposition read them)
-  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
   if (m && (e = cudaMemcpyAsync(plan->h_col_idx, col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);

@@ -87,7 +87,7 @@ gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_
   if (n_graphs == 0 || !descs) return GT_ERR_INVALID_ARG;
   for (uint32_t g = 0; g < n_graphs; ++g) {
     const gt_graph_desc &d = descs[g];
-    if (d.n_vertices == 0 || d.reserved != 0 || !d.row_ptr || !d.col_ptr) return GT_ERR_INVALID_ARG;
+    if (d.n_vertices == 0 || !d.row_ptr || !d.col_ptr) return GT_ERR_INVALID_ARG;
     if (d.n_edges > 0 && (!d.col_idx || !d.row_idx)) return GT_ERR_INVALID_ARG;
     if (has_vals && (!d.vals || !d.vals_out)) return GT_ERR_INVALID_ARG;
     if (!has_vals && (d.vals || d.vals_out)) return GT_ERR_INVALID_ARG;
@@ -145,12 +145,13 @@ gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_
       uint32_t maxn = 1;
       while (g1 < n_graphs) {
         const gt_graph_desc &d = descs[g1];
-        const uint32_t nmax = d.n_vertices > maxn ? d.n_vertices : maxn;
+        const uint32_t nc = gt::desc_cols(d);  // keys and the union col_ptr span the columns
+        const uint32_t nmax = nc > maxn ? nc : maxn;
         const uint32_t keyw = bits_of(nmax - 1 ? nmax - 1 : 1) + bits_of(g1 - g);
-        const bool fits = sm + d.n_edges <= sub_cap && sn + d.n_vertices < (1ull << 31) && keyw <= 32;
+        const bool fits = sm + d.n_edges <= sub_cap && sn + nc < (1ull << 31) && keyw <= 32;
         if (g1 > g && !fits) break;
         sm += d.n_edges;
-        sn += d.n_vertices;
+        sn += nc;
         maxn = nmax;
         ++g1;
       }
@@ -178,10 +179,11 @@ gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_
       eoff[0] = voff[0] = woff[0] = 0;
       for (uint32_t j = 0; j < sb.ng; ++j) {
         const gt_graph_desc &d = descs[sb.g0 + j];
+        const uint32_t nc = gt::desc_cols(d);
         eoff[j + 1] = eoff[j] + d.n_edges;
-        voff[j + 1] = voff[j] + d.n_vertices;
-        woff[j + 1] = woff[j] + (d.n_vertices + 31) / 32;
-        if (d.n_vertices > maxn) maxn = d.n_vertices;
+        voff[j + 1] = voff[j] + nc;                        // union column space
+        woff[j + 1] = woff[j] + (d.n_vertices + 31) / 32;  // 32-row windows of the expansion
+        if (nc > maxn) maxn = nc;
       }
       sb.m = eoff[sb.ng];
       sb.nv = (uint32_t)voff[sb.ng];

@@ -8,6 +8,9 @@
 
 namespace gt {
 
+// Columns of a batch descriptor's matrix (n_cols == 0: a graph, n_vertices x n_vertices).
+__host__ __device__ inline uint32_t desc_cols(const gt_graph_desc &d) { return d.n_cols ? d.n_cols : d.n_vertices; }
+
 constexpr uint32_t kFreqBins = 1u << 16;   // sample-frequency histogram bins
 constexpr uint32_t kTieCap = 8192;         // tie candidates kept at the threshold
 constexpr uint32_t kScanTile = 4096;       // elements per decoupled-look-back tile
@@ -21,8 +24,11 @@ inline uint64_t worklist_entries(uint64_t m) {
 }
 
 struct DevWork {
-  // sizes and derived launch shape
+  // sizes and derived launch shape: n columns (destinations: col_ptr has n + 1
+  // entries, keys and degree arrays span [0, n)), n_rows rows (row_ptr has
+  // n_rows + 1 entries, row_idx values span [0, n_rows)); a graph has n_rows == n
   uint32_t n = 0;
+  uint32_t n_rows = 0;
   uint64_t m = 0;
   int has_vals = 0;
   uint32_t kmax = 0, tlog2 = 0, W = 0, G = 0, P = 0;
@@ -30,7 +36,7 @@ struct DevWork {
   uint32_t ns = 0, ts_log2 = 0;
   uint32_t ntiles = 0;
   uint32_t big_cap = 0;
-  int flag_mode = 0;  // split-row duplicate ordering via row_idx bit 31 (weighted, n <= 2^31)
+  int flag_mode = 0;  // split-row duplicate ordering via row_idx bit 31 (weighted, n_rows <= 2^31)
   int staged = 0;     // bulk-copy staging of col_idx/vals tiles
   uint32_t stage_edges = 0;
   uint32_t smem_count = 0, smem_scatter = 0;
@@ -61,7 +67,7 @@ struct DevWork {
   int method = 0;
   uint32_t rG = 0;                            // persistent CTAs of the digit passes
   uint32_t r_items = 16;                      // elements per thread of a downsweep tile (8 or 16)
-  int r_bulk = 0;                             // bulk-copy staged downsweep (one 512-thread CTA per SM)
+  int r_bulk = 0;                             // bulk-copy staged downsweep (two 256-thread CTAs per SM)
   uint32_t *r_a_key = nullptr, *r_a_u = nullptr, *r_a_w = nullptr;  // [m] ping buffer
   uint32_t *r_b_key = nullptr;                // [m] keys of the pong buffer (u/w live in the outputs)
   uint32_t *r_long = nullptr;                 // rows longer than the window expansion handles

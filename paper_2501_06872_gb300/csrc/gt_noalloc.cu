@@ -100,6 +100,7 @@ extern "C" gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges,
   cfg.flags = GT_FLAG_AGGREGATE;
   gt::DevWork w;
   w.n = n_vertices;
+  w.n_rows = n_vertices;
   w.m = n_edges;
   w.has_vals = vals ? 1 : 0;
   w.num_sms = sms;

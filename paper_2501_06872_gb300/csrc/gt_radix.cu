@@ -101,23 +101,23 @@ __host__ __device__ constexpr bool stores_batch(int mode) { return mode == kBatc
 // ends held in registers.  Longer rows are listed for k_expand_long.
 constexpr uint32_t kLongRow = 2048;
 
-__global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n, uint64_t m, uint32_t *src,
+__global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n_rows, uint64_t m, uint32_t *src,
                               uint32_t *long_rows, uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (row_ptr[0] != 0 || row_ptr[n] != m))
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (row_ptr[0] != 0 || row_ptr[n_rows] != m))
     set_status(status, GT_ERR_BAD_ROW_PTR);
-  for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n; r0 += warps * 32) {
+  for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n_rows; r0 += warps * 32) {
     const uint64_t r = r0 + lane;
     uint64_t ri = r + 1;
-    if (ri > n) ri = n;
+    if (ri > n_rows) ri = n_rows;
     uint64_t rend = row_ptr[ri];  // end of row r (clamped)
-    uint64_t rbeg = r < n ? row_ptr[r] : rend;
+    uint64_t rbeg = r < n_rows ? row_ptr[r] : rend;
     if (rend > m || rbeg > rend) {  // invalid row pointers: report, write nothing out of range
       set_status(status, GT_ERR_BAD_ROW_PTR);
       rend = rbeg = 0;
     }
-    const bool is_long = r < n && rend - rbeg > kLongRow;
+    const bool is_long = r < n_rows && rend - rbeg > kLongRow;
     if (is_long) {
       uint32_t i = atomicAdd(n_long, 1u);
       if (i < long_cap) long_rows[i] = (uint32_t)r;
@@ -134,7 +134,7 @@ __global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n, 
       }
     } else {
       // short rows of this window one by one (the long ones are skipped)
-      uint32_t todo = __ballot_sync(kFull, r < n && !is_long && rend > rbeg);
+      uint32_t todo = __ballot_sync(kFull, r < n_rows && !is_long && rend > rbeg);
       while (todo) {
         const uint32_t j = __ffs(todo) - 1;
         todo &= todo - 1;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
           const gt_graph_desc &d = a.batch.descs[g];
           const uint64_t le = e - a.batch.eoff[g];
           const uint32_t v = __ldcs(d.col_idx + le);
-          if (v >= d.n_vertices) bad = 1;
+          if (v >= desc_cols(d)) bad = 1;
           key[i] = (g << a.batch.vbits) | (v & ((1u << a.batch.vbits) - 1u));
           if (a.g_key) {  // gather the union key (and value) for a plain first pass
             a.g_key[e] = key[i];
@@ -628,15 +628,15 @@ __device__ __forceinline__ void colptr_range(uint64_t a, uint64_t b, uint64_t va
 }
 
 // Key -> position in the col_ptr space: the key itself (clamped to n), or,
-// for a batch, the compact union index voff[graph] + vertex (clamped to the
-// graph's vertex count), which is monotone in the key.
+// for a batch, the compact union index voff[graph] + column (clamped to the
+// graph's column count), which is monotone in the key.
 template <bool BATCH>
 __device__ __forceinline__ uint32_t cp_index(uint32_t k, uint32_t n, const BatchView &bv) {
   if (!BATCH) return min(k, n);
   const uint32_t g = k >> bv.vbits;
   if (g >= bv.ng) return n;
   const uint32_t v = k & ((1u << bv.vbits) - 1u);
-  return (uint32_t)(bv.voff[g] + min(v, bv.descs[g].n_vertices));
+  return (uint32_t)(bv.voff[g] + min(v, desc_cols(bv.descs[g])));
 }
 
 template <bool BATCH>
@@ -746,7 +746,7 @@ static void launch_down(bool vals, uint32_t items, uint32_t G, size_t dsm, cudaS
 
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint32_t *launches, StepEvents *ev) {
   const uint64_t m = w.m;
-  const uint32_t n = w.n;
+  const uint32_t n = w.n;  // columns: the keys
   const bool vals = pb.vals != nullptr;
   uint32_t nl = 0;
   cudaError_t err;
@@ -769,12 +769,12 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   const bool first_to_b = ((passes - 1) % 2) == 0;
   // source rows of the first pass go to the buffer the first pass does not write
   uint32_t *src_rows = first_to_b ? w.r_a_u : b_u;
-  {
-    uint64_t warps = ((uint64_t)n + 31) / 32;
+  {  // source of every edge: rows [0, n_rows)
+    uint64_t warps = ((uint64_t)w.n_rows + 31) / 32;
     uint32_t g = (uint32_t)min64((warps + 7) / 8, (uint64_t)w.num_sms * 16);
     if (g == 0) g = 1;
     const uint32_t long_cap = (uint32_t)(m / (kLongRow + 1) + 1);
-    k_expand_rows<<<g, 256, 0, s>>>(pb.row_ptr, n, m, src_rows, w.r_long, w.r_nlong, long_cap, w.status);
+    k_expand_rows<<<g, 256, 0, s>>>(pb.row_ptr, w.n_rows, m, src_rows, w.r_long, w.r_nlong, long_cap, w.status);
     k_expand_long<<<w.num_sms * 4, 256, 0, s>>>(pb.row_ptr, w.r_long, w.r_nlong, long_cap, src_rows);
     nl += 2;
   }
@@ -822,7 +822,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
 // Batches (sub-batch of graphs laid out in union edge / vertex spaces)
 // ---------------------------------------------------------------------------
 
-// Per graph: row_ptr[0] == 0 and row_ptr[n] == m.
+// Per graph: row_ptr[0] == 0 and row_ptr[n_rows] == m (n_vertices is the row count).
 __global__ void k_b_check(BatchView bv, uint32_t *status) {
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < bv.ng; g += gridDim.x * blockDim.x) {
     const gt_graph_desc &d = bv.descs[g];
@@ -839,7 +839,7 @@ __global__ void k_b_expand(BatchView bv, const unsigned long long *__restrict__ 
   for (uint64_t wi = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); wi < windows; wi += warps) {
     const uint32_t g = upper_graph(woff, bv.ng, wi);
     const gt_graph_desc &d = bv.descs[g];
-    const uint32_t n = d.n_vertices;
+    const uint32_t n = d.n_vertices;  // rows
     const uint64_t m = d.n_edges, base = bv.eoff[g];
     const uint64_t r0 = (wi - woff[g]) * 32;
     const uint64_t r = r0 + lane;
@@ -904,7 +904,7 @@ __global__ void k_b_colptr(BatchView bv, const unsigned long long *__restrict__ 
     } else {
       const uint32_t g = (uint32_t)(x - nv);
       const gt_graph_desc &d = bv.descs[g];
-      d.col_ptr[d.n_vertices] = d.n_edges;
+      d.col_ptr[desc_cols(d)] = d.n_edges;
     }
   }
 }

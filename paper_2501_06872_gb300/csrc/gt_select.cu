@@ -179,8 +179,8 @@ __global__ void k_feat_loc(const uint64_t *__restrict__ row_ptr, const uint32_t 
 constexpr uint32_t kFinThreads = 1024;
 constexpr uint32_t kFinChunk = kFreqCap / kFinThreads;
 
-__global__ void __launch_bounds__(kFinThreads) k_feat_final(FeatWs *ws, uint32_t n, uint64_t m, uint32_t ns,
-                                                            int has_vals, float *out) {
+__global__ void __launch_bounds__(kFinThreads) k_feat_final(FeatWs *ws, uint32_t n, uint32_t n_cols, uint64_t m,
+                                                            uint32_t ns, int has_vals, float *out) {
   __shared__ unsigned long long s_cnt[kFinThreads], s_sum[kFinThreads];
   __shared__ unsigned long long s_left, s_cov;
   const uint32_t t = threadIdx.x;
@@ -236,9 +236,9 @@ __global__ void __launch_bounds__(kFinThreads) k_feat_final(FeatWs *ws, uint32_t
   }
   __syncthreads();
   if (t != 0) return;
-  const double dn = (double)n;
+  const double dn = (double)n;  // rows
   for (uint32_t b = 0; b < kDegBins; ++b) out[b] = (float)((double)ws->vcnt[b] / dn);
-  out[32] = (float)(log2(dn) / 32.0);
+  out[32] = (float)(log2((double)n_cols) / 32.0);
   out[33] = (float)(log2((double)m + 1.0) / 32.0);
   out[34] = (float)(log2((double)ws->maxdeg + 1.0) / 32.0);
   // edges out of the ceil(n/100) vertices of highest out-degree, walking the
@@ -429,11 +429,11 @@ extern "C" {
 
 uint64_t gt_selector_param_count(void) { return kParams; }
 
-gt_status gt_graph_features(uint32_t n, uint64_t m, int has_vals, const uint64_t *row_ptr, const uint32_t *col_idx,
-                            uint64_t seed, float *features, void *stream) {
-  if (n == 0 || !row_ptr || !features || (m > 0 && !col_idx)) return GT_ERR_INVALID_ARG;
+gt_status gt_graph_features_rect(uint32_t n, uint32_t n_cols, uint64_t m, int has_vals, const uint64_t *row_ptr,
+                                 const uint32_t *col_idx, uint64_t seed, float *features, void *stream) {
+  if (n == 0 || n_cols == 0 || !row_ptr || !features || (m > 0 && !col_idx)) return GT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  uint64_t ns64 = ((uint64_t)n + 99) / 100;
+  uint64_t ns64 = ((uint64_t)n_cols + 99) / 100;
   ns64 = std::max<uint64_t>(ns64, 1024);
   ns64 = std::min<uint64_t>(ns64, 1u << 20);
   const uint32_t ns = m ? (uint32_t)ns64 : 0u;
@@ -461,11 +461,16 @@ gt_status gt_graph_features(uint32_t n, uint64_t m, int has_vals, const uint64_t
       k_feat_freq<<<std::min<uint32_t>(blocks(ts, 256), sms * 8), 256, 0, s>>>(keys, cnt, (uint32_t)ts, ws);
       k_feat_loc<<<blocks((uint64_t)kLocRows * 32, 256), 256, 0, s>>>(row_ptr, col_idx, n, m, kLocRows, seed, ws);
     }
-    k_feat_final<<<1, kFinThreads, 0, s>>>(ws, n, m, ns, has_vals, features);
+    k_feat_final<<<1, kFinThreads, 0, s>>>(ws, n, n_cols, m, ns, has_vals, features);
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(blk, s);
   return cuda_status(e != cudaSuccess ? e : e2);
+}
+
+gt_status gt_graph_features(uint32_t n, uint64_t m, int has_vals, const uint64_t *row_ptr, const uint32_t *col_idx,
+                            uint64_t seed, float *features, void *stream) {
+  return gt_graph_features_rect(n, n, m, has_vals, row_ptr, col_idx, seed, features, stream);
 }
 
 gt_status gt_selector_create(gt_selector *sel, const float *host_params, uint64_t seed) {
@@ -748,8 +753,9 @@ extern "C" gt_status gt_plan_tune(gt_plan plan, int mode, gt_selector sel, const
   if (mode == GT_TUNE_LEARNED && !sel) return GT_ERR_INVALID_ARG;
   gt_config cur;
   gt_plan_get_config(plan, &cur);
-  const uint32_t n = gt_plan_vertices(plan);
-  const uint64_t m = gt_plan_edges(plan);
+  uint32_t n_rows = 0, n = 0;  // n: columns (the grid and the analytic model size by destinations)
+  uint64_t m = 0;
+  gt_plan_shape(plan, &n_rows, &n, &m);
   cudaStream_t s = (cudaStream_t)stream;
   gt_config grid[kK];
   for (uint32_t i = 0; i < kK; ++i) gt_tune_grid_config(i, n, m, &grid[i]);
@@ -801,7 +807,7 @@ extern "C" gt_status gt_plan_tune(gt_plan plan, int mode, gt_selector sel, const
     float *feat = nullptr;
     st = cuda_status(cudaMallocAsync(&feat, (kNF + kK) * 4, s));
     if (st != GT_OK) return st;
-    st = gt_graph_features(n, m, vals != nullptr, row_ptr, col_idx, cur.seed, feat, s);
+    st = gt_graph_features_rect(n_rows, n, m, vals != nullptr, row_ptr, col_idx, cur.seed, feat, s);
     float hf[kNF + kK];
     if (st == GT_OK && mode == GT_TUNE_LEARNED) st = gt_selector_forward(sel, feat, 1, feat + kNF, s);
     if (st == GT_OK) st = cuda_status(cudaMemcpyAsync(hf, feat, sizeof(hf), cudaMemcpyDeviceToHost, s));

@@ -26,7 +26,7 @@
 namespace gt {
 
 struct SortArgs {
-  uint32_t n;
+  uint32_t n;  // columns: the lists to sort
   const uint64_t *col_ptr;
   const uint64_t *row_ptr;
   const float *vals;  // input values (tagged entries re-read theirs)
@@ -42,7 +42,7 @@ struct SortArgs {
   uint32_t mid_cap, big_cap, large_cap;
   uint32_t *status;
   int flag_mode;
-  uint32_t key_bits;  // bits of a vertex ID (ceil(log2 n))
+  uint32_t key_bits;  // bits of a row ID, the sort key (ceil(log2 n_rows))
 };
 
 struct WarpSync {
@@ -617,7 +617,7 @@ cudaError_t configure_sort() {
 cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &pb, cudaStream_t s) {
   (void)cfg;
   uint32_t bits = 0;
-  while (bits < 32 && (w.n - 1) >> bits) ++bits;
+  while (bits < 32 && (w.n_rows - 1) >> bits) ++bits;
   SortArgs sa;
   sa.n = w.n;
   sa.col_ptr = pb.col_ptr;

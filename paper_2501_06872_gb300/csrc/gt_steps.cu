@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(1024) k_finalize(uint32_t *meta, const uint32_
 // processed by neighbouring warps).  Warp p owns edges [part[p], part[p+1])
 // in Steps 1 and 3.
 // ---------------------------------------------------------------------------
-__global__ void k_partition(const uint64_t *__restrict__ row_ptr, uint32_t n, uint64_t m, uint32_t P,
+__global__ void k_partition(const uint64_t *__restrict__ row_ptr, uint32_t n_rows, uint64_t m, uint32_t P,
                             uint64_t psize, int allow_split, unsigned long long *part, uint32_t *status) {
+  const uint32_t n = n_rows;
   uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p > P) return;
   if (p == 0) {
@@ -485,8 +486,8 @@ constexpr int kScanItems = kScanTile / kScanThreads;  // 16
 static_assert(kScanItems == 16, "scan layout");
 constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restrict__ deg, uint32_t n, uint64_t m,
-                                                       const uint64_t *__restrict__ row_ptr, uint64_t *col_ptr,
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restrict__ deg, uint32_t n, uint32_t n_rows,
+                                                       uint64_t m, const uint64_t *__restrict__ row_ptr, uint64_t *col_ptr,
                                                        unsigned long long *cursor, unsigned long long *state,
                                                        uint32_t *meta, uint32_t *status) {
   __shared__ uint32_t s_tile;
@@ -512,12 +513,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) d[i] = (base + i < n) ? deg[base + i] : 0u;
   }
-  // row_ptr validation on the same index range
+  // row_ptr validation on the same index range (the grid covers max(n, n_rows))
   if (row_ptr) {
     bool bad = false;
     for (int i = 0; i < kScanItems; ++i) {
       uint64_t r = base + i;
-      if (r < n && row_ptr[r] > row_ptr[r + 1]) bad = true;
+      if (r < n_rows && row_ptr[r] > row_ptr[r + 1]) bad = true;
     }
     if (bad) set_status(status, GT_ERR_BAD_ROW_PTR);
   }
@@ -605,7 +606,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t *__restric
 cudaError_t launch_scan(const uint32_t *deg, uint32_t n, uint64_t m, const uint64_t *row_ptr, uint64_t *col_ptr,
                         unsigned long long *cursor, unsigned long long *state, uint32_t ntiles, uint32_t *meta,
                         uint32_t *status, cudaStream_t s) {
-  k_scan<<<ntiles, kScanThreads, 0, s>>>(deg, n, m, row_ptr, col_ptr, cursor, state, meta, status);
+  k_scan<<<ntiles, kScanThreads, 0, s>>>(deg, n, n, m, row_ptr, col_ptr, cursor, state, meta, status);
   return cudaGetLastError();
 }
 
@@ -628,7 +629,8 @@ struct ScatterArgs {
   const uint64_t *row_ptr;
   const uint32_t *col_idx;
   const float *vals;
-  uint32_t n;
+  uint32_t n;       // columns: destinations lie in [0, n)
+  uint32_t n_rows;  // rows: row_ptr has n_rows + 1 entries
   uint64_t m;
   const unsigned long long *part;
   const uint32_t *hkeys;
@@ -676,7 +678,7 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
   // rows at both ends of the partition (they may be shared with neighbours)
   uint32_t row_first, row_last;
   {
-    uint32_t lo = 0, hi = a.n;
+    uint32_t lo = 0, hi = a.n_rows;
     while (hi - lo > 1) {
       uint32_t mid = lo + (hi - lo) / 2;
       if (a.row_ptr[mid] <= e0) lo = mid;
@@ -684,7 +686,7 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
     }
     row_first = lo;
     lo = row_first;
-    hi = a.n;
+    hi = a.n_rows;
     while (hi - lo > 1) {
       uint32_t mid = lo + (hi - lo) / 2;
       if (a.row_ptr[mid] <= e1 - 1) lo = mid;
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
   uint32_t u_lo = row_first;
 
   auto step = [&](uint64_t e, bool act, uint32_t v, float wv) {
-    uint32_t my_u = find_row(a.row_ptr, a.n, u_lo, e, act, lane, a.status);
+    uint32_t my_u = find_row(a.row_ptr, a.n_rows, u_lo, e, act, lane, a.status);
     uint32_t last_lane = 31u - __clz(__ballot_sync(kFull, act) | 1u);
     u_lo = __shfl_sync(kFull, my_u, last_lane);
     bool valid = act && v < a.n;
@@ -943,7 +945,7 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // unsorted output (GT_FLAG_UNSORTED): no LDV sort, no split-row tags
   const bool unsorted = (cfg.flags & GT_FLAG_UNSORTED) != 0;
   const int flag_mode = unsorted ? 0 : w.flag_mode;
-  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n, w.m, w.P, w.psize,
+  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n_rows, w.m, w.P, w.psize,
                                                     unsorted || w.flag_mode || !w.has_vals,
                                                      w.part, w.status);
   nl += 2;  // partition + count
@@ -977,15 +979,15 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
     dim3 b(32, 32);
     k_hdv_colscan<<<(w.kmax + 31) / 32, b, 0, s>>>(w.hdv_cnt, w.P, w.kmax, w.meta, w.hdv_ids, w.deg, w.status);
   }
-  k_scan<<<w.ntiles, kScanThreads, 0, s>>>(w.deg, w.n, w.m, pb.row_ptr, pb.col_ptr, w.cursor, w.scan_state, w.meta,
-                                           w.status);
+  k_scan<<<w.ntiles, kScanThreads, 0, s>>>(w.deg, w.n, w.n_rows, w.m, pb.row_ptr, pb.col_ptr, w.cursor,
+                                           w.scan_state, w.meta, w.status);
   if (hdv) k_hdv_start<<<(w.kmax + 255) / 256, 256, 0, s>>>(w.meta, w.hdv_ids, pb.col_ptr, w.hdv_start);
   nl += hdv ? 3 : 1;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   mark(3);
 
   // Step 3
-  ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n,         w.m,       w.part,   w.hkeys,
+  ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n, w.n_rows, w.m,       w.part,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
                  pb.col_ptr, pb.row_idx, pb.vals_out, unsorted ? nullptr : (unsigned long long *)w.scratch,
                  w.status, flag_mode, w.stage_edges};

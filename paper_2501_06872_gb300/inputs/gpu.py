@@ -140,6 +140,21 @@ def graph(scale: int, edge_factor: int = 16, kind: str = "rmat", a=0.57, b=0.19,
     return n, row_ptr, col_idx, vals
 
 
+def fold_rect(row_ptr, col_idx, row_shift: int, col_shift: int):
+    """Rectangular matrix from a square CSR by relabelling (as inputs.fold_rect):
+    rows u -> u >> row_shift (consecutive rows merge, edges keep CSR order),
+    columns v -> v >> col_shift, in place on col_idx.  Returns (n_rows,
+    n_cols, row_ptr, col_idx)."""
+    n = row_ptr.numel() - 1
+    if n & ((1 << row_shift) - 1) or n & ((1 << col_shift) - 1):
+        raise ValueError("the vertex count must be a multiple of both folds")
+    rp = row_ptr[::1 << row_shift].contiguous() if row_shift else row_ptr
+    if col_shift:
+        col_idx.bitwise_right_shift_(col_shift)  # IDs < 2^31: the sign bit is clear
+    torch.cuda.synchronize()
+    return n >> row_shift, n >> col_shift, rp, col_idx
+
+
 def _zipf_mean(s: float, n: int) -> float:
     """Mean of Zipf(s) truncated to {1..n}: ratio of generalised harmonic
     numbers, by direct sum for small n and Euler-Maclaurin tails otherwise."""

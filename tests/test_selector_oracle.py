@@ -48,6 +48,27 @@ def test_features_in_star_closed_forms():
     assert so.features(n, m, rp, ci, True, 5)[40] == 1
 
 
+def test_features_rect_closed_forms():
+    # tall: 1000 rows x 4 columns, row u -> column u % 4 (one entry per row)
+    nr, nc = 1000, 4
+    rp = np.arange(nr + 1, dtype=np.int64)
+    ci = np.arange(nr, dtype=np.int64) % nc
+    f = so.features(nr, nr, rp, ci, False, 3, n_cols=nc).astype(np.float64)
+    assert f[1] == 1.0 and f[0] == 0  # every row has degree 1 (fractions of rows)
+    assert f[32] == pytest.approx(math.log2(nc) / 32)  # the column space
+    assert f[35] == pytest.approx(10 / nr)  # the ceil(1000/100) = 10 top rows hold 10 entries
+    assert f[36] == 1.0  # 4 distinct destinations, all within the top 512
+    assert so.sample_count(nc, nr) == 1024
+    # wide: 4 rows x 10^6 columns: the sample count follows the columns
+    assert so.sample_count(10 ** 6, 4000) == 10000
+    rp = np.array([0, 1000, 2000, 3000, 4000], dtype=np.int64)
+    ci = (np.arange(4000, dtype=np.int64) * 250) % 10 ** 6
+    g = so.features(4, 4000, rp, ci, False, 3, n_cols=10 ** 6).astype(np.float64)
+    assert g[32] == pytest.approx(math.log2(10 ** 6) / 32)
+    assert g[10] == 1.0  # degree 1000 -> bin 10 for all 4 rows
+    assert g[35] == pytest.approx(1000 / 4000)  # ceil(4/100) = 1 top row of 4
+
+
 def test_features_consecutive_neighbours():
     # u -> u+1, u+2 while u+2 < n: every neighbour pair differs by one
     n = 5000
