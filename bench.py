@@ -42,21 +42,41 @@ WORKLOADS = {
     "rmat28-tall": ("rmat", 28, 16, "degree", True),   # 2^28 rows x 2^20 columns
     "rmat28-wide": ("rmat", 28, 16, "degree", True),   # 2^20 rows x 2^28 columns
     "rmat24-tall": ("rmat", 24, 16, "degree", True),   # 2^24 rows x 2^16 columns
+    # the paper's representations (Sec. V-A): generated ("natural") and randomised IDs, with --direction csr|csc
+    "rmat25-natural": ("rmat", 25, 16, "natural", False),
+    "rmat25-random": ("rmat", 25, 16, "random", False),
 }
 FOLDS = {"rmat28-tall": (0, 8), "rmat28-wide": (8, 0), "rmat24-tall": (0, 8)}
 SEED = 0x5EED0003
 
 
-def make_workload(name, seed):
-    """(n_rows, n_cols, row_ptr, col_idx, vals) of a workload, on the GPU."""
+def make_workload(name, seed, direction="csr"):
+    """(n_rows, n_cols, row_ptr, col_idx, vals) of a workload, on the GPU.
+    direction "csc": the input is the graph's CSC (in-lists in ascending
+    source order, parallel edges in CSR order, built by a stable torch sort),
+    so the call transposes CSC -> CSR (the paper's CSC representations)."""
+    import torch
     from paper_2501_06872_gb300.inputs import gpu as ggen
     kind, scale, ef, order, weighted = WORKLOADS[name]
     n, rp, ci, vv = ggen.graph(scale, ef, kind=kind, seed=seed, order=order, weighted=weighted)
     rs, cs = FOLDS.get(name, (0, 0))
+    nr = nc = n
     if rs or cs:
         nr, nc, rp, ci = ggen.fold_rect(rp, ci, rs, cs)
-        return nr, nc, rp, ci, vv
-    return n, n, rp, ci, vv
+    if direction == "csc":
+        src = torch.repeat_interleave(torch.arange(nr, dtype=torch.int64, device=rp.device), rp.diff())
+        key = (ci.to(torch.int64) << 32) | src
+        del src
+        key, perm = torch.sort(key, stable=True)
+        cp = torch.zeros(nc + 1, dtype=torch.int64, device=rp.device)
+        torch.cumsum(torch.bincount(key >> 32, minlength=nc), 0, out=cp[1:])
+        ci = (key & 0xFFFFFFFF).to(torch.int32)
+        del key
+        vv = None if vv is None else vv[perm]
+        del perm
+        torch.cuda.synchronize()
+        return nc, nr, cp, ci, vv
+    return nr, nc, rp, ci, vv
 
 
 def load_peaks():
@@ -210,7 +230,7 @@ def run_reference(args, rank, world):
     __graft_entry__.build()
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
     torch.cuda.set_device(0)
-    n, n_cols, rp, ci, vv = make_workload(args.workload, SEED)
+    n, n_cols, rp, ci, vv = make_workload(args.workload, SEED, args.direction)
     m_full = ci.numel()
     target = min(args.ref_sample_edges, ci.numel())
     R = int(torch.searchsorted(rp, torch.tensor([target], device=rp.device)).item())
@@ -236,7 +256,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": workload_config(args.workload, n, m_full, weighted, n_cols),
+            "data": "synthetic", "config": workload_config(args.workload, n, m_full, weighted, n_cols, args.direction),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -260,11 +280,13 @@ def replica_seed(rank):
     return SEED + rank
 
 
-def workload_config(name, n, m, weighted, n_cols=None):
+def workload_config(name, n, m, weighted, n_cols=None, direction="csr"):
     kind, scale, ef, order, _ = WORKLOADS[name]
     c = {"workload": f"{name}{'-weighted' if weighted else ''}", "graph": kind, "scale": scale,
          "edge_factor": ef, "n_vertices": n, "n_edges": m, "vertex_order": order, "weighted": weighted,
          "seed": SEED, "l2": "inputs larger than L2 (no flush needed)", "parallelism": "replicas"}
+    if direction != "csr":
+        c["direction"] = "CSC input -> CSR"
     if n_cols is not None and n_cols != n:
         rs, cs = FOLDS.get(name, (0, 0))
         c.update({"n_rows": n, "n_cols": n_cols, "fold": f"rows merged by 2^{rs}, columns by 2^{cs}"})
@@ -360,6 +382,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="rmat28-degree", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--direction", default="csr", choices=["csr", "csc"],
+                    help="csc: transpose the workload's CSC back to CSR")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=None, help="JSON gt_config overrides")
@@ -400,7 +424,7 @@ def main():
     from paper_2501_06872_gb300 import binding
 
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
-    n, n_cols, rp, ci, vv = make_workload(args.workload, replica_seed(rank))
+    n, n_cols, rp, ci, vv = make_workload(args.workload, replica_seed(rank), args.direction)
     m = ci.numel()
     cfg = binding.default_config(n_cols, m)
     if args.config:
@@ -482,7 +506,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": dict(workload_config(args.workload, n, m, weighted, n_cols),
+                "config": dict(workload_config(args.workload, n, m, weighted, n_cols, args.direction),
                                gt_config=plan.config().as_dict()),
                 "roofline": roof,
                 "step_hbm": {"gbs_formula": step_gbs, "frac_of_peak": step_gbs / peak,
