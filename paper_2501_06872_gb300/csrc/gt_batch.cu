@@ -147,8 +147,12 @@ gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_
         const gt_graph_desc &d = descs[g1];
         const uint32_t nc = gt::desc_cols(d);  // keys and the union col_ptr span the columns
         const uint32_t nmax = nc > maxn ? nc : maxn;
-        const uint32_t keyw = bits_of(nmax - 1 ? nmax - 1 : 1) + bits_of(g1 - g);
-        const bool fits = sm + d.n_edges <= sub_cap && sn + nc < (1ull << 31) && keyw <= 32;
+        const uint32_t vb = bits_of(nmax - 1 ? nmax - 1 : 1);
+        // keys of at most 28 bits (four passes of 7-bit digits, whose runs fill
+        // sectors better than 8-bit ones) unless the columns alone need more
+        const uint32_t cap = vb + 1 > 28 ? 32 : 28;
+        const uint32_t keyw = vb + bits_of(g1 - g);
+        const bool fits = sm + d.n_edges <= sub_cap && sn + nc < (1ull << 31) && keyw <= cap;
         if (g1 > g && !fits) break;
         sm += d.n_edges;
         sn += nc;
