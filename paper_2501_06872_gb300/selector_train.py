@@ -40,7 +40,7 @@ def graph_spec(i: int, seed: int = 0x5EED0005):
 
 
 def _norm(c: dict) -> tuple:
-    if c["method"] == 1:  # the bulk-staged kernel (tile 0) has one CTA per SM whatever ctas_per_sm says
+    if c["method"] == 1:  # the bulk-staged kernel (tile 0) runs two 256-thread CTAs per SM whatever ctas_per_sm says
         return (1, c["radix_tile"], c["ctas_per_sm"] if c["radix_tile"] else 0)
     return (0, c["hdv_k"], c["table_log2"], c["block_threads"], c["ctas_per_sm"], c["warp_edges"],
             c["stage_edges"], c["flags"])
