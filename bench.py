@@ -105,6 +105,33 @@ def kernel_source_sha(kernel):
     return h.hexdigest()[:16]
 
 
+def record_traffic(csv_path, kernel, workload, note):
+    """Writes profiles/traffic.json's entry for (kernel, workload) from an ncu
+    --csv capture of dram__bytes_read.sum and dram__bytes_write.sum (one or
+    more launches of the kernel): their per-launch average, stamped with the
+    hash of the kernel's current sources."""
+    import csv
+    rows = [r for r in csv.reader(line for line in open(csv_path) if line.startswith('"'))]
+    h = rows[0]
+    ki, mi, ui, vi = h.index("ID"), h.index("Metric Name"), h.index("Metric Unit"), h.index("Metric Value")
+    ni = h.index("Kernel Name")
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    per = {}
+    for r in rows[1:]:
+        if kernel in r[ni] and r[mi].startswith("dram__bytes"):
+            per[r[ki]] = per.get(r[ki], 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
+    if not per:
+        raise SystemExit(f"no dram__bytes rows for {kernel} in {csv_path}")
+    vals = list(per.values())
+    out = os.path.join(ROOT, "profiles", "traffic.json")
+    d = json.load(open(out)) if os.path.exists(out) else {}
+    d[f"{kernel}@{workload}"] = {"dram_bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
+                                 "per_launch": vals, "source_sha": kernel_source_sha(kernel), "capture": note}
+    with open(out, "w") as fh:
+        json.dump(d, fh, indent=1)
+    print(json.dumps(d[f"{kernel}@{workload}"]))
+
+
 def load_traffic(kernel, workload):
     """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -391,7 +418,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 26)
     ap.add_argument("--ref-sample-edges", type=int, default=1 << 24)
+    ap.add_argument("--record-traffic", nargs=3, metavar=("CSV", "KERNEL", "NOTE"), default=None,
+                    help="write profiles/traffic.json's entry for KERNEL on --workload from an ncu CSV and exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args.record_traffic[0], args.record_traffic[1], args.workload, args.record_traffic[2])
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
