@@ -1,0 +1,66 @@
+"""Host-side logic of bench.py that needs no GPU: the traffic record taken
+from an ncu CSV, the metric-formula bytes, the digit-pass byte count and the
+workload table (rectangular folds, CSC direction)."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def _fake_csv(path, kernel, launches):
+    lines = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    for i, (rd, wr) in enumerate(launches):
+        lines.append(f'"{i}","{kernel}(RadixArgs)","dram__bytes_read.sum","Gbyte","{rd}"')
+        lines.append(f'"{i}","{kernel}(RadixArgs)","dram__bytes_write.sum","Mbyte","{wr}"')
+        lines.append(f'"{i}","{kernel}(RadixArgs)","gpu__time_duration.sum","msecond","1.0"')
+    lines.append('"9","k_other(X)","dram__bytes_read.sum","Gbyte","1000"')
+    path.write_text("==PROF== noise line\n" + "\n".join(lines) + "\n")
+
+
+def test_record_traffic_averages_launches_and_stamps_the_sources(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({"other@w": {"x": 1}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_2501_06872_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "include").mkdir()
+    real = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    for f in bench.KERNEL_SOURCES["k_radix_down_bulk"]:
+        (csrc / f).write_bytes(open(os.path.join(real, "paper_2501_06872_gb300", "csrc", f), "rb").read())
+    (tmp_path / "include" / "gt.h").write_bytes(open(os.path.join(real, "include", "gt.h"), "rb").read())
+    csv_path = tmp_path / "d.csv"
+    _fake_csv(csv_path, "k_radix_down_bulk", [(2.0, 500.0), (4.0, 1500.0)])
+    bench.record_traffic(str(csv_path), "k_radix_down_bulk", "wl", "note")
+    d = json.load(open(prof / "traffic.json"))
+    e = d["k_radix_down_bulk@wl"]
+    assert d["other@w"] == {"x": 1}
+    assert e["launches"] == 2
+    assert e["dram_bytes_per_launch"] == pytest.approx((2.5e9 + 5.5e9) / 2)
+    assert e["source_sha"] == bench.kernel_source_sha("k_radix_down_bulk")
+    assert bench.load_traffic("k_radix_down_bulk", "wl") == pytest.approx(4.0e9)
+    (csrc / "gt_radix.cu").write_text("changed")  # a changed kernel voids the record
+    assert bench.load_traffic("k_radix_down_bulk", "wl") is None
+
+
+def test_metric_bytes_and_pass_bytes():
+    lit, withv = bench.algorithmic_bytes(4, 10, True)
+    assert lit == 2 * 40 + 8 * 5 + 40 + 40 + 8 * 5 and withv == lit + 40
+    lit_r, _ = bench.algorithmic_bytes(4, 10, False, n_cols=9)
+    assert lit_r == 2 * 40 + 8 * 5 + 40 + 8 * 10
+    assert bench.radix_passes(1 << 28) == 4 and bench.radix_passes(1 << 20) == 3 and bench.radix_passes(2) == 1
+    # first pass 20 B/edge (weighted: col_idx + vals in, key + source + value out), later ones 24
+    assert bench.radix_down_bytes_per_edge(True, 4) == pytest.approx((20 + 3 * 24) / 4)
+    assert bench.radix_down_bytes_per_edge(False, 1) == pytest.approx(12)
+
+
+def test_workload_table():
+    for name, (rs, cs) in bench.FOLDS.items():
+        kind, scale, ef, order, weighted = bench.WORKLOADS[name]
+        assert 0 <= rs < scale and 0 <= cs < scale
+    c = bench.workload_config("rmat28-tall", 1 << 28, 1 << 32, True, 1 << 20)
+    assert c["n_rows"] == 1 << 28 and c["n_cols"] == 1 << 20 and "2^8" in c["fold"]
+    c = bench.workload_config("rmat25-random", 1 << 25, 1 << 29, False, 1 << 25, "csc")
+    assert c["direction"] == "CSC input -> CSR" and "n_cols" not in c

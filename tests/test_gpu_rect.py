@@ -246,6 +246,32 @@ def test_rect_batch_mixed_shapes():
         assert_same((cp.cpu().numpy().view(np.uint64), ri.cpu().numpy().view(np.uint32), vo.cpu().numpy()), exp)
 
 
+def test_rect_batch_many_sub_batches(monkeypatch):
+    """Tall and wide matrices split over several sub-batches (small edge cap)."""
+    from paper_2501_06872_gb300 import binding
+    monkeypatch.setenv("GT_BATCH_MAX_EDGES", "30000")
+    graphs, keep, exps = [], [], []
+    for i in range(10):
+        nr, nc = (3000, 17) if i % 2 else (17, 3000)
+        m = 9000 + 500 * i
+        _, rp, ci, vv = inputs.random_csr(nr, m, seed=60 + i, weighted=True, n_cols=nc)
+        d_rp, d_ci, d_vv = _dev(rp, ci, vv)
+        cp = torch.full((nc + 1,), -1, dtype=torch.int64, device="cuda")
+        ri = torch.full((m,), -1, dtype=torch.int32, device="cuda")
+        vo = torch.full((m,), -1.0, dtype=torch.float32, device="cuda")
+        keep.append((d_rp, d_ci, d_vv, cp, ri, vo))
+        graphs.append(dict(n=nr, n_cols=nc, m=m, row_ptr=d_rp, col_idx=d_ci, vals=d_vv, col_ptr=cp, row_idx=ri,
+                           vals_out=vo))
+        exps.append(oracle.transpose(rp, ci, vv, n_cols=nc))
+    plan = binding.BatchPlan(graphs, True)
+    plan.transpose()
+    plan.check()
+    assert plan.info()["sub_batches"] > 3
+    plan.close()
+    for (d_rp, d_ci, d_vv, cp, ri, vo), exp in zip(keep, exps):
+        assert_same((cp.cpu().numpy().view(np.uint64), ri.cpu().numpy().view(np.uint32), vo.cpu().numpy()), exp)
+
+
 def test_rect_batch_reports_column_out_of_range():
     from paper_2501_06872_gb300 import binding
     _, rp, ci, vv = inputs.random_csr(5000, 20000, seed=3, weighted=False, n_cols=40)
