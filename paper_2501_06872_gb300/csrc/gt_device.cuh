@@ -194,6 +194,20 @@ __device__ __forceinline__ uint32_t count_le(uint64_t rend, uint64_t e) {
   return pos;  // 0..32
 }
 
+// count_le on 32-bit offsets from the window start (windows of short rows
+// hold at most 32 x 2048 edges): half the shuffles.
+__device__ __forceinline__ uint32_t count_le32(uint32_t rend, uint32_t e) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (uint32_t s = 16; s > 0; s >>= 1) {
+    const uint32_t x = __shfl_sync(kFull, rend, pos + s - 1);
+    if (x <= e) pos += s;
+  }
+  const uint32_t x = __shfl_sync(kFull, rend, pos);
+  if (x <= e) pos += 1;
+  return pos;  // 0..32
+}
+
 // Index of the row containing edge e: largest u with row_ptr[u] <= e, searched
 // from row base_u on (warp-collective).  One 32-row window covers the dense
 // case; sparse stretches are walked 256 rows per round with independent loads.

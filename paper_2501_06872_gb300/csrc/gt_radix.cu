@@ -126,10 +126,11 @@ __global__ void k_expand_rows(const uint64_t *__restrict__ row_ptr, uint32_t n_r
     const uint32_t longmask = __ballot_sync(kFull, is_long);
     const uint64_t b = __shfl_sync(kFull, rbeg, 0);
     const uint64_t e = __shfl_sync(kFull, rend, 31);
-    if (longmask == 0) {
+    if (longmask == 0) {  // at most 32 x kLongRow edges: offsets from b fit 32 bits
+      const uint32_t rrel = (uint32_t)(rend - b);
       for (uint64_t p0 = b; p0 < e; p0 += 32) {
         const uint64_t p = p0 + lane;
-        const uint32_t pos = count_le(rend, p);  // warp-collective
+        const uint32_t pos = count_le32(rrel, (uint32_t)(p - b));  // warp-collective
         if (p < e) src[p] = (uint32_t)(r0 + pos);
       }
     } else {
@@ -865,10 +866,11 @@ __global__ void k_b_expand(BatchView bv, const unsigned long long *__restrict__ 
     const uint64_t b = __shfl_sync(kFull, rbeg, 0);
     const uint64_t e = __shfl_sync(kFull, rend, 31);
     const bool sane = __all_sync(kFull, !(rend > m || rbeg > rend)) && e >= b;
-    if (longmask == 0 && sane) {
+    if (longmask == 0 && sane) {  // at most 32 x kLongRow edges: offsets from b fit 32 bits
+      const uint32_t rrel = (uint32_t)(rend - b);
       for (uint64_t p0 = b; p0 < e; p0 += 32) {
         const uint64_t p = p0 + lane;
-        const uint32_t pos = count_le(rend, p);  // warp-collective
+        const uint32_t pos = count_le32(rrel, (uint32_t)(p - b));  // warp-collective
         if (p < e) src[base + p] = (uint32_t)(r0 + pos);
       }
     } else {
