@@ -190,15 +190,19 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
                             const float *vals, uint64_t *col_ptr, uint32_t *row_idx,
                             float *vals_out, void *stream);
 
-/* Asynchronous gt_transpose_host: enqueues the input copies and the
- * transposition on `stream` and the output copies on a stream the plan owns,
- * and returns without waiting.  The next call's input copies overlap this
- * call's output copies (the next transposition waits for them), so a loop of
- * calls keeps both copy directions busy.  Host buffers must stay untouched
- * (inputs) and unread (outputs) until gt_plan_host_wait returns; calls that
- * overwrite one pair of host output buffers leave the last call's CSC there.
- * gt_plan_host_wait waits for all outstanding calls and returns the device
- * status. */
+/* Asynchronous gt_transpose_host: enqueues the transposition on `stream`,
+ * its input copies on a stream the plan owns and its output copies on a
+ * second one, and returns without waiting.  A call's input copies start as
+ * soon as the previous call's transposition has stopped reading its device
+ * inputs (after the first digit pass of the radix method; at the end of the
+ * HLH method).  The plan keeps two device output sets when memory allows
+ * (allocated on the first call) and uses them in turn, so a transposition
+ * need not wait for the previous call's output copies: a loop of calls keeps
+ * both copy directions and the SMs busy together.  Host buffers must stay
+ * untouched (inputs) and unread (outputs) until gt_plan_host_wait returns;
+ * calls that overwrite one set of host output buffers leave the last call's
+ * CSC there.  gt_plan_host_wait waits for all outstanding calls and returns
+ * the device status.  Calls on one plan use one stream. */
 gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_idx,
                                   const float *vals, uint64_t *col_ptr, uint32_t *row_idx, float *vals_out,
                                   void *stream);

@@ -40,16 +40,22 @@ struct gt_plan_s {
   uint64_t ws_bytes = 0;
   void *allocs[32] = {};
   int nalloc = 0;
-  // device copies for gt_transpose_host (allocated on first use)
-  uint64_t *h_row_ptr = nullptr, *h_col_ptr = nullptr;
-  uint32_t *h_col_idx = nullptr, *h_row_idx = nullptr;
-  float *h_vals = nullptr, *h_vals_out = nullptr;
-  void *host_allocs[6] = {};
+  // device copies for gt_transpose_host (allocated on first use); the
+  // asynchronous path adds a second output set (h_col_ptr[1] ...)
+  uint64_t *h_row_ptr[2] = {}, *h_col_ptr[2] = {};
+  uint32_t *h_col_idx[2] = {}, *h_row_idx[2] = {};
+  float *h_vals[2] = {}, *h_vals_out[2] = {};
+  void *host_allocs[12] = {};
   int nhost = 0;
-  // gt_transpose_host_async: output copies on their own stream, ordered by events
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_computed = nullptr, ev_copied = nullptr;
-  cudaStream_t async_stream = nullptr;
+  // gt_transpose_host_async: input copies on in_stream once the last
+  // transposition that read that input set is past its inputs
+  // (ev_inputs_read[set]); output copies on copy_stream; input and output
+  // sets used in turn (ev_copied[set] guards an output set's reuse)
+  cudaStream_t copy_stream = nullptr, in_stream = nullptr;
+  cudaEvent_t ev_computed = nullptr, ev_copied[2] = {}, ev_inputs_read[2] = {}, ev_inputs_in = nullptr;
+  int slot = 0, slots = 1;
+  bool second_tried = false;  // the second input and output sets are attempted once
+  cudaEvent_t pending_inputs_read = nullptr;  // handed to the next transposition's Problem
   // per-step timing
   bool timing = false;
   std::vector<gt::StepEvents> events;
@@ -411,6 +417,7 @@ static gt_status transpose_impl(gt_plan plan, uint32_t n_rows, uint32_t n, uint6
     w.smem_scatter = gt::smem_scatter_bytes(w.W, w.kmax, w.tlog2, 0, 0, w.has_vals);
   }
   gt::Problem pb{row_ptr, col_idx, vals, col_ptr, row_idx, vals_out};
+  pb.inputs_read = plan->pending_inputs_read;
   gt::StepEvents *ev = nullptr;
   if (plan->timing) {
     gt::StepEvents e;
@@ -546,28 +553,48 @@ gt_status gt_plan_shape(gt_plan plan, uint32_t *n_rows, uint32_t *n_cols, uint64
 
 uint64_t gt_plan_edges(gt_plan plan) { return plan ? plan->w.m : 0; }
 
-static gt_status host_staging(gt_plan plan) {
+static gt_status host_alloc(gt_plan plan, void **field, size_t bytes) {
+  void *q = nullptr;
+  if (plan->nhost >= 12 || cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return GT_ERR_NO_MEMORY;
+  }
+  plan->host_allocs[plan->nhost++] = q;
+  *field = q;
+  return GT_OK;
+}
+
+// Device staging of the host paths: input and output set 0 (and, with
+// second_set, set 1 if it can be allocated).
+static gt_status host_staging(gt_plan plan, bool second_set) {
   const size_t n = plan->w.n, nr = plan->w.n_rows, m = plan->w.m;
-  if (!plan->h_row_ptr) {
-    void *q;
-#define GT_HA(field, bytes)                                              \
-  do {                                                                   \
-    if (cudaMalloc(&q, (bytes) ? (bytes) : 16) != cudaSuccess) {         \
-      cudaGetLastError();                                                \
-      return GT_ERR_NO_MEMORY;                                           \
-    }                                                                    \
-    plan->host_allocs[plan->nhost++] = q;                                \
-    plan->field = (decltype(plan->field))q;                              \
-  } while (0)
-    GT_HA(h_row_ptr, (nr + 1) * 8);
-    GT_HA(h_col_ptr, (n + 1) * 8);
-    GT_HA(h_col_idx, m * 4);
-    GT_HA(h_row_idx, m * 4);
-    if (plan->w.has_vals) {
-      GT_HA(h_vals, m * 4);
-      GT_HA(h_vals_out, m * 4);
+  const bool v = plan->w.has_vals != 0;
+  auto alloc_set = [&](int k) {
+    return host_alloc(plan, (void **)&plan->h_row_ptr[k], (nr + 1) * 8) == GT_OK &&
+           host_alloc(plan, (void **)&plan->h_col_ptr[k], (n + 1) * 8) == GT_OK &&
+           host_alloc(plan, (void **)&plan->h_col_idx[k], m * 4) == GT_OK &&
+           host_alloc(plan, (void **)&plan->h_row_idx[k], m * 4) == GT_OK &&
+           (!v || host_alloc(plan, (void **)&plan->h_vals[k], m * 4) == GT_OK) &&
+           (!v || host_alloc(plan, (void **)&plan->h_vals_out[k], m * 4) == GT_OK);
+  };
+  auto drop_set = [&](int k, int keep) {  // frees what a failed alloc_set(k) got
+    while (plan->nhost > keep) cudaFree(plan->host_allocs[--plan->nhost]);
+    plan->h_row_ptr[k] = plan->h_col_ptr[k] = nullptr;
+    plan->h_col_idx[k] = plan->h_row_idx[k] = nullptr;
+    plan->h_vals[k] = plan->h_vals_out[k] = nullptr;
+  };
+  if (!plan->h_row_ptr[0]) {
+    const int keep = plan->nhost;
+    if (!alloc_set(0)) {
+      drop_set(0, keep);
+      return GT_ERR_NO_MEMORY;
     }
-#undef GT_HA
+  }
+  if (second_set && !plan->second_tried) {  // optional: without it the calls share one set
+    plan->second_tried = true;
+    const int keep = plan->nhost;
+    if (alloc_set(1)) plan->slots = 2;
+    else drop_set(1, keep);
   }
   return GT_OK;
 }
@@ -587,24 +614,26 @@ gt_status gt_transpose_host(gt_plan plan, const uint64_t *row_ptr, const uint32_
   if (ast != GT_OK) return ast;
   const size_t n = plan->w.n, nr = plan->w.n_rows, m = plan->w.m;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((ast = host_staging(plan)) != GT_OK) return ast;
+  if ((ast = host_staging(plan, false)) != GT_OK) return ast;
+  // asynchronous calls still copying use the same device buffers
+  if (plan->in_stream && cudaStreamSynchronize(plan->in_stream) != cudaSuccess) return GT_ERR_CUDA;
   if (plan->copy_stream && cudaStreamSynchronize(plan->copy_stream) != cudaSuccess) return GT_ERR_CUDA;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(plan->h_row_ptr[0], row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
-  if (m && (e = cudaMemcpyAsync(plan->h_col_idx, col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if (m && (e = cudaMemcpyAsync(plan->h_col_idx[0], col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
-  if (vals && m && (e = cudaMemcpyAsync(plan->h_vals, vals, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if (vals && m && (e = cudaMemcpyAsync(plan->h_vals[0], vals, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return from_cuda(e);
-  gt_status st = gt_transpose(plan, plan->h_row_ptr, plan->h_col_idx, vals ? plan->h_vals : nullptr,
-                              plan->h_col_ptr, plan->h_row_idx, vals ? plan->h_vals_out : nullptr, stream);
+  gt_status st = gt_transpose(plan, plan->h_row_ptr[0], plan->h_col_idx[0], vals ? plan->h_vals[0] : nullptr,
+                              plan->h_col_ptr[0], plan->h_row_idx[0], vals ? plan->h_vals_out[0] : nullptr, stream);
   if (st != GT_OK) return st;
-  if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr[0], (n + 1) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return from_cuda(e);
-  if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx, m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx[0], m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return from_cuda(e);
   if (vals && m &&
-      (e = cudaMemcpyAsync(vals_out, plan->h_vals_out, m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      (e = cudaMemcpyAsync(vals_out, plan->h_vals_out[0], m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return from_cuda(e);
   return gt_plan_status(plan);
 }
@@ -615,46 +644,63 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
   if (ast != GT_OK) return ast;
   const size_t n = plan->w.n, nr = plan->w.n_rows, m = plan->w.m;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((ast = host_staging(plan)) != GT_OK) return ast;
+  if ((ast = host_staging(plan, true)) != GT_OK) return ast;
   if (!plan->copy_stream) {
-    if (cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return GT_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&plan->ev_computed, cudaEventDisableTiming) != cudaSuccess) return GT_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&plan->ev_copied, cudaEventDisableTiming) != cudaSuccess) return GT_ERR_CUDA;
-    if (cudaEventRecord(plan->ev_copied, plan->copy_stream) != cudaSuccess) return GT_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&plan->in_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_computed, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_copied[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_copied[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_inputs_read[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_inputs_read[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_inputs_in, cudaEventDisableTiming) != cudaSuccess)
+      return from_cuda(cudaGetLastError());
+    // the device inputs are free once everything enqueued on s so far is done
+    if (cudaEventRecord(plan->ev_inputs_read[0], s) != cudaSuccess ||
+        cudaEventRecord(plan->ev_inputs_read[1], s) != cudaSuccess)
+      return GT_ERR_CUDA;
   }
-  plan->async_stream = s;
+  const int k = plan->slot;
+  plan->slot = (plan->slot + 1) % plan->slots;
   cudaError_t e;
-  // inputs: on the caller's stream (after the previous transposition read them)
-  if ((e = cudaMemcpyAsync(plan->h_row_ptr, row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  // inputs: on in_stream, once the last transposition that read set k is past its inputs
+  cudaStream_t in = plan->in_stream;
+  if ((e = cudaStreamWaitEvent(in, plan->ev_inputs_read[k], 0)) != cudaSuccess) return from_cuda(e);
+  if ((e = cudaMemcpyAsync(plan->h_row_ptr[k], row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, in)) != cudaSuccess)
     return from_cuda(e);
-  if (m && (e = cudaMemcpyAsync(plan->h_col_idx, col_idx, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if (m && (e = cudaMemcpyAsync(plan->h_col_idx[k], col_idx, m * 4, cudaMemcpyHostToDevice, in)) != cudaSuccess)
     return from_cuda(e);
-  if (vals && m && (e = cudaMemcpyAsync(plan->h_vals, vals, m * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if (vals && m && (e = cudaMemcpyAsync(plan->h_vals[k], vals, m * 4, cudaMemcpyHostToDevice, in)) != cudaSuccess)
     return from_cuda(e);
-  // the transposition overwrites the device outputs: wait for the previous call's output copies
-  if ((e = cudaStreamWaitEvent(s, plan->ev_copied, 0)) != cudaSuccess) return from_cuda(e);
-  gt_status st = gt_transpose(plan, plan->h_row_ptr, plan->h_col_idx, vals ? plan->h_vals : nullptr,
-                              plan->h_col_ptr, plan->h_row_idx, vals ? plan->h_vals_out : nullptr, stream);
+  if ((e = cudaEventRecord(plan->ev_inputs_in, in)) != cudaSuccess) return from_cuda(e);
+  // the transposition: after its inputs arrived and output set k's last copy-out
+  if ((e = cudaStreamWaitEvent(s, plan->ev_inputs_in, 0)) != cudaSuccess) return from_cuda(e);
+  if ((e = cudaStreamWaitEvent(s, plan->ev_copied[k], 0)) != cudaSuccess) return from_cuda(e);
+  plan->pending_inputs_read = plan->ev_inputs_read[k];
+  gt_status st = gt_transpose(plan, plan->h_row_ptr[k], plan->h_col_idx[k], vals ? plan->h_vals[k] : nullptr,
+                              plan->h_col_ptr[k], plan->h_row_idx[k], vals ? plan->h_vals_out[k] : nullptr, stream);
+  plan->pending_inputs_read = nullptr;
   if (st != GT_OK) return st;
-  // outputs: on the plan's copy stream, after the transposition
+  // outputs: on copy_stream, after the transposition
   cudaStream_t c = plan->copy_stream;
   if ((e = cudaEventRecord(plan->ev_computed, s)) != cudaSuccess) return from_cuda(e);
   if ((e = cudaStreamWaitEvent(c, plan->ev_computed, 0)) != cudaSuccess) return from_cuda(e);
-  if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr[k], (n + 1) * 8, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
     return from_cuda(e);
-  if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx, m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
+  if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx[k], m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
     return from_cuda(e);
   if (vals && m &&
-      (e = cudaMemcpyAsync(vals_out, plan->h_vals_out, m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
+      (e = cudaMemcpyAsync(vals_out, plan->h_vals_out[k], m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
     return from_cuda(e);
-  if ((e = cudaEventRecord(plan->ev_copied, c)) != cudaSuccess) return from_cuda(e);
+  if ((e = cudaEventRecord(plan->ev_copied[k], c)) != cudaSuccess) return from_cuda(e);
   return GT_OK;
 }
 
 gt_status gt_plan_host_wait(gt_plan plan) {
   if (!plan) return GT_ERR_INVALID_ARG;
-  if (plan->copy_stream) {
-    cudaError_t e = cudaStreamSynchronize(plan->copy_stream);
+  for (cudaStream_t q : {plan->in_stream, plan->copy_stream}) {
+    if (!q) continue;
+    cudaError_t e = cudaStreamSynchronize(q);
     if (e != cudaSuccess) return from_cuda(e);
   }
   return gt_plan_status(plan);
@@ -664,9 +710,12 @@ void gt_plan_destroy(gt_plan plan) {
   if (!plan) return;
   if (plan->last) cudaStreamSynchronize(plan->last);
   if (plan->copy_stream) {
+    cudaStreamSynchronize(plan->in_stream);
     cudaStreamSynchronize(plan->copy_stream);
-    cudaEventDestroy(plan->ev_computed);
-    cudaEventDestroy(plan->ev_copied);
+    for (cudaEvent_t x : {plan->ev_computed, plan->ev_copied[0], plan->ev_copied[1], plan->ev_inputs_read[0],
+                          plan->ev_inputs_read[1], plan->ev_inputs_in})
+      if (x) cudaEventDestroy(x);
+    cudaStreamDestroy(plan->in_stream);
     cudaStreamDestroy(plan->copy_stream);
   }
   drop_events(plan);

@@ -85,6 +85,9 @@ struct Problem {
   uint64_t *col_ptr;
   uint32_t *row_idx;
   float *vals_out;
+  // if set: recorded on the stream once no later kernel of the call reads
+  // row_ptr, col_idx or vals (the next call's inputs may then be copied in)
+  cudaEvent_t inputs_read = nullptr;
 };
 
 // Events recorded between the steps of one call (null = not timed).

@@ -780,6 +780,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     nl += 2;
   }
   if (m == 0) {  // the expansion only validated row_ptr
+    if (pb.inputs_read && (err = cudaEventRecord(pb.inputs_read, s)) != cudaSuccess) return err;
     if (launches) *launches += nl;
     return cudaGetLastError();
   }
@@ -806,6 +807,8 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     }
     nl += 3;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // the first pass was the last to read col_idx and vals (row_ptr: the expansion)
+    if (p == 1 && pb.inputs_read && (err = cudaEventRecord(pb.inputs_read, s)) != cudaSuccess) return err;
     in_key = ok;
     in_u = ou;
     in_w = ow;

@@ -321,6 +321,31 @@ def test_host_async_pipeline():
     plan.close()
 
 
+@pytest.mark.parametrize("name", ["radix", "hdv64", "atomic"])
+def test_host_async_pipeline_different_graphs(name):
+    """Four overlapped host calls on three different graphs of one shape: the
+    next call's input copies start once the previous transposition stopped
+    reading its inputs, and the two device output sets alternate; every call
+    must still give its own graph's CSC."""
+    from paper_2501_06872_gb300 import binding
+    n, m = 6000, 120000
+    graphs = [inputs.random_csr(n, m, seed=70 + k, weighted=True, hot=5, hot_frac=0.3) for k in range(3)]
+    order = [0, 1, 2, 1]
+    plan = binding.Plan(n, m, True, config(**CONFIGS[name]))
+    hin = [[torch.from_numpy(np.ascontiguousarray(x).view(t)).pin_memory()
+            for x, t in ((g[1], np.int64), (g[2], np.int32), (g[3], np.float32))] for g in graphs]
+    outs = [(torch.empty(n + 1, dtype=torch.int64).pin_memory(), torch.empty(m, dtype=torch.int32).pin_memory(),
+             torch.empty(m, dtype=torch.float32).pin_memory()) for _ in order]
+    for k, gi in enumerate(order):
+        plan.transpose_host_async(*hin[gi], *outs[k])
+    plan.host_wait()
+    for k, gi in enumerate(order):
+        _, rp, ci, vv = graphs[gi]
+        got = (outs[k][0].numpy().view(np.uint64), outs[k][1].numpy().view(np.uint32), outs[k][2].numpy())
+        assert_same(got, oracle.transpose(rp, ci, vv))
+    plan.close()
+
+
 def test_plan_reuse_and_stats():
     from paper_2501_06872_gb300 import binding
     n, rp, ci, vv = inputs.rmat_csr(13, 16, seed=2, order="degree", weighted=True)
