@@ -321,13 +321,14 @@ def test_host_async_pipeline():
     plan.close()
 
 
-@pytest.mark.parametrize("name", ["radix", "hdv64", "atomic"])
-def test_host_async_pipeline_different_graphs(name):
+@pytest.mark.parametrize("name,sets", [("radix", 2), ("hdv64", 2), ("atomic", 2), ("radix", 1), ("hdv64", 1)])
+def test_host_async_pipeline_different_graphs(name, sets, monkeypatch):
     """Four overlapped host calls on three different graphs of one shape: the
     next call's input copies start once the previous transposition stopped
     reading its inputs, and the two device output sets alternate; every call
     must still give its own graph's CSC."""
     from paper_2501_06872_gb300 import binding
+    monkeypatch.setenv("GT_HOST_SETS", str(sets))  # 1: the one-set fallback of a plan short of memory
     n, m = 6000, 120000
     graphs = [inputs.random_csr(n, m, seed=70 + k, weighted=True, hot=5, hot_frac=0.3) for k in range(3)]
     order = [0, 1, 2, 1]
