@@ -62,12 +62,12 @@ extern "C" {
 typedef enum gt_status {
     GT_OK = 0,
     GT_ERR_INVALID_ARG = 1,   /* null pointer, size mismatch, bad config field   */
-    GT_ERR_OUT_OF_RANGE = 2,  /* some col_idx[e] >= n (device-detected)           */
-    GT_ERR_BAD_ROW_PTR = 3,   /* row_ptr[0] != 0, decreasing, or row_ptr[n] != m  */
+    GT_ERR_OUT_OF_RANGE = 2,  /* some col_idx[e] >= n_cols (device-detected)      */
+    GT_ERR_BAD_ROW_PTR = 3,   /* row_ptr[0] != 0, decreasing, row_ptr[n_rows] != m */
     GT_ERR_NO_MEMORY = 4,     /* workspace allocation failed                       */
     GT_ERR_CUDA = 5,          /* a CUDA runtime call failed                        */
     GT_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired                */
-    GT_ERR_UNSUPPORTED = 7    /* size outside what this build handles              */
+    GT_ERR_UNSUPPORTED = 7    /* size outside what the library handles             */
 } gt_status;
 
 /* Launch/method configuration.  Any valid configuration yields the same bytes. */

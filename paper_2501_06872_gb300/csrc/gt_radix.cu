@@ -8,7 +8,7 @@
 // graphs whose working set is far larger than L2.
 //
 // Per call: the row expansion writes the source of every edge; then per
-// digit pass (passes = ceil(bits(n-1) / 8), digits split evenly):
+// digit pass (passes = ceil(bits(n-1) / 8) for n columns, digits split evenly):
 //   upsweep    per-CTA digit counts of the CTA's contiguous tile range
 //              (with the bulk downsweep, two upsweep CTAs per range)
 //   offsets    exclusive scan of the table in (digit, CTA) order
