@@ -59,9 +59,9 @@ struct DevWork {
   uint32_t *cand = nullptr;                    // [kmax]
   uint32_t *ties = nullptr;                    // [kTieCap]
   uint32_t *biglist = nullptr;                 // [big_cap]
-  // [m] entries: weighted graphs keep LDV entries here as u64 (value bits << 32 |
-  // source, bit 31 of the source tagging split rows) until the LDV sort moves them
-  // to the outputs; both kinds reuse it as the radix sort's second buffer.
+  // HLH, [m] entries: weighted graphs keep LDV entries here as u64 (value bits
+  // << 32 | source, bit 31 of the source tagging split rows) until the LDV sort
+  // moves them to the outputs; the long-list radix sort uses it as its second buffer.
   void *scratch = nullptr;
   // radix method
   int method = 0;
@@ -102,7 +102,8 @@ struct StepEvents {
 cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem &pb, cudaStream_t stream,
                           StepEvents *events, uint32_t *launches);
 
-// Radix method: enqueues the digit passes and the degree runs (deg must be zeroed).
+// Radix method: enqueues the row expansion, the digit passes and col_ptr
+// from the sorted keys (w.r_nlong and the gap count must be zeroed).
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches,
                       StepEvents *events);
 
