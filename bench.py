@@ -575,6 +575,25 @@ def selector_summary(plan, rp, ci, vv, cp, ri, vo, n, m):
             "heldout_graphs": rep["n_test"]}
 
 
+def gpu_local_cpus(device):
+    """CPUs of the NUMA node the GPU's PCI function reports (sysfs), or None."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(device)
+        path = f"/sys/bus/pci/devices/{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0/numa_node"
+        node = int(open(path).read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
 def host_inputs(rp, ci, vv, n, m, weighted, n_cols=None):
     """Pinned host copies of the inputs and pinned host outputs for the
     end-to-end leg, or a note if host memory is too small."""
@@ -590,6 +609,28 @@ def host_inputs(rp, ci, vv, n, m, weighted, n_cols=None):
         pass
     if avail and need > 0.7 * avail:
         return f"host memory {avail / 2**30:.0f} GiB too small for {need / 2**30:.0f} GiB pinned buffers"
+    # pinned pages land on the NUMA node of the CPU that first touches them:
+    # allocate and fill them from the CPUs next to the GPU
+    keep = None
+    cpus = gpu_local_cpus(rp.device.index if rp.device.index is not None else 0)
+    if cpus:
+        try:
+            keep = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, cpus)
+        except OSError:
+            keep = None
+    try:
+        return _pinned_buffers(rp, ci, vv, n, m, weighted, nc)
+    finally:
+        if keep:
+            try:
+                os.sched_setaffinity(0, keep)
+            except OSError:
+                pass
+
+
+def _pinned_buffers(rp, ci, vv, n, m, weighted, nc):
+    import torch
     h_rp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
     h_ci = torch.empty(m, dtype=torch.int32, pin_memory=True)
     h_vv = torch.empty(m, dtype=torch.float32, pin_memory=True) if weighted else None
