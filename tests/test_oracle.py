@@ -297,3 +297,24 @@ def test_rect_sampled_columns_match_full():
         d = int(deg[i])
         assert np.array_equal(rows[off:off + d], full[1][full[0][v]:full[0][v + 1]])
         off += d
+
+
+def test_property_random_shapes_vs_definition():
+    """Arbitrary small CSR matrices (any shape, duplicates, empty rows and
+    columns, weighted or not) against the brute-force definition."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=300, deadline=None, derandomize=True)
+    @hyp.given(st.integers(1, 12), st.integers(1, 12), st.data(), st.booleans())
+    def check(nr, nc, data, weighted):
+        rows = [data.draw(st.lists(st.integers(0, nc - 1), max_size=6)) for _ in range(nr)]
+        row_ptr, col_idx = csr_from_rows(nr, rows)
+        vals = (np.arange(col_idx.size, dtype=np.float32) * 0.5 - 3.0) if weighted else None
+        got = oracle.transpose(row_ptr, col_idx, vals, n_cols=nc)
+        exp = brute_transpose(row_ptr, col_idx, vals, n_cols=nc)
+        assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+        if weighted:
+            assert np.array_equal(got[2].view(np.uint32), exp[2].view(np.uint32))
+
+    check()
