@@ -114,19 +114,26 @@ def transpose(row_ptr, col_idx, vals=None, n_cols=None):
 
 
 def transpose_range(row_ptr, col_idx, vals, v_lo, v_hi):
-    """Destinations [v_lo, v_hi) only: (col_ptr[v_lo..v_hi], rows, vals) with global offsets."""
+    """Destinations [v_lo, v_hi) only: (col_ptr[v_lo..v_hi], rows, vals) with
+    global offsets.  A first call of the C routine gives the sizes, a second
+    one the lists.  The C call releases the GIL (ctypes), so ranges may run in
+    parallel threads; the arrays must not change meanwhile."""
     n, row_ptr, col_idx, vals = _inputs(row_ptr, col_idx, vals)
     m = col_idx.shape[0]
-    sel = (col_idx >= v_lo) & (col_idx < v_hi)
-    cnt = int(np.count_nonzero(sel))
+    lib = _load()
     col_ptr = np.empty(v_hi - v_lo + 1, dtype=np.uint64)
-    rows = np.empty(cnt, dtype=np.uint32)
-    vo = np.empty(cnt, dtype=np.float32) if vals is not None else None
-    rc = _load().oracle_transpose_range(n, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), v_lo, v_hi,
-                                        _ptr(col_ptr), _ptr(rows), _ptr(vo))
+    rc = lib.oracle_transpose_range(n, m, _ptr(row_ptr), _ptr(col_idx), None, v_lo, v_hi, _ptr(col_ptr),
+                                    None, None)
     if rc:
         raise OracleError(rc)
-    return col_ptr, rows, vo
+    cnt = int(col_ptr[-1] - col_ptr[0])
+    rows = np.empty(max(cnt, 1), dtype=np.uint32)
+    vo = np.empty(max(cnt, 1), dtype=np.float32) if vals is not None else None
+    rc = lib.oracle_transpose_range(n, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), v_lo, v_hi,
+                                    _ptr(col_ptr), _ptr(rows), _ptr(vo))
+    if rc:
+        raise OracleError(rc)
+    return col_ptr, rows[:cnt], (vo[:cnt] if vo is not None else None)
 
 
 def columns(row_ptr, col_idx, vals, cols, n_cols=None):

@@ -101,6 +101,8 @@ int oracle_transpose(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint
  * entries holding the GLOBAL offsets col_ptr[v_lo .. v_hi]; row_idx_part and
  * vals_out_part hold entries col_ptr[v_lo] .. col_ptr[v_hi]-1 of the full
  * output.  Running it over consecutive ranges reproduces oracle_transpose.
+ * With row_idx_part == NULL only col_ptr_part is produced (the sizes the
+ * caller needs to hold the range's lists).
  */
 int oracle_transpose_range(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32_t *col_idx,
                            const float *vals, uint32_t v_lo, uint32_t v_hi, uint64_t *col_ptr_part,
@@ -125,6 +127,7 @@ int oracle_transpose_range(uint32_t n, uint64_t m, const uint64_t *row_ptr, cons
         run += d;
     }
     col_ptr_part[w] = run;
+    if (!row_idx_part) { free(ip); return OR_OK; } /* sizes only */
     for (uint64_t u = 0; u < n; ++u) {
         for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
             uint32_t v = col_idx[e];
