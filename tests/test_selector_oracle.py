@@ -267,3 +267,33 @@ def test_trainer_graph_specs_follow_the_stated_ranges():
     assert all(8 <= s["edge_factor"] <= 32 for s in specs)
     assert {s["order"] for s in specs} == {"degree", "random"}
     assert specs[3] == st.graph_spec(3)  # seeded
+
+
+def test_forward_hand_worked_2_3_2_network():
+    """A 2-3-2 network with small integer weights, worked out by hand (the
+    values below are not computed by any code).  The parameter vector is laid
+    out in the documented order mu, sd, lo, hi, W1 (rows = hidden units), b1,
+    W2, b2, W3, b3.  A transposed W2, a missing standardisation, a missing
+    ReLU in either layer or a wrong bias would each change the outputs.
+
+    sample 1: x = (3, 0) -> x' = ((3-1)/2, (0+1)/1) = (1, 1)
+      a1 = (1+2+0, -3+1+1, 0-1+2) = (3, -1, 1) -> h1 = (3, 0, 1)
+      a2 = (3+1-1, 0+0, -3+0-9) = (3, 0, -12) -> h2 = (3, 0, 0)
+      y  = (3+0.5, 6+1) = (3.5, 7)
+    sample 2: x = (-1, -1) -> x' = (-1, 0)
+      a1 = (-1+0, 3+1, 0+2) = (-1, 4, 2) -> h1 = (0, 4, 2)
+      a2 = (2-1, 8+0, 4-9) = (1, 8, -5) -> h2 = (1, 8, 0)
+      y  = (1+8+0.5, 2+1) = (9.5, 3)
+    """
+    mu, sd = [1.0, -1.0], [2.0, 1.0]
+    lo, hi = [0.0, 0.0], [1.0, 1.0]
+    W1 = [1.0, 2.0, -3.0, 1.0, 0.0, -1.0]
+    b1 = [0.0, 1.0, 2.0]
+    W2 = [1.0, 0.0, 1.0, 0.0, 2.0, 0.0, -1.0, 1.0, 0.0]
+    b2 = [-1.0, 0.0, -9.0]
+    W3 = [1.0, 1.0, 1.0, 2.0, 0.0, -3.0]
+    b3 = [0.5, 1.0]
+    p = np.array(mu + sd + lo + hi + W1 + b1 + W2 + b2 + W3 + b3)
+    assert so.layout(2, 3, 2)["total"] == p.size == 37
+    y, _ = so.forward(p, np.array([[3.0, 0.0], [-1.0, -1.0]]), 2, 3, 2)
+    assert np.array_equal(y, np.array([[3.5, 7.0], [9.5, 3.0]]))
