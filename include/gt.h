@@ -208,6 +208,21 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
                                   void *stream);
 gt_status gt_plan_host_wait(gt_plan plan);
 
+/* Copy timing of gt_transpose_host_async calls made while per-step timing is
+ * enabled (gt_plan_enable_timing; up to 64 calls per enable), from CUDA
+ * events recorded around each call's input copies (on the plan's input
+ * stream) and output copies (on its output stream).  Synchronises those
+ * events.  All fields are 0 when no call was recorded. */
+typedef struct gt_host_timing {
+    uint32_t calls;     /* calls recorded                                          */
+    float h2d_ms;       /* average duration of one call's input copies              */
+    float d2h_ms;       /* average duration of one call's output copies             */
+    float overlap_ms;   /* average time per call with copies in both directions in
+                           progress at once                                          */
+    float span_ms;      /* first recorded input copy start to last output copy end  */
+} gt_host_timing;
+gt_status gt_plan_host_timing(gt_plan plan, gt_host_timing *timing);
+
 /* Allocation-free variant of gt_transpose (no counterpart in the paper).
  * For callers that must not allocate device memory on the call path, e.g. a
  * host program whose pool already owns all device memory, or a latency-
@@ -216,11 +231,15 @@ gt_status gt_plan_host_wait(gt_plan plan);
  * gt_transpose; the workspace comes from a fixed 64 MiB array that every GPU
  * loading this library holds until the process exits.  Graphs whose
  * workspace does not fit (roughly 12 bytes per vertex plus 4 bytes per edge,
- * 8 with values) return GT_ERR_UNSUPPORTED.  Runs the pure-atomic
- * configuration, synchronises `stream`, and returns the device status.  All
- * calls share the array: calls that overlap on the GPU race.  The first call
- * on a device performs a one-time set-up (looks up the array's address, sets
- * kernel limits) and should come before any stream capture on that device. */
+ * 8 with values) return GT_ERR_UNSUPPORTED before anything is enqueued.
+ * Runs the pure-atomic configuration, synchronises `stream`, and returns the
+ * device status (CUDA failures: GT_ERR_CUDA with the text in
+ * gt_last_cuda_error(); a call that fails after enqueueing work waits for it
+ * before returning).  All calls share the array and it keeps the previous
+ * call's contents: calls that overlap on the GPU race.  Every call looks up
+ * the array's address in the current context; the first call in each CUDA
+ * context also sets kernel limits and should come before any stream capture
+ * on that device. */
 gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint64_t *row_ptr,
                                const uint32_t *col_idx, const float *vals, uint64_t *col_ptr,
                                uint32_t *row_idx, float *vals_out, void *stream);

@@ -59,16 +59,27 @@ struct gt_plan_s {
   // per-step timing
   bool timing = false;
   std::vector<gt::StepEvents> events;
+  // gt_transpose_host_async while timing: events around each call's input
+  // copies (on in_stream) and output copies (on copy_stream)
+  struct HostEvents {
+    cudaEvent_t in0, in1, out0, out1;
+  };
+  std::vector<HostEvents> host_events;
   uint32_t launches = 0;
 };
 
 namespace {
+constexpr size_t kMaxHostEvents = 64;  // calls whose copies are timed per enable
+
 void drop_events(gt_plan p) {
   for (auto &e : p->events) {
     for (int i = 0; i < 6; ++i) cudaEventDestroy(e.ev[i]);
     for (int i = 0; i < 8; ++i) cudaEventDestroy(e.down[i]);
   }
   p->events.clear();
+  for (auto &h : p->host_events)
+    for (cudaEvent_t x : {h.in0, h.in1, h.out0, h.out1}) cudaEventDestroy(x);
+  p->host_events.clear();
 }
 }  // namespace
 
@@ -238,6 +249,9 @@ gt_status apply_config(gt_plan p, const gt_config &c) {
   return st;
 }
 
+}  // namespace
+
+namespace gt {
 thread_local const char *g_last_cuda = "no error";
 
 gt_status from_cuda(cudaError_t e) {
@@ -246,8 +260,10 @@ gt_status from_cuda(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) return GT_ERR_NO_MEMORY;
   return GT_ERR_CUDA;
 }
+}  // namespace gt
 
-}  // namespace
+using gt::from_cuda;
+using gt::g_last_cuda;
 
 extern "C" {
 
@@ -669,12 +685,26 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
   // inputs: on in_stream, once the last transposition that read set k is past its inputs
   cudaStream_t in = plan->in_stream;
   if ((e = cudaStreamWaitEvent(in, plan->ev_inputs_read[k], 0)) != cudaSuccess) return from_cuda(e);
+  gt_plan_s::HostEvents *hev = nullptr;
+  if (plan->timing && plan->host_events.size() < kMaxHostEvents) {
+    gt_plan_s::HostEvents h{};
+    if (cudaEventCreate(&h.in0) != cudaSuccess || cudaEventCreate(&h.in1) != cudaSuccess ||
+        cudaEventCreate(&h.out0) != cudaSuccess || cudaEventCreate(&h.out1) != cudaSuccess) {
+      for (cudaEvent_t x : {h.in0, h.in1, h.out0, h.out1})
+        if (x) cudaEventDestroy(x);
+      return from_cuda(cudaGetLastError());
+    }
+    plan->host_events.push_back(h);
+    hev = &plan->host_events.back();
+    if ((e = cudaEventRecord(hev->in0, in)) != cudaSuccess) return from_cuda(e);
+  }
   if ((e = cudaMemcpyAsync(plan->h_row_ptr[k], row_ptr, (nr + 1) * 8, cudaMemcpyHostToDevice, in)) != cudaSuccess)
     return from_cuda(e);
   if (m && (e = cudaMemcpyAsync(plan->h_col_idx[k], col_idx, m * 4, cudaMemcpyHostToDevice, in)) != cudaSuccess)
     return from_cuda(e);
   if (vals && m && (e = cudaMemcpyAsync(plan->h_vals[k], vals, m * 4, cudaMemcpyHostToDevice, in)) != cudaSuccess)
     return from_cuda(e);
+  if (hev && (e = cudaEventRecord(hev->in1, in)) != cudaSuccess) return from_cuda(e);
   if ((e = cudaEventRecord(plan->ev_inputs_in, in)) != cudaSuccess) return from_cuda(e);
   // the transposition: after its inputs arrived and output set k's last copy-out
   if ((e = cudaStreamWaitEvent(s, plan->ev_inputs_in, 0)) != cudaSuccess) return from_cuda(e);
@@ -688,6 +718,7 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
   cudaStream_t c = plan->copy_stream;
   if ((e = cudaEventRecord(plan->ev_computed, s)) != cudaSuccess) return from_cuda(e);
   if ((e = cudaStreamWaitEvent(c, plan->ev_computed, 0)) != cudaSuccess) return from_cuda(e);
+  if (hev && (e = cudaEventRecord(hev->out0, c)) != cudaSuccess) return from_cuda(e);
   if ((e = cudaMemcpyAsync(col_ptr, plan->h_col_ptr[k], (n + 1) * 8, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
     return from_cuda(e);
   if (m && (e = cudaMemcpyAsync(row_idx, plan->h_row_idx[k], m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
@@ -695,7 +726,47 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
   if (vals && m &&
       (e = cudaMemcpyAsync(vals_out, plan->h_vals_out[k], m * 4, cudaMemcpyDeviceToHost, c)) != cudaSuccess)
     return from_cuda(e);
+  if (hev && (e = cudaEventRecord(hev->out1, c)) != cudaSuccess) return from_cuda(e);
   if ((e = cudaEventRecord(plan->ev_copied[k], c)) != cudaSuccess) return from_cuda(e);
+  return GT_OK;
+}
+
+gt_status gt_plan_host_timing(gt_plan plan, gt_host_timing *t) {
+  if (!plan || !t) return GT_ERR_INVALID_ARG;
+  memset(t, 0, sizeof(*t));
+  const size_t c = plan->host_events.size();
+  if (c == 0) return GT_OK;
+  cudaError_t e;
+  for (const auto &h : plan->host_events)
+    if ((e = cudaEventSynchronize(h.out1)) != cudaSuccess) return from_cuda(e);
+  // intervals relative to the first call's input start
+  std::vector<double> a(c), b(c), d0(c), d1(c);
+  cudaEvent_t base = plan->host_events[0].in0;
+  for (size_t i = 0; i < c; ++i) {
+    const auto &h = plan->host_events[i];
+    float x[4];
+    cudaEvent_t ev[4] = {h.in0, h.in1, h.out0, h.out1};
+    for (int j = 0; j < 4; ++j)
+      if ((e = cudaEventElapsedTime(&x[j], base, ev[j])) != cudaSuccess) return from_cuda(e);
+    a[i] = x[0], b[i] = x[1], d0[i] = x[2], d1[i] = x[3];
+  }
+  // each direction's copies run one call after another on their own stream,
+  // so the overlap is the sum of the pairwise interval intersections
+  double h2d = 0, d2h = 0, ov = 0, end = 0;
+  for (size_t i = 0; i < c; ++i) {
+    h2d += b[i] - a[i];
+    d2h += d1[i] - d0[i];
+    if (d1[i] > end) end = d1[i];
+    for (size_t j = 0; j < c; ++j) {
+      const double lo = a[i] > d0[j] ? a[i] : d0[j], hi = b[i] < d1[j] ? b[i] : d1[j];
+      if (hi > lo) ov += hi - lo;
+    }
+  }
+  t->calls = (uint32_t)c;
+  t->h2d_ms = (float)(h2d / (double)c);
+  t->d2h_ms = (float)(d2h / (double)c);
+  t->overlap_ms = (float)(ov / (double)c);
+  t->span_ms = (float)end;
   return GT_OK;
 }
 

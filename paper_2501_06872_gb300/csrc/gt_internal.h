@@ -148,6 +148,10 @@ uint32_t smem_count_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged,
 uint32_t smem_scatter_bytes(uint32_t W, uint32_t kmax, uint32_t tlog2, int staged, uint32_t stage_edges,
                             int has_vals);
 
+// Maps a CUDA error to a gt_status and records its text for
+// gt_last_cuda_error() (cudaSuccess -> GT_OK).
+gt_status from_cuda(cudaError_t e);
+
 // Raises the dynamic shared-memory limits of the kernels, once per device
 // (the current device must be `device`; thread-safe).
 cudaError_t configure_kernels(int device);

@@ -17,9 +17,13 @@
 // undefined results.  The call runs the pure-atomic configuration (no HDV
 // table), synchronises `stream` and returns the device status.
 //
-// Set-up: the first call made on a device (with that device current) looks up
-// the array's device address and sets the kernels' shared-memory limits; make
-// that first call before any stream capture on the device.
+// Set-up: every call looks up the array's device address on the current
+// device (cudaGetSymbolAddress, a host-side lookup that allocates nothing),
+// so a new context after cudaDeviceReset, whose module image may sit at
+// another address, is never handed a stale pointer.  The first call in each
+// CUDA context also sets the kernels' shared-memory limits (kept per context
+// by its unique ID); make that first call before any stream capture on the
+// device.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -42,12 +46,50 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of g_noalloc_scratch per device ordinal, filled on the first
-// call made with that device current.
-std::atomic<void *> g_scratch_ptr[kMaxDevices];
-std::atomic<int> g_configured[kMaxDevices];
+// Unique ID of the CUDA context in which the kernels' limits were last set,
+// per device ordinal (0 = never).
+std::atomic<unsigned long long> g_configured_ctx[kMaxDevices];
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Unique ID of the current context through the driver's cuCtxGetCurrent and
+// cuCtxGetId (looked up once, without linking the driver library); 0 when
+// either is unavailable, which makes every call set the limits again.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::atomic<int> looked_up{0};
+  if (!looked_up.load()) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = (CtxGetCurrentFn)f1;
+      get_id = (CtxGetIdFn)f2;
+    }
+    cudaGetLastError();
+    looked_up.store(1);
+  }
+  if (!get_current || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Enqueued work may still use the shared array: wait for it before an error
+// return, so that the caller's next call cannot overlap it unknowingly.
+gt_status fail_after_enqueue(cudaStream_t s, cudaError_t e) {
+  gt_status st = gt::from_cuda(e);
+  cudaGetLastError();
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  return st;
+}
 
 }  // namespace
 
@@ -60,37 +102,41 @@ extern "C" gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges,
   if (n_vertices == 0 && n_edges != 0) return GT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    gt_status st = ce != cudaSuccess ? gt::from_cuda(ce) : GT_ERR_UNSUPPORTED;
     cudaGetLastError();
-    return GT_ERR_CUDA;
+    return st;
   }
-  // once per device: the device address of the static array, and the
-  // kernels' shared-memory limits
-  void *base = g_scratch_ptr[dev].load();
-  if (!base) {
-    void *ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return GT_ERR_CUDA;
-    }
-    g_scratch_ptr[dev].store(ptr);
-    base = ptr;
+  // the device address of the static array in the current context
+  void *base = nullptr;
+  if ((ce = cudaGetSymbolAddress(&base, g_noalloc_scratch)) != cudaSuccess || !base) {
+    gt_status st = gt::from_cuda(ce != cudaSuccess ? ce : cudaErrorInvalidSymbol);
+    cudaGetLastError();
+    return st;
   }
-  if (!g_configured[dev].load()) {
-    if (gt::configure_steps() != cudaSuccess || gt::configure_sort() != cudaSuccess) {
+  // the kernels' shared-memory limits, once per context
+  const unsigned long long ctx = current_context_id();
+  if (ctx == 0 || g_configured_ctx[dev].load() != ctx) {
+    if ((ce = gt::configure_steps()) != cudaSuccess || (ce = gt::configure_sort()) != cudaSuccess) {
+      gt_status st = gt::from_cuda(ce);
       cudaGetLastError();
-      return GT_ERR_CUDA;
+      return st;
     }
-    g_configured[dev].store(1);
+    g_configured_ctx[dev].store(ctx);
   }
   if (n_vertices == 0) {
-    if (cudaMemsetAsync(col_ptr, 0, 8, s) != cudaSuccess) return GT_ERR_CUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? GT_OK : GT_ERR_CUDA;
+    if ((ce = cudaMemsetAsync(col_ptr, 0, 8, s)) != cudaSuccess) return fail_after_enqueue(s, ce);
+    return gt::from_cuda(cudaStreamSynchronize(s));
   }
 
   // launch shape: 256-thread CTAs, 4 per SM, partitions of >= 4096 edges per warp
   int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GT_ERR_CUDA;
+  if ((ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+    gt_status st = gt::from_cuda(ce);
+    cudaGetLastError();
+    return st;
+  }
   gt_config cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.block_threads = 256;
@@ -156,12 +202,15 @@ extern "C" gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges,
 
   gt::Problem pb{row_ptr, col_idx, vals, col_ptr, row_idx, vals_out};
   uint32_t launches = 0;
-  if (gt::run_transpose(w, cfg, pb, s, nullptr, &launches) != cudaSuccess) {
-    cudaGetLastError();
-    return GT_ERR_CUDA;
-  }
-  if (cudaStreamSynchronize(s) != cudaSuccess) return GT_ERR_CUDA;
+  if ((ce = gt::run_transpose(w, cfg, pb, s, nullptr, &launches)) != cudaSuccess) return fail_after_enqueue(s, ce);
+  // the device status word, read on the same stream: one host wait
   uint32_t st = 0;
-  if (cudaMemcpy(&st, w.status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GT_ERR_CUDA;
+  if ((ce = cudaMemcpyAsync(&st, w.status, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail_after_enqueue(s, ce);
+  if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+    gt_status e = gt::from_cuda(ce);
+    cudaGetLastError();
+    return e;
+  }
   return (gt_status)st;
 }
