@@ -233,58 +233,116 @@ def radix_down_bytes_per_edge(weighted, passes):
     return (first + later * (passes - 1)) / passes
 
 
-def cpu_baseline_sample(rp_h, ci_h, vv_h, target_edges, n_cols=None):
-    """Rows [0, R) of the workload, R chosen so the prefix holds about target_edges."""
-    import oracle
+def dominant_kernel(cfg, n_cols, m, weighted):
+    """(name, own algorithmic bytes per launch) of the kernel that dominates a call."""
+    if cfg.method == 1:
+        # the bulk-staged downsweep runs when radix_tile is 0 and every array is 16-byte aligned (torch's are)
+        name = "k_radix_down_bulk" if cfg.radix_tile == 0 else "k_radix_down"
+        passes = radix_passes(n_cols)
+        return name, int(radix_down_bytes_per_edge(weighted, passes) * m + 8 * (n_cols + 1) / passes)
+    return "k_scatter", stage_bytes(n_cols, m, weighted)["scatter"]
+
+
+def roofline(cfg, timing, n, n_cols, m, weighted, peak, peak_kind, workload):
+    """Roofline of the dominant kernel on the METHOD's algorithmic bytes: the
+    metric formula's bytes per call (2 x col_idx read + row_ptr read + row_idx
+    (+ vals_out) write + col_ptr write; a second figure adds the vals read)
+    over the time the dominant kernel's launches take per call (its average
+    CUDA-event launch duration x launches per call).  kernel_own: the same
+    kernel on the bytes it moves itself per launch.  traffic: ncu DRAM bytes
+    per launch (committed summary, only while the kernel's sources are
+    unchanged)."""
+    name, own_bytes = dominant_kernel(cfg, n_cols, m, weighted)
+    lit, withv = algorithmic_bytes(n, m, weighted, n_cols)
+    dom_ms = timing["dominant_ms"]
+    per_call = timing["dominant_launches"] / max(1, timing["calls"])
+    call_ms = dom_ms * per_call
+    ach = lit / (call_ms * 1e-3) / 1e9
+    own = own_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = load_traffic(name, workload)
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": traffic, "kernel": name, "launch_ms": dom_ms, "launches_per_call": per_call,
+            "launches_timed": timing["dominant_launches"], "peak_kind": peak_kind,
+            "algorithmic_bytes_per_call": lit, "algorithmic_bytes_per_call_with_vals_read": withv,
+            "frac_with_vals_read": withv / (call_ms * 1e-3) / 1e9 / peak,
+            "kernel_own": {"bytes_per_launch": own_bytes, "achieved": own, "frac": own / peak},
+            "dram_over_algorithmic": (traffic * per_call / lit) if traffic else None}
+
+
+def sample_rows(rp_h, ci_h_fn, vv_h_fn, target_edges, windows=16):
+    """A bounded, representative sample of a workload for the host-side oracle:
+    `windows` runs of consecutive rows starting at evenly spaced rows
+    (k * n / windows), each holding about target_edges / windows edges; every
+    other row is left empty.  ci_h_fn(a, b) / vv_h_fn(a, b) return the host
+    copies of col_idx / vals over [a, b).  Returns (row_ptr, col_idx, vals,
+    edges, rows, description); the sample keeps all n rows and all columns."""
     n = rp_h.size - 1
-    R = int(np.searchsorted(rp_h, np.uint64(target_edges), side="left"))
-    R = max(1, min(R, n))
-    mS = int(rp_h[R])
-    rp_s = rp_h.copy()
-    rp_s[R:] = mS
-    t0 = time.perf_counter()
-    oracle.transpose(rp_s, ci_h[:mS], None if vv_h is None else vv_h[:mS], n_cols=n_cols)
-    dt = time.perf_counter() - t0
-    return mS, R, dt
+    per = max(1, target_edges // windows)
+    spans, rows = [], 0
+    for k in range(windows):
+        r0 = (k * n) // windows
+        r1 = int(np.searchsorted(rp_h, rp_h[r0] + np.uint64(per), side="left"))
+        r1 = max(r0 + 1, min(r1, ((k + 1) * n) // windows, n))
+        spans.append((r0, r1))
+        rows += r1 - r0
+    deg = np.zeros(n, dtype=np.uint64)
+    cis, vvs = [], []
+    for r0, r1 in spans:
+        deg[r0:r1] = rp_h[r0 + 1:r1 + 1] - rp_h[r0:r1]
+        a, b = int(rp_h[r0]), int(rp_h[r1])
+        cis.append(ci_h_fn(a, b))
+        if vv_h_fn is not None:
+            vvs.append(vv_h_fn(a, b))
+    rp_s = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(deg, out=rp_s[1:])
+    ci_s = np.ascontiguousarray(np.concatenate(cis), dtype=np.uint32)
+    vv_s = None if vv_h_fn is None else np.ascontiguousarray(np.concatenate(vvs), dtype=np.float32)
+    mS = int(rp_s[-1])
+    desc = (f"{windows} runs of consecutive rows at evenly spaced starts (k*n/{windows}): {rows} rows, "
+            f"{mS} edges, all {n} rows and columns in the arrays")
+    return rp_s, ci_s, vv_s, mS, rows, desc
+
+
+def host_cores():
+    return os.cpu_count() or 1
 
 
 def run_reference(args, rank, world):
-    """The oracle (single-threaded C, host cores) on bounded samples of the same workload."""
+    """The oracle (single-threaded C, host cores) on bounded samples of the same
+    workload.  Only the oracle and the input generator are built and loaded in
+    this process; the CUDA library is not."""
     if rank != 0:
         return
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
+    import oracle
+    from paper_2501_06872_gb300 import build as pkg_build
+    pkg_build.build_generators()
+    oracle.build()
     kind, scale, ef, order, weighted = WORKLOADS[args.workload]
     torch.cuda.set_device(0)
     n, n_cols, rp, ci, vv = make_workload(args.workload, SEED, args.direction)
     m_full = ci.numel()
-    target = min(args.ref_sample_edges, ci.numel())
-    R = int(torch.searchsorted(rp, torch.tensor([target], device=rp.device)).item())
-    R = max(1, min(R, n))
-    mS = int(rp[R].item())
-    rp_h = rp.cpu().numpy().view(np.uint64).copy()
-    rp_h[R:] = mS
-    ci_h = ci[:mS].cpu().numpy().view(np.uint32)
-    vv_h = None if vv is None else vv[:mS].cpu().numpy()
-    del rp, ci, vv
+    rp_h = rp.cpu().numpy().view(np.uint64)
+    rp_s, ci_s, vv_s, mS, rows, desc = sample_rows(
+        rp_h, lambda a, b: ci[a:b].cpu().numpy().view(np.uint32),
+        None if vv is None else (lambda a, b: vv[a:b].cpu().numpy()), min(args.ref_sample_edges, m_full))
+    del rp, ci, vv, rp_h
     torch.cuda.empty_cache()
-    import oracle
     for _ in range(args.warmup):
-        oracle.transpose(rp_h, ci_h, vv_h, n_cols=n_cols)
+        oracle.transpose(rp_s, ci_s, vv_s, n_cols=n_cols)
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.transpose(rp_h, ci_h, vv_h, n_cols=n_cols)
+        oracle.transpose(rp_s, ci_s, vv_s, n_cols=n_cols)
         ts.append(time.perf_counter() - t0)
     total = sum(ts)
     value = mS * args.steps / total
-    sample = f"rows [0,{R}) of the workload ({mS} edges, all {n} rows, {n_cols} columns)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": workload_config(args.workload, n, m_full, weighted, n_cols, args.direction),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": host_cores(),
+                             "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -320,37 +378,39 @@ def workload_config(name, n, m, weighted, n_cols=None, direction="csr"):
     return c
 
 
-def run_batched(args):
-    """Config 4: 4096 uneven matrices transposed by one batch plan (CUDA-graph
-    replay) vs one plain gt_transpose_sub launch sequence per matrix."""
+def batched_leg(n_graphs, steps, warmup, pg_reps, config_json=None):
+    """Config 4: uneven matrices transposed by one batch plan (CUDA-graph
+    replay) vs one plain gt_transpose_sub launch sequence per matrix (the
+    library's default configuration for each size), with the outputs compared
+    element by element.  Returns a dict; frees its device memory."""
     import torch
     from paper_2501_06872_gb300 import binding
     from paper_2501_06872_gb300.inputs import gpu as ggen
-    b = ggen.batch(n_graphs=args.batch_graphs, seed=0x5EED0004)
+    b = ggen.batch(n_graphs=n_graphs, seed=0x5EED0004)
     m_tot, v_tot, ng = b["total_m"], b["total_v"], b["n_graphs"]
     cp = torch.empty(v_tot + ng, dtype=torch.int64, device="cuda")
     ri = torch.empty(m_tot, dtype=torch.int32, device="cuda")
     vo = torch.empty(m_tot, dtype=torch.float32, device="cuda")
     s = torch.cuda.Stream()
     cfg = None
-    if args.config:
+    if config_json:
         cfg = binding.default_config(1 << 20, 1 << 24)
-        for k, v in json.loads(args.config).items():
+        for k, v in json.loads(config_json).items():
             setattr(cfg, k, int(v))
     plan = binding.BatchPlan(ggen.batch_graphs(b, cp, ri, vo), True, cfg)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.transpose(s)
     plan.check()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     with Clocks(0) as clk:
         ev0.record(s)
-        for _ in range(args.steps):
+        for _ in range(steps):
             plan.transpose(s)
         ev1.record(s)
         torch.cuda.synchronize()
     plan.check()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     info = plan.info()
     plan.close()
     # per-graph baseline: the library's default configuration per matrix size
@@ -375,32 +435,86 @@ def run_batched(args):
     per_graph()
     torch.cuda.synchronize()
     e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(1, min(args.steps, 2))
     e0_.record(s)
-    for _ in range(reps):
+    for _ in range(pg_reps):
         per_graph()
     e1_.record(s)
     torch.cuda.synchronize()
-    ms_pg = e0_.elapsed_time(e1_) / reps
+    ms_pg = e0_.elapsed_time(e1_) / pg_reps
     for p_ in plans.values():
         p_.check()
         p_.close()
     same = bool(torch.equal(cp, cp2) and torch.equal(ri, ri2) and torch.equal(vo.view(torch.int32), vo2.view(torch.int32)))
-    peak, peak_kind = load_peaks()
     lit = sum(algorithmic_bytes(int(b["n"][g]), int(b["m"][g]), True)[0] for g in range(ng))
-    gbs = lit / (ms * 1e-3) / 1e9
-    line = {"metric": METRIC, "value": m_tot / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    del cp, ri, vo, cp2, ri2, vo2, b, rp, ci, vv
+    torch.cuda.empty_cache()
+    return {"value": m_tot / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "graphs": ng, "n_edges": m_tot, "n_vertices": v_tot, "algorithmic_bytes": lit,
+            "per_graph_baseline": {"value": m_tot / (ms_pg * 1e-3), "unit": UNIT, "ms_per_step": ms_pg,
+                                   "reps": pg_reps, "speedup_batched": ms_pg / ms, "identical_output": same},
+            "batch_info": info, "clocks": clk.summary(), "gpu_launches": info["kernel_launches"] * steps}
+
+
+def run_batched(args):
+    """--workload batched: the batch leg as its own JSON line."""
+    peak, peak_kind = load_peaks()
+    r = batched_leg(args.batch_graphs, args.steps, args.warmup, max(1, min(args.steps, 2)), args.config)
+    gbs = r["algorithmic_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "batched-4096-zipf", "graphs": ng, "n_edges": m_tot, "n_vertices": v_tot,
+            "config": {"workload": "batched-4096-zipf", "graphs": r["graphs"], "n_edges": r["n_edges"],
+                       "n_vertices": r["n_vertices"],
                        "sizes": "n log-uniform [1024, 262144], Zipf(2) out-degree mean U[8,32], Zipf(1.5) dst",
                        "l2": "inputs larger than L2 (no flush needed)"},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "traffic": None, "kernel": "whole batch (CUDA graph replay)", "peak_kind": peak_kind},
-            "per_graph_baseline": {"value": m_tot / (ms_pg * 1e-3), "unit": UNIT, "ms_per_step": ms_pg,
-                                   "speedup_batched": ms_pg / ms, "identical_output": same},
-            "batch_info": info, "clocks": clk.summary(), "gpu_launches": info["kernel_launches"] * args.steps}
+            "per_graph_baseline": r["per_graph_baseline"], "batch_info": r["batch_info"], "clocks": r["clocks"],
+            "gpu_launches": r["gpu_launches"]}
     print(json.dumps(line), flush=True)
+
+
+def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1):
+    """PoTra's own method (Algorithm 2, k = 512 HDVs, with the LDV list sort)
+    on the same resident graph: per-step device time, per-step stage times,
+    and whether its output equals the default method's bytes."""
+    import torch
+    from paper_2501_06872_gb300 import binding
+    cfg = binding.default_config(n_cols, m)
+    cfg.method, cfg.hdv_k, cfg.table_log2 = 0, 512, 10
+    plan = binding.Plan(n, m, weighted, cfg, n_cols=n_cols)
+    cp = torch.empty(n_cols + 1, dtype=torch.int64, device="cuda")
+    ri = torch.empty(m, dtype=torch.int32, device="cuda")
+    vo = torch.empty(m, dtype=torch.float32, device="cuda") if weighted else None
+    stream = torch.cuda.current_stream()
+    try:
+        for _ in range(warmup):
+            plan.transpose(rp, ci, vv, cp, ri, vo)
+        plan.check()
+        plan.enable_timing(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            plan.transpose(rp, ci, vv, cp, ri, vo)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms = ev0.elapsed_time(ev1) / steps
+        t = plan.timing()
+        st = plan.stats()
+    finally:
+        plan.close()
+    same = bool(torch.equal(cp, ref_out[0]) and torch.equal(ri, ref_out[1]) and
+                (vo is None or torch.equal(vo.view(torch.int32), ref_out[2].view(torch.int32))))
+    del cp, ri, vo
+    torch.cuda.empty_cache()
+    return {"method": "hlh", "value": m / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "gt_config": cfg.as_dict(),
+            "stage_ms": {k: t[k] for k in ("sample_ms", "count_ms", "scan_ms", "scatter_ms", "sort_ms")},
+            "scatter_launch_ms": t["dominant_ms"], "hdv_selected": st["hdv_selected"],
+            "coverage": st["hdv_edges"] / max(1, m), "identical_output": same,
+            "gpu_launches": int(st["kernel_launches"]) * steps}
 
 
 def main():
@@ -416,6 +530,8 @@ def main():
     ap.add_argument("--config", default=None, help="JSON gt_config overrides")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hlh", action="store_true", help="skip the PoTra-method leg of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched leg of the default line")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 26)
     ap.add_argument("--ref-sample-edges", type=int, default=1 << 24)
     ap.add_argument("--record-traffic", nargs=3, metavar=("CSV", "KERNEL", "NOTE"), default=None,
@@ -496,22 +612,8 @@ def main():
     method = plan.config().method
     stage_ms = {"count": timing["count_ms"], "scan": timing["scan_ms"], "scatter": timing["scatter_ms"],
                 "sort": timing["sort_ms"], "sample": timing["sample_ms"]}
-    if method == 1:
-        # the bulk-staged downsweep runs when radix_tile is 0 and every array is 16-byte aligned (torch's are)
-        kname = "k_radix_down_bulk" if plan.config().radix_tile == 0 else "k_radix_down"
-        passes = radix_passes(n_cols)
-        per_edge = radix_down_bytes_per_edge(weighted, passes)
-        dom_bytes = int(per_edge * m + 8 * (n_cols + 1) / passes)
-    else:
-        kname = "k_scatter"
-        dom_bytes = stage_bytes(n, m, weighted)["scatter"]  # graphs only (HLH is not the default above 4 M edges)
-    dom_ms = timing["dominant_ms"]
-    ach = dom_bytes / (dom_ms * 1e-3) / 1e9
     lit, withv = algorithmic_bytes(n, m, weighted, n_cols)
-    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": load_traffic(kname, args.workload), "kernel": kname,
-            "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": dom_ms,
-            "launches_timed": timing["dominant_launches"], "peak_kind": peak_kind}
+    roof = roofline(plan.config(), timing, n, n_cols, m, weighted, peak, peak_kind, args.workload)
     step_gbs = lit / (ms_step * 1e-3) / 1e9
 
     learned = None
@@ -520,28 +622,47 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
         rp_h = rp.cpu().numpy().view(np.uint64)
-        target = min(args.cpu_sample_edges, m)
-        R = int(np.searchsorted(rp_h, np.uint64(target), side="left"))
-        mS = int(rp_h[max(1, min(R, n))])
-        ci_h = ci[:mS].cpu().numpy().view(np.uint32)
-        vv_h = None if vv is None else vv[:mS].cpu().numpy()
-        mS, R, dt = cpu_baseline_sample(rp_h, ci_h, vv_h, target, n_cols)
-        cpu = {"value": mS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"rows [0,{R}) of the workload: {mS} edges, all {n} rows, {n_cols} columns, {dt:.1f} s"}
+        rp_s, ci_s, vv_s, mS, rows, desc = sample_rows(
+            rp_h, lambda a, b: ci[a:b].cpu().numpy().view(np.uint32),
+            None if vv is None else (lambda a, b: vv[a:b].cpu().numpy()), min(args.cpu_sample_edges, m))
+        del rp_h
+        t0 = time.perf_counter()
+        oracle.transpose(rp_s, ci_s, vv_s, n_cols=n_cols)
+        dt = time.perf_counter() - t0
+        del rp_s, ci_s, vv_s
+        cpu = {"value": mS / dt, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
+               "sample": f"{desc}; {dt:.1f} s"}
+
+    hlh = None
+    if not args.no_hlh and rank == 0 and world == 1 and method == 1:
+        hlh = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo))
 
     e2e = None
     if not args.no_e2e and rank == 0:
         host = host_inputs(rp, ci, vv, n, m, weighted, n_cols)
         del rp, ci, vv, cp, ri, vo  # the end-to-end leg works from host memory only
         e2e = run_e2e(plan, host, n, m, weighted, args, n_cols)
+        del host
+    gt_config = plan.config().as_dict()
+    plan.close()
+    try:
+        del rp, ci, vv, cp, ri, vo
+    except NameError:
+        pass
+    torch.cuda.empty_cache()
+
+    batched = None
+    if not args.no_batched and rank == 0 and world == 1:
+        batched = batched_leg(args.batch_graphs, 2, 3, 1)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": dict(workload_config(args.workload, n, m, weighted, n_cols, args.direction),
-                               gt_config=plan.config().as_dict()),
+                               gt_config=gt_config),
                 "roofline": roof,
                 "step_hbm": {"gbs_formula": step_gbs, "frac_of_peak": step_gbs / peak,
                              "frac_of_8tbs": step_gbs / 8000.0, "bytes_formula": lit, "bytes_with_vals_read": withv,
@@ -550,9 +671,8 @@ def main():
                 "coverage": stats["hdv_edges"] / max(1, m),
                 "clocks": clk.summary(),
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps,
-                "learned": learned, "e2e": e2e, "cpu_baseline": cpu}
+                "learned": learned, "e2e": e2e, "cpu_baseline": cpu, "hlh": hlh, "batched": batched}
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -660,15 +780,25 @@ def run_e2e(plan, host, n, m, weighted, args, n_cols=None):
     torch.cuda.synchronize()
     # every step copies its inputs in and its CSC out; gt_transpose_host_async
     # overlaps a step's output copies with the next step's input copies
+    plan.enable_timing(True)  # events around each call's copies (and steps)
     t0 = time.perf_counter()
     for _ in range(steps):
         plan.transpose_host_async(h_rp, h_ci, h_vv, h_cp, h_ri, h_vo)
     plan.host_wait()
     dt = (time.perf_counter() - t0) / steps
+    ht = plan.host_timing()
+    ct = plan.timing()
+    plan.enable_timing(False)
     h2d = 8 * (n + 1) + 4 * m + (4 * m if weighted else 0)
     d2h = 8 * (nc + 1) + 4 * m + (4 * m if weighted else 0)
+    copies = {"h2d_gbs": h2d / (ht["h2d_ms"] * 1e-3) / 1e9 if ht["h2d_ms"] else None,
+              "d2h_gbs": d2h / (ht["d2h_ms"] * 1e-3) / 1e9 if ht["d2h_ms"] else None,
+              "h2d_ms": ht["h2d_ms"], "d2h_ms": ht["d2h_ms"], "overlap_ms": ht["overlap_ms"],
+              "overlap_share": ht["overlap_ms"] / min(ht["h2d_ms"], ht["d2h_ms"]) if ht["calls"] else None,
+              "directions_overlapped": bool(ht["calls"] and ht["overlap_ms"] > 0.25 * min(ht["h2d_ms"], ht["d2h_ms"])),
+              "transpose_ms": ct["total_ms"] or None, "calls_timed": ht["calls"]}
     return {"value": m / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": dt * 1e3, "steps": steps}
+            "ms_per_step": dt * 1e3, "steps": steps, "copies": copies}
 
 
 if __name__ == "__main__":

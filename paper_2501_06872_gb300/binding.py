@@ -65,6 +65,14 @@ class Timing(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class HostTiming(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_uint32), ("h2d_ms", ctypes.c_float), ("d2h_ms", ctypes.c_float),
+                ("overlap_ms", ctypes.c_float), ("span_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class GraphDesc(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_uint32), ("n_cols", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
@@ -96,7 +104,7 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_selector_forward", "gt_selector_backward", "gt_selector_adam_step", "gt_selector_destroy",
            "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges", "gt_selector_in_range", "gt_transpose_host_async",
            "gt_plan_host_wait", "gt_plan_create_rect", "gt_transpose_sub_rect", "gt_plan_shape",
-           "gt_graph_features_rect"]
+           "gt_graph_features_rect", "gt_plan_host_timing"]
 
 N_FEATURES = 41
 TUNE_GRID = 12
@@ -128,6 +136,8 @@ def load():
     lib.gt_transpose_host_async.restype = ctypes.c_int
     lib.gt_plan_host_wait.argtypes = [P]
     lib.gt_plan_host_wait.restype = ctypes.c_int
+    lib.gt_plan_host_timing.argtypes = [P, ctypes.POINTER(HostTiming)]
+    lib.gt_plan_host_timing.restype = ctypes.c_int
     lib.gt_transpose_sub.argtypes = [P, u32, u64, P, P, P, P, P, P, P]
     lib.gt_transpose_sub.restype = ctypes.c_int
     lib.gt_transpose_sub_rect.argtypes = [P, u32, u32, u64, P, P, P, P, P, P, P]
@@ -282,6 +292,11 @@ class Plan:
         rc = self._lib.gt_transpose_host_async(self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
                                                _ptr(row_idx), _ptr(vals_out), _stream(stream))
         _check(rc, "gt_transpose_host_async")
+
+    def host_timing(self) -> dict:
+        t = HostTiming()
+        _check(self._lib.gt_plan_host_timing(self._h, ctypes.byref(t)), "gt_plan_host_timing")
+        return t.as_dict()
 
     def host_wait(self):
         _check(self._lib.gt_plan_host_wait(self._h), "gt_plan_host_wait")

@@ -67,6 +67,14 @@ def build_lib(name: str, sources, headers, extra=()) -> str:
     return out
 
 
+def build_generators() -> str:
+    """libgtgen.so alone (the seeded input generators), without the CUDA
+    library of the method."""
+    gen_dir = os.path.join(PKG, "inputs")
+    return build_lib("gtgen", sorted(glob.glob(os.path.join(gen_dir, "*.cu"))),
+                     glob.glob(os.path.join(gen_dir, "*.h")))
+
+
 def build(force: bool = False) -> dict:
     if force and os.path.isdir(BUILD):
         shutil.rmtree(BUILD)

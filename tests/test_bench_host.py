@@ -4,6 +4,7 @@ workload table (rectangular folds, CSC direction)."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
@@ -64,3 +65,44 @@ def test_workload_table():
     assert c["n_rows"] == 1 << 28 and c["n_cols"] == 1 << 20 and "2^8" in c["fold"]
     c = bench.workload_config("rmat25-random", 1 << 25, 1 << 29, False, 1 << 25, "csc")
     assert c["direction"] == "CSC input -> CSR" and "n_cols" not in c
+
+
+def test_sample_rows_keeps_whole_rows_at_spread_starts():
+    import bench
+    rng = np.random.default_rng(3)
+    n = 1000
+    deg = rng.integers(0, 20, n).astype(np.uint64)
+    rp = np.zeros(n + 1, np.uint64)
+    np.cumsum(deg, out=rp[1:])
+    m = int(rp[-1])
+    ci = rng.integers(0, n, m).astype(np.uint32)
+    vv = rng.random(m).astype(np.float32)
+    rp_s, ci_s, vv_s, mS, rows, desc = bench.sample_rows(rp, lambda a, b: ci[a:b], lambda a, b: vv[a:b], 400,
+                                                         windows=4)
+    assert rp_s.size == n + 1 and rp_s[0] == 0 and int(rp_s[-1]) == mS == ci_s.size == vv_s.size
+    kept = np.nonzero(np.diff(rp_s) > 0)[0]
+    # every kept row is whole and in place; the four runs start at k * n / 4
+    for u in kept:
+        a, b = int(rp_s[u]), int(rp_s[u + 1])
+        assert np.array_equal(ci_s[a:b], ci[int(rp[u]):int(rp[u + 1])])
+        assert np.array_equal(vv_s[a:b], vv[int(rp[u]):int(rp[u + 1])])
+    starts = [k * n // 4 for k in range(4)]
+    assert all(np.diff(rp_s)[s] == rp[s + 1] - rp[s] for s in starts)
+    assert 300 <= mS <= 400 + 4 * 20
+
+
+def test_roofline_uses_the_method_bytes_per_call():
+    import bench
+    from types import SimpleNamespace
+    cfg = SimpleNamespace(method=1, radix_tile=0)
+    n, m = 1 << 10, 1 << 14
+    timing = {"dominant_ms": 2.0, "dominant_launches": 8, "calls": 2}
+    r = bench.roofline(cfg, timing, n, n, m, True, 1000.0, "measured", "no-such-workload")
+    lit, withv = bench.algorithmic_bytes(n, m, True)
+    assert r["launches_per_call"] == 4
+    assert r["achieved"] == pytest.approx(lit / 8e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
+    assert r["frac_with_vals_read"] == pytest.approx(withv / 8e-3 / 1e9 / 1000.0)
+    own = bench.radix_down_bytes_per_edge(True, bench.radix_passes(n)) * m + 8 * (n + 1) / bench.radix_passes(n)
+    assert r["kernel_own"]["bytes_per_launch"] == int(own)
+    assert r["traffic"] is None and r["dram_over_algorithmic"] is None
