@@ -86,6 +86,10 @@ typedef struct gt_config {
                                  else as 4096); 2048 or 4096 = register tiles of 256 threads,
                                  ctas_per_sm CTAs per SM */
     uint64_t seed;            /* seed of the sampling positions                            */
+    uint32_t batch_key_bits;  /* batch plans: widest union key (graph, column) in bits, 16..32;
+                                 0 = 28 (or 32 when the columns need more than 27 bits)       */
+    uint32_t batch_edges_log2;/* batch plans: log2 of the union edges of one sub-batch, 16..31;
+                                 0 = 31                                                          */
 } gt_config;
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
@@ -245,11 +249,18 @@ gt_status gt_transpose_noalloc(uint32_t n_vertices, uint64_t n_edges, const uint
                                uint32_t *row_idx, float *vals_out, void *stream);
 
 /* ---- Batches: many independent graphs in one launch sequence ------------
- * A batch plan transposes every graph of a fixed descriptor list with the
- * radix method over the union of the graphs (key = graph, destination),
- * split into sub-batches of at most ~2^31 edges; the whole kernel sequence
- * is captured once into a CUDA graph and replayed by gt_transpose_batched.
- * The output of every graph equals gt_transpose's. */
+ * (north-star addition "batching"; each graph's output is the transposition
+ * of Sec. II-A, equal to gt_transpose's.)  A batch plan is sized by limits;
+ * every gt_transpose_batched call passes its own DEVICE descriptor array,
+ * graph count and DEVICE per-graph status array.  Kernels read them at run
+ * time: a layout kernel checks every descriptor, lays the graphs out one after
+ * another in a union edge / column space, and splits them into sub-batches
+ * (runs of graphs with at most 2^batch_edges_log2 edges, 2^31 columns and
+ * 2^(key bits - column bits) graphs); each sub-batch is transposed by the
+ * radix method over the union key (local graph, column).  The kernel sequence
+ * is captured once into a CUDA graph per stream and replayed by later calls,
+ * so batches of any shape within the limits reuse one plan.  The output of
+ * every graph equals gt_transpose's. */
 typedef struct gt_graph_desc {
     uint32_t n_vertices;      /* rows (the vertices of a graph), >= 1                */
     uint32_t n_cols;          /* columns of a rectangular matrix; 0 = n_vertices    */
@@ -262,33 +273,74 @@ typedef struct gt_graph_desc {
     float *vals_out;          /* device, n_edges, NULL iff vals is NULL */
 } gt_graph_desc;
 
+/* The largest batch one call of a plan may pass. */
+typedef struct gt_batch_limits {
+    uint32_t max_graphs;      /* descriptors per call, >= 1                          */
+    uint32_t max_cols;        /* columns (n_cols, else n_vertices) of any graph, >= 1 */
+    uint64_t max_graph_edges; /* edges of any one graph                              */
+    uint64_t max_edges;       /* edges of all graphs of a call together              */
+    uint64_t max_cols_total;  /* columns of all graphs of a call together            */
+} gt_batch_limits;
+
 typedef struct gt_batch_info {
-    uint32_t n_graphs;
-    uint32_t sub_batches;
-    uint32_t passes_max;      /* digit passes of the widest sub-batch          */
-    uint32_t kernel_launches; /* kernels in one batch transposition            */
-    uint64_t n_edges;         /* total edges                                  */
+    uint32_t n_graphs;        /* graphs of the last call                      */
+    uint32_t sub_batches;     /* sub-batches the last call used               */
+    uint32_t passes_max;      /* digit passes of every sub-batch              */
+    uint32_t kernel_launches; /* kernels in one batch call (all slots)        */
+    uint64_t n_edges;         /* edges of the last call's transposed graphs   */
     uint64_t workspace_bytes;
+    uint32_t slots;           /* sub-batch slots of the captured sequence     */
+    uint32_t key_bits;        /* union key width                              */
+    uint64_t sub_batch_edges; /* edges one sub-batch may hold                 */
 } gt_batch_info;
 
 typedef struct gt_batch_plan_s *gt_batch_plan;
 
-/* descs: HOST array of n_graphs descriptors (copied; the pointers inside are
- * used by every later gt_transpose_batched).  Graphs may be empty; every
- * graph needs n_vertices >= 1.  cfg: method must be GT_METHOD_RADIX (or cfg
- * NULL); the digit passes always use the bulk-copy staged downsweep; flags
- * bit GT_FLAG_NO_GRAPH runs the kernels directly instead of through a CUDA
- * graph. */
-gt_status gt_batch_plan_create(gt_batch_plan *plan, uint32_t n_graphs, const gt_graph_desc *descs, int has_vals,
+/* Limits that fit exactly the given HOST descriptor list. */
+gt_status gt_batch_limits_from_descs(uint32_t n_graphs, const gt_graph_desc *descs, gt_batch_limits *limits);
+
+/* Creates a plan for batches within `limits` (workspace allocated here).
+ * has_vals: every graph carries values (or none does).  cfg: NULL or
+ * method GT_METHOD_RADIX with radix_tile 0 (the bulk-staged digit passes);
+ * batch_key_bits / batch_edges_log2 shape the sub-batches; flags bit
+ * GT_FLAG_NO_GRAPH launches the kernels directly instead of replaying a CUDA
+ * graph.  Fails with GT_ERR_UNSUPPORTED when the limits need more than 4096
+ * sub-batch slots or a graph larger than a sub-batch. */
+gt_status gt_batch_plan_create(gt_batch_plan *plan, const gt_batch_limits *limits, int has_vals,
                                const gt_config *cfg, void *stream);
 
-/* Enqueues the transposition of every graph of the plan on `stream`
- * (captures the CUDA graph on the first call: make it before any outside
- * capture of that stream).  Device errors: gt_batch_plan_status. */
-gt_status gt_transpose_batched(gt_batch_plan plan, void *stream);
+/* Replaces the configuration (reallocates the workspace; synchronous). */
+gt_status gt_batch_plan_set_config(gt_batch_plan plan, const gt_config *cfg);
+gt_status gt_batch_plan_get_config(gt_batch_plan plan, gt_config *cfg);
 
+/* Enqueues the transposition of graphs d_descs[0 .. n_graphs) on `stream`.
+ * d_descs: DEVICE array of descriptors (read by the kernels when they run);
+ * d_status: DEVICE array of n_graphs gt_status codes (32-bit), or NULL: each
+ * gets GT_OK, or the first error of that graph -- GT_ERR_INVALID_ARG (n_vertices
+ * 0, a null array, values present or absent against the plan),
+ * GT_ERR_UNSUPPORTED (beyond the plan's limits), GT_ERR_BAD_ROW_PTR,
+ * GT_ERR_OUT_OF_RANGE.  Graphs with an error are skipped (their outputs are
+ * unspecified); the others are transposed.  The first call on a stream
+ * captures the CUDA graph: make it before any outside capture of that stream.
+ * Host errors: n_graphs above the limit -> GT_ERR_UNSUPPORTED.  Any device
+ * error is also latched in the plan's status word (gt_batch_plan_status). */
+gt_status gt_transpose_batched(gt_batch_plan plan, uint32_t n_graphs, const gt_graph_desc *d_descs,
+                               gt_status *d_status, void *stream);
+
+/* Synchronises the last stream; returns the first device error of the last call. */
 gt_status gt_batch_plan_status(gt_batch_plan plan);
+/* Synchronises the last stream; shape of the plan and of its last call. */
 gt_status gt_batch_plan_info(gt_batch_plan plan, gt_batch_info *info);
+
+/* Batch autotuner: times the batch configurations of gt_batch_tune_grid_config
+ * on this batch (1 warm-up + reps calls each, median of CUDA-event times) and
+ * installs the fastest.  The batch's outputs then hold its transposition.
+ * table: optional host array of GT_BATCH_TUNE_GRID entries (ms = -1 where a
+ * point could not run); chosen: optional grid index.  Synchronous. */
+#define GT_BATCH_TUNE_GRID 6
+gt_status gt_batch_tune_grid_config(uint32_t index, gt_config *cfg);
+gt_status gt_batch_plan_tune(gt_batch_plan plan, uint32_t n_graphs, const gt_graph_desc *d_descs,
+                             gt_status *d_status, uint32_t reps, float *table_ms, uint32_t *chosen, void *stream);
 void gt_batch_plan_destroy(gt_batch_plan plan);
 
 /* ---- Configuration search: features, grid, analytic model, autotuner, -----

@@ -32,7 +32,8 @@ class Config(ctypes.Structure):
                 ("warp_edges", ctypes.c_uint32), ("stage_edges", ctypes.c_uint32),
                 ("sample_permille", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("method", ctypes.c_uint32), ("radix_tile", ctypes.c_uint32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("batch_key_bits", ctypes.c_uint32),
+                ("batch_edges_log2", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,7 +87,17 @@ class TuneEntry(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_uint32), ("sub_batches", ctypes.c_uint32), ("passes_max", ctypes.c_uint32),
                 ("kernel_launches", ctypes.c_uint32), ("n_edges", ctypes.c_uint64),
-                ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32), ("key_bits", ctypes.c_uint32),
+                ("sub_batch_edges", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchLimits(ctypes.Structure):
+    _fields_ = [("max_graphs", ctypes.c_uint32), ("max_cols", ctypes.c_uint32),
+                ("max_graph_edges", ctypes.c_uint64), ("max_edges", ctypes.c_uint64),
+                ("max_cols_total", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -104,12 +115,15 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_selector_forward", "gt_selector_backward", "gt_selector_adam_step", "gt_selector_destroy",
            "gt_plan_tune", "gt_plan_vertices", "gt_plan_edges", "gt_selector_in_range", "gt_transpose_host_async",
            "gt_plan_host_wait", "gt_plan_create_rect", "gt_transpose_sub_rect", "gt_plan_shape",
-           "gt_graph_features_rect", "gt_plan_host_timing"]
+           "gt_graph_features_rect", "gt_plan_host_timing",
+           "gt_batch_limits_from_descs", "gt_batch_plan_set_config", "gt_batch_plan_get_config",
+           "gt_batch_tune_grid_config", "gt_batch_plan_tune"]
 
 N_FEATURES = 41
 TUNE_GRID = 12
 SEL_HIDDEN = 64
 TUNE_ANALYTIC, TUNE_EXHAUSTIVE, TUNE_LEARNED = 0, 1, 2
+BATCH_TUNE_GRID = 6
 
 
 def load():
@@ -146,9 +160,17 @@ def load():
     lib.gt_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.gt_transpose_noalloc.argtypes = [u32, u64, P, P, P, P, P, P, P]
     lib.gt_transpose_noalloc.restype = ctypes.c_int
-    lib.gt_batch_plan_create.argtypes = [ctypes.POINTER(P), u32, ctypes.POINTER(GraphDesc), ctypes.c_int,
+    lib.gt_batch_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(BatchLimits), ctypes.c_int,
                                          ctypes.POINTER(Config), P]
-    lib.gt_transpose_batched.argtypes = [P, P]
+    lib.gt_transpose_batched.argtypes = [P, u32, P, P, P]
+    lib.gt_batch_limits_from_descs.argtypes = [u32, ctypes.POINTER(GraphDesc), ctypes.POINTER(BatchLimits)]
+    lib.gt_batch_plan_set_config.argtypes = [P, ctypes.POINTER(Config)]
+    lib.gt_batch_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
+    lib.gt_batch_tune_grid_config.argtypes = [u32, ctypes.POINTER(Config)]
+    lib.gt_batch_plan_tune.argtypes = [P, u32, P, P, u32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(u32), P]
+    for f in ["gt_batch_limits_from_descs", "gt_batch_plan_set_config", "gt_batch_plan_get_config",
+              "gt_batch_tune_grid_config", "gt_batch_plan_tune"]:
+        getattr(lib, f).restype = ctypes.c_int
     lib.gt_batch_plan_status.argtypes = [P]
     lib.gt_batch_plan_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
     lib.gt_batch_plan_destroy.argtypes = [P]
@@ -348,16 +370,21 @@ class Plan:
 
 
 class BatchPlan:
-    """Owns a gt_batch_plan over a fixed list of graphs (device pointers).
+    """Owns a gt_batch_plan and the device descriptor / status arrays of a
+    graph list.
 
     graphs: sequence of dicts with n, m, row_ptr, col_idx, vals, col_ptr,
     row_idx, vals_out (torch tensors or raw device addresses) and, for an
-    n x n_cols matrix, n_cols."""
+    n x n_cols matrix, n_cols.  limits (dict of gt_batch_limits fields, or
+    None = the limits of `graphs`) sizes the plan; transpose() runs the
+    plan's own graph list, transpose_descs() any device descriptor array."""
 
-    def __init__(self, graphs, weighted: bool, config: Config | dict | None = None, stream=None):
+    def __init__(self, graphs, weighted: bool, config: Config | dict | None = None, stream=None, limits=None):
+        import torch
         lib = load()
         self._lib = lib
-        arr = (GraphDesc * len(graphs))()
+        self._h = None
+        arr = (GraphDesc * max(1, len(graphs)))()
 
         def addr(x):
             if x is None:
@@ -366,16 +393,41 @@ class BatchPlan:
         for i, g in enumerate(graphs):
             arr[i] = GraphDesc(int(g["n"]), int(g.get("n_cols", 0)), int(g["m"]), addr(g["row_ptr"]), addr(g["col_idx"]),
                                addr(g.get("vals")), addr(g["col_ptr"]), addr(g["row_idx"]), addr(g.get("vals_out")))
+        lim = BatchLimits()
+        if limits is None:
+            _check(lib.gt_batch_limits_from_descs(len(graphs), arr, ctypes.byref(lim)), "gt_batch_limits_from_descs")
+        else:
+            for k, v in limits.items():
+                setattr(lim, k, int(v))
         if isinstance(config, dict):
             config = Config.from_dict(config)
         h = ctypes.c_void_p()
         cfgp = ctypes.byref(config) if config is not None else None
-        _check(lib.gt_batch_plan_create(ctypes.byref(h), len(graphs), arr, int(weighted), cfgp, None),
+        _check(lib.gt_batch_plan_create(ctypes.byref(h), ctypes.byref(lim), int(weighted), cfgp, None),
                "gt_batch_plan_create")
         self._h = h
+        self.n_graphs = len(graphs)
+        raw = bytes(arr)[:ctypes.sizeof(GraphDesc) * len(graphs)] or bytes(16)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.d_descs = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+        self.d_status = torch.zeros(max(1, len(graphs)), dtype=torch.int32, device=dev)
 
     def transpose(self, stream=None):
-        _check(self._lib.gt_transpose_batched(self._h, _stream(stream)), "gt_transpose_batched")
+        self.transpose_descs(self.n_graphs, self.d_descs, self.d_status, stream)
+
+    def transpose_descs(self, n_graphs, d_descs, d_status=None, stream=None):
+        """gt_transpose_batched on a device descriptor array (tensor or
+        address) and an optional device int32 status array."""
+        dp = d_descs if isinstance(d_descs, int) else d_descs.data_ptr()
+        sp = None if d_status is None else (d_status if isinstance(d_status, int) else d_status.data_ptr())
+        _check(self._lib.gt_transpose_batched(self._h, int(n_graphs), dp, sp, _stream(stream)),
+               "gt_transpose_batched")
+
+    def graph_status(self):
+        """Per-graph status codes of the last transpose() (synchronises)."""
+        import torch
+        torch.cuda.synchronize()
+        return self.d_status[:self.n_graphs].cpu().tolist()
 
     def status(self) -> int:
         return self._lib.gt_batch_plan_status(self._h)
@@ -388,6 +440,25 @@ class BatchPlan:
         _check(self._lib.gt_batch_plan_info(self._h, ctypes.byref(b)), "gt_batch_plan_info")
         return b.as_dict()
 
+    def config(self) -> Config:
+        c = Config()
+        _check(self._lib.gt_batch_plan_get_config(self._h, ctypes.byref(c)), "gt_batch_plan_get_config")
+        return c
+
+    def set_config(self, config: Config | dict):
+        if isinstance(config, dict):
+            config = Config.from_dict(config)
+        _check(self._lib.gt_batch_plan_set_config(self._h, ctypes.byref(config)), "gt_batch_plan_set_config")
+
+    def tune(self, reps=3, stream=None):
+        """gt_batch_plan_tune on the plan's graph list: (chosen index, ms per grid point)."""
+        table = (ctypes.c_float * BATCH_TUNE_GRID)()
+        chosen = ctypes.c_uint32()
+        _check(self._lib.gt_batch_plan_tune(self._h, self.n_graphs, self.d_descs.data_ptr(), self.d_status.data_ptr(),
+                                            int(reps), table, ctypes.byref(chosen), _stream(stream)),
+               "gt_batch_plan_tune")
+        return int(chosen.value), [float(x) for x in table]
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gt_batch_plan_destroy(self._h)
@@ -398,6 +469,12 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def batch_grid_config(index: int) -> Config:
+    c = Config()
+    _check(load().gt_batch_tune_grid_config(int(index), ctypes.byref(c)), "gt_batch_tune_grid_config")
+    return c
 
 
 def grid_config(index: int, n: int, m: int) -> Config:

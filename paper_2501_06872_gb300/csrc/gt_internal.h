@@ -107,34 +107,68 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches,
                       StepEvents *events);
 
-// One sub-batch of a batch plan (device pointers; sizes on the host).
-struct SubBatch {
-  uint32_t g0 = 0, ng = 0;                // graphs [g0, g0 + ng) of the plan
-  uint64_t m = 0;                         // union edges
-  uint32_t nv = 0;                        // union vertices
-  uint32_t vbits = 1, passes = 1, dbits = 1;
-  uint64_t windows = 0;                   // 32-row windows over all graphs
-  const gt_graph_desc *descs = nullptr;   // device, ng entries
-  unsigned long long *eoff = nullptr, *voff = nullptr, *woff = nullptr;  // device, ng + 1 each
+// The arguments of one batch call, in device memory (written by a small
+// kernel before the captured sequence, which reads them).
+struct BatchCall {
+  const gt_graph_desc *descs;  // device, n_graphs entries
+  int32_t *status;             // device, n_graphs per-graph gt_status codes, or null
+  uint32_t n_graphs;
+};
+
+// A batch plan's limits and sub-batch rule, passed to the layout kernel.
+struct BatchLimitsDev {
+  uint32_t max_graphs, max_cols;
+  uint64_t max_graph_edges, max_edges, max_cols_total;
+  uint64_t cap_e, cap_v;  // sub-batch slot = eoff / cap_e + voff / cap_v + g / cap_g
+  uint32_t cap_g, slots;
+  int has_vals;
+};
+
+// One sub-batch of a call: graphs [g0, g0 + ng), laid out by k_b_layout.
+struct BatchSlot {
+  const gt_graph_desc *descs;                    // the call's descriptors + g0
+  int32_t *gstatus;                              // the call's status array + g0, or null
+  const uint32_t *gx;                            // excluded graphs (nonzero) + g0
+  const unsigned long long *eoff, *voff, *woff;  // the call's prefix sums + g0 (entries g0 .. g0 + ng)
+  unsigned long long e0, v0, w0;                 // eoff[g0], voff[g0], woff[g0]
+  unsigned long long m, nv, windows;             // union edges, columns, 32-row windows
+  uint32_t g0, ng;
+};
+
+struct BatchTotals {
+  uint64_t n_edges;
+  uint32_t n_graphs, slots_used;
 };
 
 struct BatchWork {
   int has_vals = 0;
   int num_sms = 0;
-  uint32_t rG = 0, r_items = 16;
-  uint32_t *a_key = nullptr, *a_u = nullptr, *a_w = nullptr;  // [max m]
-  uint32_t *b_key = nullptr, *b_u = nullptr, *b_w = nullptr;  // [max m]
-  unsigned long long *ucp = nullptr;                            // [max nv + 1]
-  uint32_t *table = nullptr;                                    // [rG][256]
-  unsigned long long *offsets = nullptr;                        // [rG][256]
+  uint32_t vbits = 1, passes = 1, dbits = 1;
+  uint64_t cap_edges = 0;                                       // union edges one sub-batch may hold
+  BatchLimitsDev lim{};
+  uint32_t *a_key = nullptr, *a_u = nullptr, *a_w = nullptr;  // [cap_edges]
+  uint32_t *b_key = nullptr, *b_u = nullptr, *b_w = nullptr;  // [cap_edges]
+  unsigned long long *ucp = nullptr;                            // [columns of one sub-batch + 1]
+  uint32_t *table = nullptr;                                    // [rows][256]
+  unsigned long long *offsets = nullptr;                        // [rows][256]
   uint32_t *long_g = nullptr, *long_r = nullptr, *n_long = nullptr;
   uint32_t long_cap = 0;
   unsigned long long *gaps = nullptr;  // [1 + 2 * gap_cap] long col_ptr ranges
   uint32_t gap_cap = 0;
-  uint32_t *status = nullptr, *meta = nullptr;
+  uint32_t *status = nullptr;
+  BatchCall *call = nullptr;
+  unsigned long long *eoff = nullptr, *voff = nullptr, *woff = nullptr;  // [max_graphs + 1]
+  uint32_t *gx = nullptr;                                                 // [max_graphs]
+  BatchSlot *slots = nullptr;                                             // [lim.slots]
+  BatchTotals *totals = nullptr;
 };
 
-cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_t s, uint32_t *launches);
+// Stores a call's arguments for the captured sequence; lays the call out.
+cudaError_t launch_batch_call(BatchCall *call, const gt_graph_desc *descs, int32_t *status, uint32_t n_graphs,
+                              cudaStream_t s);
+cudaError_t launch_batch_layout(const BatchWork &bw, cudaStream_t s);
+// The kernels of one sub-batch slot (sizes read on the device).
+cudaError_t run_radix_batch(const BatchWork &bw, uint32_t slot, cudaStream_t s, uint32_t *launches);
 
 // Exclusive look-back scan (Step 2) as a separate launch; row_ptr may be null
 // (no row-pointer validation); cursor may be null.

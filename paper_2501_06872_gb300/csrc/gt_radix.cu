@@ -47,14 +47,14 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t dbits, bool
   return mm;
 }
 
-// Batch view: graphs g0 .. g0+ng-1 of the descriptor array, laid out one after
-// another in a union edge space (eoff) and vertex space (voff); a union key is
-// (local graph << vbits) | vertex.
+// Batch view: the sub-batch (graphs g0 .. g0+ng-1 of a call) whose layout
+// k_b_layout wrote on the device for this call.  Its graphs lie one after
+// another in a union edge space, column space and row-window space; a union
+// key is (local graph << vbits) | column.  slot == nullptr: a single graph
+// (the sizes are the kernel arguments).
 struct BatchView {
-  const gt_graph_desc *descs;         // descriptors of this sub-batch (device)
-  const unsigned long long *eoff;     // [ng + 1]
-  const unsigned long long *voff;     // [ng + 1]
-  uint32_t ng, vbits;
+  const BatchSlot *slot;
+  uint32_t vbits;
 };
 
 __device__ __forceinline__ uint32_t upper_graph(const unsigned long long *off, uint32_t ng, uint64_t x) {
@@ -65,6 +65,13 @@ __device__ __forceinline__ uint32_t upper_graph(const unsigned long long *off, u
     else hi = mid;
   }
   return lo;
+}
+
+// The graph's status word of the call (if the caller passed one) and the
+// batch's status word both receive the first error.
+__device__ __forceinline__ void graph_error(const BatchSlot &sl, uint32_t g, uint32_t *status, gt_status code) {
+  if (sl.gstatus) atomicCAS((unsigned int *)(sl.gstatus + g), 0u, (unsigned int)code);
+  set_status(status, code);
 }
 
 struct RadixArgs {
@@ -87,6 +94,18 @@ struct RadixArgs {
   uint32_t sub = 1;  // upsweep CTAs per downsweep CTA (table rows = G * sub)
   uint32_t *g_key = nullptr, *g_w = nullptr;  // batch first upsweep: gathered union keys / values
 };
+
+// Sizes of a pass: the kernel arguments, or for a sub-batch the union edge
+// count of this call (tiles of `tile` edges over `ctas` persistent CTAs).
+struct PassSizes {
+  uint64_t m, ntiles;
+  uint32_t tpc;
+};
+__device__ __forceinline__ PassSizes pass_sizes(const RadixArgs &a, uint32_t ctas) {
+  if (!a.batch.slot) return PassSizes{a.m, a.ntiles, a.tiles_per_cta};
+  const uint64_t m = a.batch.slot->m, nt = (m + a.tile - 1) / a.tile;
+  return PassSizes{m, nt, (uint32_t)((nt + ctas - 1) / ctas)};
+}
 
 // Pass modes: plain arrays; a batch's first upsweep, which reads through the
 // descriptors (and gathers the union keys); a batch's last downsweep, which
@@ -166,8 +185,9 @@ __global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
   __syncthreads();
   const uint32_t mask = (1u << a.dbits) - 1u;
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-  const uint64_t t0 = (uint64_t)(blockIdx.x / a.sub) * a.tiles_per_cta;
-  uint64_t e0 = min64(t0 * a.tile, a.m), e1 = min64((t0 + a.tiles_per_cta) * a.tile, a.m);
+  const PassSizes ps = pass_sizes(a, gridDim.x / a.sub);
+  const uint64_t t0 = (uint64_t)(blockIdx.x / a.sub) * ps.tpc;
+  uint64_t e0 = min64(t0 * a.tile, ps.m), e1 = min64((t0 + ps.tpc) * a.tile, ps.m);
   if (a.sub > 1) {  // this CTA counts part (blockIdx.x % sub) of the downsweep CTA's range
     const uint64_t part = (e1 - e0 + a.sub - 1) / a.sub, s0 = e0 + (blockIdx.x % a.sub) * part;
     e1 = min64(s0 + part, e1);
@@ -179,17 +199,23 @@ __global__ void __launch_bounds__(kRThreads) k_radix_up(RadixArgs a) {
   for (uint64_t c = e0 + (uint64_t)w * 32 * U; c < e1; c += (uint64_t)kRWarps * 32 * U) {
     uint32_t key[U];
     if (loads_batch(MODE)) {
-      uint32_t g = upper_graph(a.batch.eoff, a.batch.ng, c < e1 ? c : e1 - 1);
+      const BatchSlot &sl = *a.batch.slot;
+      // union edge e of the sub-batch is edge sl.e0 + e of the call
+      uint32_t g = upper_graph(sl.eoff, sl.ng, sl.e0 + (c < e1 ? c : e1 - 1));
 #pragma unroll
       for (int i = 0; i < U; ++i) {
         const uint64_t e = c + (uint64_t)i * 32 + lane;
         key[i] = 0xFFFFFFFFu;
         if (e < e1) {
-          while (e >= a.batch.eoff[g + 1]) ++g;
-          const gt_graph_desc &d = a.batch.descs[g];
-          const uint64_t le = e - a.batch.eoff[g];
-          const uint32_t v = __ldcs(d.col_idx + le);
-          if (v >= desc_cols(d)) bad = 1;
+          while (sl.e0 + e >= sl.eoff[g + 1]) ++g;
+          const gt_graph_desc &d = sl.descs[g];
+          const uint64_t le = sl.e0 + e - sl.eoff[g];
+          uint32_t v = __ldcs(d.col_idx + le);
+          if (v >= desc_cols(d)) {  // reported; kept inside the graph's own key range
+            bad = 1;
+            graph_error(sl, g, a.status, GT_ERR_OUT_OF_RANGE);
+            v = desc_cols(d) - 1u;
+          }
           key[i] = (g << a.batch.vbits) | (v & ((1u << a.batch.vbits) - 1u));
           if (a.g_key) {  // gather the union key (and value) for a plain first pass
             a.g_key[e] = key[i];
@@ -429,8 +455,9 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
   __shared__ uint32_t s_abort;
   const uint32_t tid = threadIdx.x, w = tid >> 5, lane = tid & 31u;
   const uint32_t mask = (1u << a.dbits) - 1u;
-  const uint64_t t0 = (uint64_t)blockIdx.x * a.tiles_per_cta;
-  const uint64_t t1 = min64(t0 + a.tiles_per_cta, a.ntiles);
+  const PassSizes ps = pass_sizes(a, gridDim.x);
+  const uint64_t t0 = (uint64_t)blockIdx.x * ps.tpc;
+  const uint64_t t1 = min64(t0 + ps.tpc, ps.ntiles);
   if (t0 >= t1) return;
   run_off[tid] = a.offsets[(size_t)blockIdx.x * a.sub * kRBins + tid];  // kBThreads == kRBins
   if (tid == 0) {
@@ -440,7 +467,7 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
     fence_barrier_init();
   }
   __syncthreads();
-  auto full = [&](uint64_t t) { return (t + 1) * kBTile <= a.m; };
+  auto full = [&](uint64_t t) { return (t + 1) * kBTile <= ps.m; };
   auto issue = [&](uint64_t t, uint32_t b) {  // one thread
     uint32_t *dst = dsm + b * NA * kBTile;
     const uint64_t e = t * kBTile;
@@ -459,7 +486,7 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
     const uint32_t b = (uint32_t)((t - t0) & 1u);
     uint32_t *bk = dsm + b * NA * kBTile, *bu = bk + kBTile, *bw = bk + 2 * kBTile;
     const uint64_t tbase = t * kBTile;
-    const uint32_t tcount = (uint32_t)min64(kBTile, a.m - tbase);
+    const uint32_t tcount = (uint32_t)min64(kBTile, ps.m - tbase);
     const uint32_t wpar = (par >> b) & 1u;  // parity of this tile's copy
     if (tcount == kBTile) {
       if (!mbar_wait(&bar[b], wpar)) s_abort = 1;
@@ -569,9 +596,10 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       }
       a.out_key[pos] = k;
       if (stores_batch(MODE)) {  // the last pass of a batch stores through the graph's descriptor
+        const BatchSlot &sl = *a.batch.slot;
         const uint32_t g = k >> a.batch.vbits;
-        const gt_graph_desc &gd = a.batch.descs[g];
-        const uint64_t lp = pos - a.batch.eoff[g];
+        const gt_graph_desc &gd = sl.descs[g];
+        const uint64_t lp = sl.e0 + pos - sl.eoff[g];
         gd.row_idx[lp] = u;
         if (VALS) gd.vals_out[lp] = __uint_as_float(wv);
       } else {
@@ -634,10 +662,11 @@ __device__ __forceinline__ void colptr_range(uint64_t a, uint64_t b, uint64_t va
 template <bool BATCH>
 __device__ __forceinline__ uint32_t cp_index(uint32_t k, uint32_t n, const BatchView &bv) {
   if (!BATCH) return min(k, n);
+  const BatchSlot &sl = *bv.slot;
   const uint32_t g = k >> bv.vbits;
-  if (g >= bv.ng) return n;
+  if (g >= sl.ng) return n;
   const uint32_t v = k & ((1u << bv.vbits) - 1u);
-  return (uint32_t)(bv.voff[g] + min(v, desc_cols(bv.descs[g])));
+  return (uint32_t)(sl.voff[g] - sl.v0 + min(v, desc_cols(sl.descs[g])));
 }
 
 template <bool BATCH>
@@ -647,6 +676,10 @@ __global__ void __launch_bounds__(256) k_radix_colptr(const uint32_t *__restrict
   __shared__ uint32_t sk[8][kCpChunk];
   const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
   uint32_t *ck = sk[w];
+  if (BATCH) {  // this call's sub-batch: its union edges and columns
+    m = bv.slot->m;
+    n = (uint32_t)bv.slot->nv;
+  }
   const uint64_t nwarps = (uint64_t)gridDim.x * 8;
   for (uint64_t c = ((uint64_t)blockIdx.x * 8 + w) * kCpChunk; c < m; c += nwarps * kCpChunk) {
     const uint32_t cnt = (uint32_t)min64(kCpChunk, m - c);
@@ -826,33 +859,175 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
 // Batches (sub-batch of graphs laid out in union edge / vertex spaces)
 // ---------------------------------------------------------------------------
 
+// ---- layout of one batch call (device-side, read by every later kernel) ----
+
+// The call's arguments, stored where the captured kernels read them.
+__global__ void k_b_set_call(BatchCall *call, const gt_graph_desc *descs, int32_t *status, uint32_t n_graphs) {
+  call->descs = descs;
+  call->status = status;
+  call->n_graphs = n_graphs;
+}
+
+// One CTA of kLayoutThreads threads.  Per graph: the descriptor's checks
+// (an excluded graph gets its status code and no edges, columns or rows),
+// then exclusive prefix sums of the edges, columns and 32-row windows over
+// the graphs in order, the exclusion of every graph from the first one whose
+// prefix end passes a limit of the plan, and the sub-batch of every graph:
+// slot(g) = floor(eoff[g] / cap_e) + floor(voff[g] / cap_v) + floor(g / cap_g),
+// non-decreasing in g, so each sub-batch is a run of graphs with at most
+// cap_e + max graph edges edges, cap_v + max columns columns and cap_g graphs.
+constexpr uint32_t kLayoutThreads = 1024;
+
+__global__ void __launch_bounds__(kLayoutThreads) k_b_layout(const BatchCall *__restrict__ call, BatchLimitsDev lim,
+                                                             unsigned long long *eoff, unsigned long long *voff,
+                                                             unsigned long long *woff, uint32_t *gx, BatchSlot *slots,
+                                                             BatchTotals *totals, uint32_t *status) {
+  __shared__ unsigned long long s_e[kLayoutThreads], s_v[kLayoutThreads], s_w[kLayoutThreads];
+  __shared__ uint32_t s_cut;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t n = min(call->n_graphs, lim.max_graphs);
+  const gt_graph_desc *descs = call->descs;
+  int32_t *gst = call->status;
+  if (tid == 0) s_cut = n;
+  const uint32_t per = (n + kLayoutThreads - 1) / kLayoutThreads;
+  const uint32_t g0 = min(tid * per, n), g1 = min(g0 + per, n);
+  // checks and chunk sums
+  unsigned long long se = 0, sv = 0, sw = 0;
+  for (uint32_t g = g0; g < g1; ++g) {
+    const gt_graph_desc d = descs[g];
+    gt_status code = GT_OK;
+    const uint32_t cols = desc_cols(d);
+    if (d.n_vertices == 0 || !d.row_ptr || !d.col_ptr || (d.n_edges > 0 && (!d.col_idx || !d.row_idx)))
+      code = GT_ERR_INVALID_ARG;
+    else if (lim.has_vals && d.n_edges > 0 && (!d.vals || !d.vals_out))
+      code = GT_ERR_INVALID_ARG;
+    else if (!lim.has_vals && (d.vals || d.vals_out))
+      code = GT_ERR_INVALID_ARG;
+    else if (cols > lim.max_cols || d.n_edges > lim.max_graph_edges)
+      code = GT_ERR_UNSUPPORTED;
+    if (gst) gst[g] = (int32_t)code;
+    gx[g] = code != GT_OK;
+    if (code != GT_OK) {
+      set_status(status, code);
+      continue;
+    }
+    se += d.n_edges;
+    sv += cols;
+    sw += (d.n_vertices + 31u) / 32u;
+  }
+  s_e[tid] = se, s_v[tid] = sv, s_w[tid] = sw;
+  __syncthreads();
+  for (uint32_t o = 1; o < kLayoutThreads; o <<= 1) {  // inclusive scans over the chunks
+    unsigned long long ye = 0, yv = 0, yw = 0;
+    if (tid >= o) ye = s_e[tid - o], yv = s_v[tid - o], yw = s_w[tid - o];
+    __syncthreads();
+    s_e[tid] += ye, s_v[tid] += yv, s_w[tid] += yw;
+    __syncthreads();
+  }
+  unsigned long long re = tid ? s_e[tid - 1] : 0, rv = tid ? s_v[tid - 1] : 0, rw = tid ? s_w[tid - 1] : 0;
+  for (uint32_t g = g0; g < g1; ++g) {
+    eoff[g] = re, voff[g] = rv, woff[g] = rw;
+    if (!gx[g]) {
+      const gt_graph_desc &d = descs[g];
+      re += d.n_edges;
+      rv += desc_cols(d);
+      rw += (d.n_vertices + 31u) / 32u;
+      if (re > lim.max_edges || rv > lim.max_cols_total) atomicMin(&s_cut, g);
+    }
+  }
+  __syncthreads();
+  // graphs from the first one past a limit on are excluded (their prefix ends only grow)
+  const uint32_t cut = s_cut;
+  for (uint32_t g = max(g0, cut); g < g1; ++g) {
+    if (!gx[g]) {
+      if (gst) gst[g] = GT_ERR_UNSUPPORTED;
+      set_status(status, GT_ERR_UNSUPPORTED);
+    }
+    gx[g] = 1;
+    eoff[g] = eoff[cut], voff[g] = voff[cut], woff[g] = woff[cut];  // eoff[cut] is never rewritten
+  }
+  if (tid == kLayoutThreads - 1) {
+    const uint32_t last = n;
+    if (cut < n) {
+      eoff[last] = eoff[cut], voff[last] = voff[cut], woff[last] = woff[cut];
+    } else {
+      eoff[last] = s_e[tid], voff[last] = s_v[tid], woff[last] = s_w[tid];
+    }
+  }
+  __syncthreads();
+  // sub-batches: slot s holds graphs [first(s), first(s + 1)) with
+  // first(s) = the first graph whose slot is >= s (n if none)
+  auto slot_of = [&](uint32_t g) -> unsigned long long {
+    return eoff[g] / lim.cap_e + voff[g] / lim.cap_v + g / lim.cap_g;
+  };
+  auto first = [&](uint32_t sidx) -> uint32_t {
+    uint32_t lo = 0, hi = n;  // first g in [0, n) with slot_of(g) >= sidx, else n
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (slot_of(mid) >= sidx) hi = mid;
+      else lo = mid + 1;
+    }
+    return lo;
+  };
+  for (uint32_t sidx = tid; sidx < lim.slots; sidx += kLayoutThreads) {
+    const uint32_t a = first(sidx), b = first(sidx + 1);
+    BatchSlot sl;
+    sl.descs = descs + a;
+    sl.gstatus = gst ? gst + a : nullptr;
+    sl.gx = gx + a;
+    sl.eoff = eoff + a, sl.voff = voff + a, sl.woff = woff + a;
+    sl.e0 = eoff[a], sl.v0 = voff[a], sl.w0 = woff[a];
+    sl.m = eoff[b] - eoff[a], sl.nv = voff[b] - voff[a], sl.windows = woff[b] - woff[a];
+    sl.g0 = a, sl.ng = b - a;
+    slots[sidx] = sl;
+  }
+  // graphs past the last sub-batch (not reachable within the plan's limits)
+  const uint32_t tail = first(lim.slots);
+  for (uint32_t g = max(tail, g0); g < g1; ++g)
+    if (!gx[g]) {
+      gx[g] = 1;
+      if (gst) gst[g] = GT_ERR_UNSUPPORTED;
+      set_status(status, GT_ERR_UNSUPPORTED);
+    }
+  if (tid == 0) {
+    totals->n_graphs = n;
+    totals->n_edges = eoff[min(tail, n)];
+    uint32_t used = 0;
+    for (uint32_t sidx = 0; sidx < lim.slots; ++sidx) used += first(sidx + 1) > first(sidx);
+    totals->slots_used = used;
+  }
+}
+
 // Per graph: row_ptr[0] == 0 and row_ptr[n_rows] == m (n_vertices is the row count).
 __global__ void k_b_check(BatchView bv, uint32_t *status) {
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < bv.ng; g += gridDim.x * blockDim.x) {
-    const gt_graph_desc &d = bv.descs[g];
-    if (d.n_vertices == 0 || d.row_ptr[0] != 0 || d.row_ptr[d.n_vertices] != d.n_edges)
-      set_status(status, GT_ERR_BAD_ROW_PTR);
+  const BatchSlot &sl = *bv.slot;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < sl.ng; g += gridDim.x * blockDim.x) {
+    if (sl.gx[g]) continue;
+    const gt_graph_desc &d = sl.descs[g];
+    if (d.row_ptr[0] != 0 || d.row_ptr[d.n_vertices] != d.n_edges) graph_error(sl, g, status, GT_ERR_BAD_ROW_PTR);
   }
 }
 
 // Source rows of every union edge: windows of 32 rows of one graph per warp step.
-__global__ void k_b_expand(BatchView bv, const unsigned long long *__restrict__ woff, uint64_t windows, uint32_t *src,
-                           uint32_t *long_g, uint32_t *long_r, uint32_t *n_long, uint32_t long_cap, uint32_t *status) {
+__global__ void k_b_expand(BatchView bv, uint32_t *src, uint32_t *long_g, uint32_t *long_r, uint32_t *n_long,
+                           uint32_t long_cap, uint32_t *status) {
+  const BatchSlot &sl = *bv.slot;
+  const uint64_t windows = sl.windows;
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t wi = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); wi < windows; wi += warps) {
-    const uint32_t g = upper_graph(woff, bv.ng, wi);
-    const gt_graph_desc &d = bv.descs[g];
+    const uint32_t g = upper_graph(sl.woff, sl.ng, sl.w0 + wi);
+    const gt_graph_desc &d = sl.descs[g];
     const uint32_t n = d.n_vertices;  // rows
-    const uint64_t m = d.n_edges, base = bv.eoff[g];
-    const uint64_t r0 = (wi - woff[g]) * 32;
+    const uint64_t m = d.n_edges, base = sl.eoff[g] - sl.e0;
+    const uint64_t r0 = (sl.w0 + wi - sl.woff[g]) * 32;
     const uint64_t r = r0 + lane;
     uint64_t ri = r + 1;
     if (ri > n) ri = n;
     uint64_t rend = d.row_ptr[ri];
     uint64_t rbeg = r < n ? d.row_ptr[r] : rend;
     if (rend > m || rbeg > rend) {
-      set_status(status, GT_ERR_BAD_ROW_PTR);
+      graph_error(sl, g, status, GT_ERR_BAD_ROW_PTR);
       rend = rbeg = 0;
     }
     const bool is_long = r < n && rend - rbeg > kLongRow;
@@ -890,91 +1065,109 @@ __global__ void k_b_expand(BatchView bv, const unsigned long long *__restrict__ 
 
 __global__ void k_b_expand_long(BatchView bv, const uint32_t *__restrict__ long_g, const uint32_t *__restrict__ long_r,
                                 const uint32_t *__restrict__ n_long, uint32_t long_cap, uint32_t *src) {
+  const BatchSlot &sl = *bv.slot;
   const uint32_t cnt = min(*n_long, long_cap);
   for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const uint32_t g = long_g[i], r = long_r[i];
-    const gt_graph_desc &d = bv.descs[g];
-    const uint64_t b = d.row_ptr[r], e = d.row_ptr[r + 1], base = bv.eoff[g];
+    const gt_graph_desc &d = sl.descs[g];
+    const uint64_t b = d.row_ptr[r], e = d.row_ptr[r + 1], base = sl.eoff[g] - sl.e0;
     for (uint64_t p = b + threadIdx.x; p < e; p += blockDim.x) src[base + p] = r;
   }
 }
 
+// A sub-batch without edges: its union col_ptr is all zero.
+__global__ void k_b_zero_ucp(BatchView bv, unsigned long long *ucp) {
+  const BatchSlot &sl = *bv.slot;
+  if (sl.m != 0) return;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x <= sl.nv; x += (uint64_t)gridDim.x * blockDim.x)
+    ucp[x] = 0;
+}
+
 // col_ptr of every graph from the union col_ptr (and the last entry).
-__global__ void k_b_colptr(BatchView bv, const unsigned long long *__restrict__ ucp, uint64_t nv) {
-  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nv + bv.ng;
+__global__ void k_b_colptr(BatchView bv, const unsigned long long *__restrict__ ucp) {
+  const BatchSlot &sl = *bv.slot;
+  const uint64_t nv = sl.nv;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < nv + sl.ng;
        x += (uint64_t)gridDim.x * blockDim.x) {
     if (x < nv) {
-      const uint32_t g = upper_graph(bv.voff, bv.ng, x);
-      bv.descs[g].col_ptr[x - bv.voff[g]] = ucp[x] - bv.eoff[g];
+      const uint32_t g = upper_graph(sl.voff, sl.ng, sl.v0 + x);
+      sl.descs[g].col_ptr[sl.v0 + x - sl.voff[g]] = ucp[x] - (sl.eoff[g] - sl.e0);
     } else {
       const uint32_t g = (uint32_t)(x - nv);
-      const gt_graph_desc &d = bv.descs[g];
+      if (sl.gx[g]) continue;
+      const gt_graph_desc &d = sl.descs[g];
       d.col_ptr[desc_cols(d)] = d.n_edges;
     }
   }
 }
 
-cudaError_t run_radix_batch(const BatchWork &bw, const SubBatch &sb, cudaStream_t s, uint32_t *launches) {
+cudaError_t launch_batch_layout(const BatchWork &bw, cudaStream_t s) {
+  k_b_layout<<<1, kLayoutThreads, 0, s>>>(bw.call, bw.lim, bw.eoff, bw.voff, bw.woff, bw.gx, bw.slots, bw.totals,
+                                          bw.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_call(BatchCall *call, const gt_graph_desc *descs, int32_t *status, uint32_t n_graphs,
+                              cudaStream_t s) {
+  k_b_set_call<<<1, 1, 0, s>>>(call, descs, status, n_graphs);
+  return cudaGetLastError();
+}
+
+// The kernels of sub-batch `slot` (its sizes are read on the device).
+cudaError_t run_radix_batch(const BatchWork &bw, uint32_t slot, cudaStream_t s, uint32_t *launches) {
   uint32_t nl = 0;
   cudaError_t err;
-  BatchView bv{sb.descs, sb.eoff, sb.voff, sb.ng, sb.vbits};
+  BatchView bv{bw.slots + slot, bw.vbits};
   const bool vals = bw.has_vals != 0;
-  const uint64_t m = sb.m;
-  const uint32_t passes = sb.passes, dbits = sb.dbits;
-  if ((err = cudaMemsetAsync(bw.meta, 0, kMetaCount * 4, s)) != cudaSuccess) return err;
+  const uint64_t M = bw.cap_edges;  // sizes the grids; the kernels read this call's sizes
+  const uint32_t passes = bw.passes, dbits = bw.dbits;
   if ((err = cudaMemsetAsync(bw.n_long, 0, 4, s)) != cudaSuccess) return err;
-  k_b_check<<<(sb.ng + 255) / 256, 256, 0, s>>>(bv, bw.status);
+  const uint32_t gchk = (bw.lim.cap_g + 255) / 256;
+  k_b_check<<<gchk < 1024 ? gchk : 1024, 256, 0, s>>>(bv, bw.status);
   ++nl;
-  if (m > 0) {
-    const bool first_to_b = ((passes - 1) % 2) == 0;
-    uint32_t *src_rows = first_to_b ? bw.a_u : bw.b_u;
-    uint32_t g = (uint32_t)min64((sb.windows + 7) / 8, (uint64_t)bw.num_sms * 16);
-    if (g == 0) g = 1;
-    k_b_expand<<<g, 256, 0, s>>>(bv, sb.woff, sb.windows, src_rows, bw.long_g, bw.long_r, bw.n_long, bw.long_cap,
-                                 bw.status);
-    k_b_expand_long<<<bw.num_sms * 4, 256, 0, s>>>(bv, bw.long_g, bw.long_r, bw.n_long, bw.long_cap, src_rows);
-    nl += 2;
-    // The first upsweep reads through the descriptors and gathers the union
-    // keys and values into the buffers the first pass does not write; every
-    // pass then runs the bulk-staged downsweep on plain arrays, the last one
-    // storing through the descriptors.
-    const uint32_t Gb = (uint32_t)bw.num_sms * kBCtasPerSm, subb = 2;
-    const uint32_t ntb = (uint32_t)((m + kBTile - 1) / kBTile), tpcb = (ntb + Gb - 1) / Gb;
-    uint32_t *gk = first_to_b ? bw.a_key : bw.b_key, *gw = vals ? (first_to_b ? bw.a_w : bw.b_w) : nullptr;
-    const uint32_t *in_key = gk, *in_u = src_rows, *in_w = gw;
-    for (uint32_t p = 1; p <= passes; ++p) {
-      const bool toB = ((passes - p) % 2) == 0;
-      uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
-      RadixArgs ra{nullptr, nullptr, nullptr, 0, m, in_key, in_u, in_w, ok, ou, ow,
-                   (p - 1) * dbits, dbits, ntb, tpcb, kBTile, bw.table, bw.offsets, bw.status, bv, subb,
-                   p == 1 ? gk : nullptr, p == 1 ? gw : nullptr};
-      const uint32_t rows = Gb * subb;
-      if (p == 1) k_radix_up<true, kBatchFirst><<<rows, kRThreads, 0, s>>>(ra);
-      else k_radix_up<false, kPlain><<<rows, kRThreads, 0, s>>>(ra);
-      k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, rows, bw.offsets);
-      if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-      else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
-      else if (vals) k_radix_down_bulk<true, kPlain><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-      else k_radix_down_bulk<false, kPlain><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
-      nl += 3;
-      if ((err = cudaGetLastError()) != cudaSuccess) return err;
-      in_key = ok;
-      in_u = ou;
-      in_w = ow;
-    }
-    // union col_ptr straight from the sorted keys (compact vertex space)
-    uint32_t gr = (uint32_t)min64((m + 255) / 256, (uint64_t)bw.num_sms * 16);
-    if ((err = cudaMemsetAsync(bw.gaps, 0, 8, s)) != cudaSuccess) return err;
-    k_radix_colptr<true><<<gr, 256, 0, s>>>(bw.b_key, m, sb.nv, (uint64_t *)bw.ucp, bw.gaps, bw.gap_cap, bw.status,
-                                            bv);
-    k_radix_gaps<<<bw.num_sms * 4, 256, 0, s>>>(bw.gaps, bw.gap_cap, (uint64_t *)bw.ucp);
-    nl += 2;
-  } else if ((err = cudaMemsetAsync(bw.ucp, 0, ((size_t)sb.nv + 1) * 8, s)) != cudaSuccess) {
-    return err;
+  const bool first_to_b = ((passes - 1) % 2) == 0;
+  uint32_t *src_rows = first_to_b ? bw.a_u : bw.b_u;
+  k_b_expand<<<(uint32_t)bw.num_sms * 16, 256, 0, s>>>(bv, src_rows, bw.long_g, bw.long_r, bw.n_long, bw.long_cap,
+                                                       bw.status);
+  k_b_expand_long<<<bw.num_sms * 4, 256, 0, s>>>(bv, bw.long_g, bw.long_r, bw.n_long, bw.long_cap, src_rows);
+  nl += 2;
+  // The first upsweep reads through the descriptors and gathers the union
+  // keys and values into the buffers the first pass does not write; every
+  // pass then runs the bulk-staged downsweep on plain arrays, the last one
+  // storing through the descriptors.
+  const uint32_t Gb = (uint32_t)bw.num_sms * kBCtasPerSm, subb = 2;
+  const uint32_t ntb = (uint32_t)((M + kBTile - 1) / kBTile), tpcb = (ntb + Gb - 1) / Gb;
+  uint32_t *gk = first_to_b ? bw.a_key : bw.b_key, *gw = vals ? (first_to_b ? bw.a_w : bw.b_w) : nullptr;
+  const uint32_t *in_key = gk, *in_u = src_rows, *in_w = gw;
+  for (uint32_t p = 1; p <= passes; ++p) {
+    const bool toB = ((passes - p) % 2) == 0;
+    uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
+    RadixArgs ra{nullptr, nullptr, nullptr, 0, M, in_key, in_u, in_w, ok, ou, ow,
+                 (p - 1) * dbits, dbits, ntb, tpcb, kBTile, bw.table, bw.offsets, bw.status, bv, subb,
+                 p == 1 ? gk : nullptr, p == 1 ? gw : nullptr};
+    const uint32_t rows = Gb * subb;
+    if (p == 1) k_radix_up<true, kBatchFirst><<<rows, kRThreads, 0, s>>>(ra);
+    else k_radix_up<false, kPlain><<<rows, kRThreads, 0, s>>>(ra);
+    k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, rows, bw.offsets);
+    if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+    else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+    else if (vals) k_radix_down_bulk<true, kPlain><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+    else k_radix_down_bulk<false, kPlain><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+    nl += 3;
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    in_key = ok;
+    in_u = ou;
+    in_w = ow;
   }
-  uint32_t gc = (uint32_t)min64((sb.nv + sb.ng + 255) / 256, (uint64_t)bw.num_sms * 16);
-  k_b_colptr<<<gc, 256, 0, s>>>(bv, bw.ucp, sb.nv);
-  ++nl;
+  // union col_ptr straight from the sorted keys (compact column space)
+  const uint32_t gr = (uint32_t)min64((M + 255) / 256, (uint64_t)bw.num_sms * 16);
+  if ((err = cudaMemsetAsync(bw.gaps, 0, 8, s)) != cudaSuccess) return err;
+  k_b_zero_ucp<<<bw.num_sms * 4, 256, 0, s>>>(bv, bw.ucp);
+  k_radix_colptr<true><<<gr ? gr : 1, 256, 0, s>>>(bw.b_key, M, 0, (uint64_t *)bw.ucp, bw.gaps, bw.gap_cap, bw.status,
+                                                   bv);
+  k_radix_gaps<<<bw.num_sms * 4, 256, 0, s>>>(bw.gaps, bw.gap_cap, (uint64_t *)bw.ucp);
+  k_b_colptr<<<(uint32_t)bw.num_sms * 16, 256, 0, s>>>(bv, bw.ucp);
+  nl += 4;
   if (launches) *launches += nl;
   return cudaGetLastError();
 }
