@@ -12,6 +12,7 @@ destination (see ``gt_oracle.c``).  The result is the CSC of Sec. II-A with
 every in-list in ascending source order and duplicate edges in CSR order.
 Rectangular matrices (``n_cols`` columns, ``len(row_ptr) - 1`` rows) follow
 the same definition; the default is the square case of a graph.
+``transpose64`` is the same definition with 64-bit vertex IDs.
 """
 from __future__ import annotations
 
@@ -69,6 +70,8 @@ def _load():
     lib.oracle_columns_rect.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P, P, P, P,
                                         ctypes.c_uint64, P, P, P, P, ctypes.c_uint64]
     lib.oracle_columns_rect.restype = ctypes.c_int
+    lib.oracle_transpose64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, P, P, P, P, P, P]
+    lib.oracle_transpose64.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -108,6 +111,31 @@ def transpose(row_ptr, col_idx, vals=None, n_cols=None):
     vals_out = np.empty(m, dtype=np.float32) if vals is not None else None
     rc = _load().oracle_transpose_rect(n, nc, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
                                        _ptr(col_ptr), _ptr(row_idx), _ptr(vals_out))
+    if rc:
+        raise OracleError(rc)
+    return col_ptr, row_idx, vals_out
+
+
+def transpose64(row_ptr, col_idx, vals=None, n_cols=None):
+    """CSR -> CSC with 64-bit vertex IDs: row_ptr u64[n_rows+1], col_idx
+    u64[m] (< n_cols, default n_rows).  Returns (col_ptr u64[n_cols+1],
+    row_idx u64[m], vals_out f32[m] or None)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.uint64)
+    if vals is not None:
+        vals = np.ascontiguousarray(vals, dtype=np.float32)
+        if vals.shape != col_idx.shape:
+            raise ValueError("vals must have one entry per edge")
+    n_rows = row_ptr.shape[0] - 1
+    if n_rows < 0:
+        raise ValueError("row_ptr must have n_rows + 1 entries")
+    nc = n_rows if n_cols is None else int(n_cols)
+    m = col_idx.shape[0]
+    col_ptr = np.empty(nc + 1, dtype=np.uint64)
+    row_idx = np.empty(m, dtype=np.uint64)
+    vals_out = np.empty(m, dtype=np.float32) if vals is not None else None
+    rc = _load().oracle_transpose64(n_rows, nc, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
+                                    _ptr(row_idx), _ptr(vals_out))
     if rc:
         raise OracleError(rc)
     return col_ptr, row_idx, vals_out

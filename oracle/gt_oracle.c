@@ -216,3 +216,46 @@ int oracle_columns(uint32_t n, uint64_t m, const uint64_t *row_ptr, const uint32
     return oracle_columns_rect(n, n, m, row_ptr, col_idx, vals, cols, ncols, col_start, col_deg, out_rows,
                                out_vals, out_cap);
 }
+
+/*
+ * 64-bit vertex IDs (matrices with more than 2^32 - 1 rows or columns): the
+ * same definition and the same three steps of Algorithm 1 run by one thread,
+ * with u64 column indices in and u64 row IDs out.  col_ptr has n_cols + 1
+ * entries; the counters take 8 (n_cols + 1) bytes of host memory.
+ */
+int oracle_transpose64(uint64_t n_rows, uint64_t n_cols, uint64_t m, const uint64_t *row_ptr,
+                       const uint64_t *col_idx, const float *vals, uint64_t *col_ptr, uint64_t *row_idx,
+                       float *vals_out) {
+    if (!row_ptr || !col_ptr || (m > 0 && (!col_idx || !row_idx)) || (vals && m > 0 && !vals_out)) return OR_ERR_ARG;
+    if (row_ptr[0] != 0 || row_ptr[n_rows] != m) return OR_ERR_ROWPTR;
+    for (uint64_t u = 0; u < n_rows; ++u)
+        if (row_ptr[u] > row_ptr[u + 1]) return OR_ERR_ROWPTR;
+    for (uint64_t e = 0; e < m; ++e)
+        if (col_idx[e] >= n_cols) return OR_ERR_RANGE;
+
+    /* Step 1: in-degrees. */
+    uint64_t *ip = (uint64_t *)calloc((size_t)n_cols + 1, sizeof(uint64_t));
+    if (!ip) return OR_ERR_NOMEM;
+    for (uint64_t e = 0; e < m; ++e) ip[col_idx[e]] += 1;
+
+    /* Step 2: exclusive prefix sum; IP starts as a copy. */
+    uint64_t run = 0;
+    for (uint64_t v = 0; v < n_cols; ++v) {
+        uint64_t d = ip[v];
+        col_ptr[v] = run;
+        ip[v] = run;
+        run += d;
+    }
+    col_ptr[n_cols] = run;
+
+    /* Step 3: edges in CSR order append their source to their destination's list. */
+    for (uint64_t u = 0; u < n_rows; ++u) {
+        for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            uint64_t slot = ip[col_idx[e]]++;
+            row_idx[slot] = u;
+            if (vals) vals_out[slot] = vals[e];
+        }
+    }
+    free(ip);
+    return OR_OK;
+}

@@ -318,3 +318,38 @@ def test_property_random_shapes_vs_definition():
             assert np.array_equal(got[2].view(np.uint32), exp[2].view(np.uint32))
 
     check()
+
+
+def test_oracle64_matches_brute_force_and_the_32_bit_oracle():
+    """The 64-bit-ID routine against the definition (lexicographic sort of the
+    (v, u, e) triples) on random rectangular matrices with duplicates and
+    values, and against the 32-bit routine where IDs fit 32 bits."""
+    from tests._graphs import brute_transpose
+    rng = np.random.default_rng(64)
+    for trial in range(40):
+        nr, nc = int(rng.integers(1, 60)), int(rng.integers(1, 60))
+        deg = rng.integers(0, 6, nr)
+        rp = np.zeros(nr + 1, np.uint64)
+        np.cumsum(deg, out=rp[1:])
+        m = int(rp[-1])
+        ci = rng.integers(0, nc, m).astype(np.uint64)
+        vv = rng.standard_normal(m).astype(np.float32)
+        got = oracle.transpose64(rp, ci, vv, n_cols=nc)
+        exp = brute_transpose(rp, ci, vv, n_cols=nc)
+        assert np.array_equal(got[0], exp[0])
+        assert np.array_equal(got[1], exp[1].astype(np.uint64))
+        assert np.array_equal(got[2].view(np.uint32), exp[2].view(np.uint32))
+        o32 = oracle.transpose(rp, ci.astype(np.uint32), vv, n_cols=nc)
+        assert np.array_equal(got[0], o32[0]) and np.array_equal(got[1], o32[1].astype(np.uint64))
+
+
+def test_oracle64_errors_and_degenerate_shapes():
+    rp = np.array([0, 2, 3], np.uint64)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.transpose64(rp, np.array([0, 5, 1], np.uint64), n_cols=5)  # 5 >= n_cols
+    assert e.value.code == 2
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.transpose64(np.array([0, 2, 1], np.uint64), np.array([0, 1], np.uint64), n_cols=4)
+    assert e.value.code == 3
+    cp, ri, vo = oracle.transpose64(np.zeros(4, np.uint64), np.zeros(0, np.uint64), n_cols=7)
+    assert np.array_equal(cp, np.zeros(8, np.uint64)) and ri.size == 0 and vo is None
