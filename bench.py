@@ -412,6 +412,15 @@ def batched_leg(n_graphs, steps, warmup, pg_reps, config_json=None):
     plan.check()
     ms = ev0.elapsed_time(ev1) / steps
     info = plan.info()
+    # the same captured sequence on an empty call: its launch and layout cost
+    plan.transpose_descs(0, plan.d_descs, None, s)
+    torch.cuda.synchronize()
+    ev0.record(s)
+    for _ in range(steps):
+        plan.transpose_descs(0, plan.d_descs, None, s)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    ms_empty = ev0.elapsed_time(ev1) / steps
     plan.close()
     # per-graph baseline: the library's default configuration per matrix size
     nmax, mmax = int(b["n"].max()), int(b["m"].max())
@@ -452,7 +461,8 @@ def batched_leg(n_graphs, steps, warmup, pg_reps, config_json=None):
             "graphs": ng, "n_edges": m_tot, "n_vertices": v_tot, "algorithmic_bytes": lit,
             "per_graph_baseline": {"value": m_tot / (ms_pg * 1e-3), "unit": UNIT, "ms_per_step": ms_pg,
                                    "reps": pg_reps, "speedup_batched": ms_pg / ms, "identical_output": same},
-            "batch_info": info, "clocks": clk.summary(), "gpu_launches": info["kernel_launches"] * steps}
+            "batch_info": info, "clocks": clk.summary(), "gpu_launches": info["kernel_launches"] * steps,
+            "empty_call_ms": ms_empty, "launch_share": ms_empty / ms}
 
 
 def run_batched(args):
@@ -474,6 +484,17 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def step3_imbalance(busy_ms):
+    """Load imbalance of Step 3 over the warp partitions (Sec. V-F): the share
+    of the step's time the average partition is idle, 1 - mean / max of the
+    busy times, and the coefficient of variation of the busy times."""
+    busy = np.asarray(busy_ms, dtype=np.float64)
+    if busy.size == 0 or busy.max() <= 0:
+        return None
+    return {"partitions": int(busy.size), "idle_share": float(1.0 - busy.mean() / busy.max()),
+            "cv": float(busy.std() / busy.mean()), "max_ms": float(busy.max()), "mean_ms": float(busy.mean())}
+
+
 def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1):
     """PoTra's own method (Algorithm 2, k = 512 HDVs, with the LDV list sort)
     on the same resident graph: per-step device time, per-step stage times,
@@ -482,6 +503,7 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1):
     from paper_2501_06872_gb300 import binding
     cfg = binding.default_config(n_cols, m)
     cfg.method, cfg.hdv_k, cfg.table_log2 = 0, 512, 10
+    cfg.flags |= binding.FLAG_PARTITION_TIMES  # Step 3's per-partition busy times (Sec. V-F imbalance)
     plan = binding.Plan(n, m, weighted, cfg, n_cols=n_cols)
     cp = torch.empty(n_cols + 1, dtype=torch.int64, device="cuda")
     ri = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -503,6 +525,7 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1):
         ms = ev0.elapsed_time(ev1) / steps
         t = plan.timing()
         st = plan.stats()
+        pt = np.array(plan.partition_times())
     finally:
         plan.close()
     same = bool(torch.equal(cp, ref_out[0]) and torch.equal(ri, ref_out[1]) and
@@ -513,6 +536,7 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1):
             "warmup": warmup, "gt_config": cfg.as_dict(),
             "stage_ms": {k: t[k] for k in ("sample_ms", "count_ms", "scan_ms", "scatter_ms", "sort_ms")},
             "scatter_launch_ms": t["dominant_ms"], "hdv_selected": st["hdv_selected"],
+            "step3_imbalance": step3_imbalance(pt),
             "coverage": st["hdv_edges"] / max(1, m), "identical_output": same,
             "gpu_launches": int(st["kernel_launches"]) * steps}
 

@@ -90,6 +90,8 @@ typedef struct gt_config {
                                  0 = 28 (or 32 when the columns need more than 27 bits)       */
     uint32_t batch_edges_log2;/* batch plans: log2 of the union edges of one sub-batch, 16..31;
                                  0 = 31                                                          */
+    uint32_t radix_digit_bits;/* GT_METHOD_RADIX: widest digit of a pass, 4..8 (0 = 8): the
+                                 passes are ceil(key bits / radix_digit_bits) equal digits   */
 } gt_config;
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
@@ -101,11 +103,15 @@ typedef struct gt_config {
  * the paper times them (Sec. V excludes the sort).  The radix method ignores
  * it: its lists are always sorted. */
 #define GT_FLAG_UNSORTED 4u
+/* GT_METHOD_HLH: record the start and end (global timer) of every warp
+ * partition in Step 3, read with gt_plan_partition_times (Sec. V-F measures
+ * Step 3's load imbalance between the threads' partitions). */
+#define GT_FLAG_PARTITION_TIMES 8u
 
 /* GT_METHOD_HLH: PoTra's hash-based LDV-HDV method (Algorithm 2; hdv_k = 0 is
  *   Atomic GT, Algorithm 1) with the LDV list sort.
  * GT_METHOD_RADIX: stable LSD radix sort of the CSR edge sequence by
- *   destination (ceil(bits / 8) passes of equal digits of at most 8 bits);
+ *   destination (ceil(bits / radix_digit_bits) passes of equal digits);
  *   streams the data once per digit, independent of vertex order.  Uses
  *   12-16 bytes per edge of extra workspace. */
 #define GT_METHOD_HLH 0u
@@ -226,6 +232,22 @@ typedef struct gt_host_timing {
     float span_ms;      /* first recorded input copy start to last output copy end  */
 } gt_host_timing;
 gt_status gt_plan_host_timing(gt_plan plan, gt_host_timing *timing);
+
+/* The transposition (Sec. II-A) of a matrix with 64-bit vertex IDs, for more
+ * than 2^32 - 1 rows or columns.  row_ptr: u64[n_rows+1]; col_idx: u64[m]
+ * (< n_cols); vals: f32[m] or NULL; col_ptr: u64[n_cols+1]; row_idx: u64[m];
+ * vals_out: f32[m], NULL iff vals is NULL -- all DEVICE arrays owned by the
+ * caller.  Same output order as gt_transpose (the stable sort of the CSR edge
+ * sequence by destination).  Method: the radix method's digit passes over
+ * the two 32-bit halves of the keys, carrying the edge index, then a gather
+ * of the sources (a search of row_ptr) and values, and col_ptr over the
+ * 64-bit column space.  n_edges < 2^32.  The workspace (32 bytes per edge
+ * plus a few MB) is allocated and freed stream-ordered on `stream`
+ * (cudaMallocAsync).  Synchronises `stream` and returns the device status
+ * (GT_ERR_BAD_ROW_PTR, GT_ERR_OUT_OF_RANGE). */
+gt_status gt_transpose_u64(uint64_t n_rows, uint64_t n_cols, uint64_t n_edges, const uint64_t *row_ptr,
+                           const uint64_t *col_idx, const float *vals, uint64_t *col_ptr, uint64_t *row_idx,
+                           float *vals_out, void *stream);
 
 /* Allocation-free variant of gt_transpose (no counterpart in the paper).
  * For callers that must not allocate device memory on the call path, e.g. a
@@ -381,18 +403,22 @@ gt_status gt_graph_features_rect(uint32_t n_rows, uint32_t n_cols, uint64_t n_ed
                                  void *stream);
 
 /* Grid point `index` (0..GT_TUNE_GRID-1) for a graph of this size
- * (n_vertices: the column count of a rectangular matrix):
- *   0 Atomic GT (hdv_k = 0, Algorithm 1)   1 same without warp aggregation
- *   2 HLH k=64   3 HLH k=512 (Eq. 1)   4 k=512, 1024-edge bulk-copy stages
- *   5 k=2048   6 k=512, 1024-edge partitions   7 k=512, 512 threads x 2 CTAs/SM
- *   8 radix, bulk-copy staged 4096-edge tiles, two 256-thread CTAs per SM
- *   9 radix, register tiles of 4096 edges, 2 CTAs/SM   10 same, 4/SM   11 2048-edge tiles, 4/SM
+ * (n_vertices: the column count of a rectangular matrix).  The two choices
+ * of the paper's probe (Sec. IV-B) and ten radix configurations whose digit
+ * width (pass count), tile kind and CTAs per SM change the time:
+ *   0 Atomic GT (hdv_k = 0, Algorithm 1)   1 HLH, k = 512 (Eq. 1 sizing)
+ *   2 radix, bulk-staged 4096-edge tiles, digits <= 8 bits (the default)
+ *   3 same, digits <= 7   4 same, digits <= 6
+ *   5 radix, register tiles of 4096 edges, 2 CTAs/SM, digits <= 8   6 same, digits <= 7
+ *   7 register 4096, 3 CTAs/SM, digits <= 6
+ *   8 register tiles of 2048 edges, 4 CTAs/SM, digits <= 8   9 same, digits <= 7
+ *   10 register 2048, 6 CTAs/SM, digits <= 8   11 register 2048, 6 CTAs/SM, digits <= 6
  * An HDV count above n/2 becomes 0 (the point then equals Atomic GT). */
 gt_status gt_tune_grid_config(uint32_t index, uint32_t n_vertices, uint64_t n_edges, gt_config *cfg);
 
 /* Analytic choice (the Sec. IV-B cost model, Eqs. 2-3, with GB300 rates and a
  * streaming term for the radix method) from host copies of the features:
- * writes the grid index (0, 3 or 8).  n_vertices: the column count of a
+ * writes the grid index (0, 1 or 2).  n_vertices: the column count of a
  * rectangular matrix. */
 gt_status gt_tune_analytic(const float *features, uint32_t n_vertices, uint64_t n_edges, uint32_t *index);
 
@@ -425,8 +451,11 @@ gt_status gt_selector_backward(gt_selector sel, const float *features, const flo
 /* *in_range = 1 if host features (F floats) lie in the selector's trained
  * range (widened by 5 % of its width), else 0. */
 gt_status gt_selector_in_range(gt_selector sel, const float *host_features, int *in_range);
-/* One Adam step (bias-corrected) with the last gradients on W and b. */
-gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float beta2, float eps, void *stream);
+/* One Adam step (bias-corrected) with the last gradients on W and b; the
+ * moments see g + weight_decay * p (an L2 penalty weight_decay/2 |W, b|^2;
+ * 0 = plain Adam). */
+gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float beta2, float eps, float weight_decay,
+                                void *stream);
 void gt_selector_destroy(gt_selector sel);
 
 typedef struct gt_tune_entry {
@@ -467,6 +496,13 @@ gt_status gt_plan_enable_timing(gt_plan plan, int enable);
 
 /* Averages of the recorded calls (synchronises the plan's stream). */
 gt_status gt_plan_timing(gt_plan plan, gt_timing *timing);
+
+/* Step 3's per-partition busy times (ms, end - start of each warp
+ * partition) of the last gt_transpose of a plan configured with
+ * GT_FLAG_PARTITION_TIMES (HLH method): writes min(P, cap) entries and
+ * *count = P (the warp partitions).  Synchronises.  GT_ERR_INVALID_ARG if the
+ * plan does not record them. */
+gt_status gt_plan_partition_times(gt_plan plan, float *busy_ms, uint32_t cap, uint32_t *count);
 
 /* Device bytes held by the plan's workspace. */
 uint64_t gt_plan_workspace_bytes(gt_plan plan);

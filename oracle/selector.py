@@ -187,12 +187,14 @@ def backward(p, X, T, M, F=N_FEATURES, H=HIDDEN, K=GRID):
     return L, g
 
 
-def adam(p, g, m1, m2, t, lr, b1=0.9, b2=0.999, eps=1e-8, first=None):
-    """Adam step t (1-based) on entries [first, end) (all when first is None)."""
+def adam(p, g, m1, m2, t, lr, b1=0.9, b2=0.999, eps=1e-8, first=None, wd=0.0):
+    """Adam step t (1-based) on entries [first, end) (all when first is None),
+    with an L2 penalty wd/2 |p|^2: the moments see g + wd * p."""
     p, g, m1, m2 = (np.array(a, dtype=np.float64) for a in (p, g, m1, m2))
     lo = 0 if first is None else first
-    m1[lo:] = b1 * m1[lo:] + (1.0 - b1) * g[lo:]
-    m2[lo:] = b2 * m2[lo:] + (1.0 - b2) * g[lo:] ** 2
+    gw = g[lo:] + wd * p[lo:]
+    m1[lo:] = b1 * m1[lo:] + (1.0 - b1) * gw
+    m2[lo:] = b2 * m2[lo:] + (1.0 - b2) * gw ** 2
     mh = m1[lo:] / (1.0 - b1 ** t)
     vh = m2[lo:] / (1.0 - b2 ** t)
     p[lo:] = p[lo:] - lr * mh / (np.sqrt(vh) + eps)

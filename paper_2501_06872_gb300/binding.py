@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgt.so")
 GT_OK = 0
 STATUS = {0: "GT_OK", 1: "GT_ERR_INVALID_ARG", 2: "GT_ERR_OUT_OF_RANGE", 3: "GT_ERR_BAD_ROW_PTR",
           4: "GT_ERR_NO_MEMORY", 5: "GT_ERR_CUDA", 6: "GT_ERR_TIMEOUT", 7: "GT_ERR_UNSUPPORTED"}
-FLAG_AGGREGATE, FLAG_NO_GRAPH, FLAG_UNSORTED = 1, 2, 4
+FLAG_AGGREGATE, FLAG_NO_GRAPH, FLAG_UNSORTED, FLAG_PARTITION_TIMES = 1, 2, 4, 8
 METHOD_HLH = 0
 METHOD_RADIX = 1
 
@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
                 ("sample_permille", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("method", ctypes.c_uint32), ("radix_tile", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("batch_key_bits", ctypes.c_uint32),
-                ("batch_edges_log2", ctypes.c_uint32)]
+                ("batch_edges_log2", ctypes.c_uint32), ("radix_digit_bits", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -117,7 +117,8 @@ EXPORTS = ["gt_default_config", "gt_plan_create", "gt_plan_set_config", "gt_plan
            "gt_plan_host_wait", "gt_plan_create_rect", "gt_transpose_sub_rect", "gt_plan_shape",
            "gt_graph_features_rect", "gt_plan_host_timing",
            "gt_batch_limits_from_descs", "gt_batch_plan_set_config", "gt_batch_plan_get_config",
-           "gt_batch_tune_grid_config", "gt_batch_plan_tune"]
+           "gt_batch_tune_grid_config", "gt_batch_plan_tune", "gt_transpose_u64",
+           "gt_plan_partition_times"]
 
 N_FEATURES = 41
 TUNE_GRID = 12
@@ -168,8 +169,13 @@ def load():
     lib.gt_batch_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
     lib.gt_batch_tune_grid_config.argtypes = [u32, ctypes.POINTER(Config)]
     lib.gt_batch_plan_tune.argtypes = [P, u32, P, P, u32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(u32), P]
+    lib.gt_plan_partition_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), u32, ctypes.POINTER(u32)]
+    lib.gt_plan_partition_times.restype = ctypes.c_int
+    lib.gt_transpose_u64.argtypes = [u64, u64, u64, P, P, P, P, P, P, P]
+    lib.gt_transpose_u64.restype = ctypes.c_int
     for f in ["gt_batch_limits_from_descs", "gt_batch_plan_set_config", "gt_batch_plan_get_config",
-              "gt_batch_tune_grid_config", "gt_batch_plan_tune"]:
+              "gt_batch_tune_grid_config", "gt_batch_plan_tune", "gt_transpose_u64",
+           "gt_plan_partition_times"]:
         getattr(lib, f).restype = ctypes.c_int
     lib.gt_batch_plan_status.argtypes = [P]
     lib.gt_batch_plan_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
@@ -189,7 +195,7 @@ def load():
     lib.gt_selector_set_params.argtypes = [P, P]
     lib.gt_selector_forward.argtypes = [P, P, u32, P, P]
     lib.gt_selector_backward.argtypes = [P, P, P, P, u32, P, P, P]
-    lib.gt_selector_adam_step.argtypes = [P, F, F, F, F, P]
+    lib.gt_selector_adam_step.argtypes = [P, F, F, F, F, F, P]
     lib.gt_selector_in_range.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     lib.gt_selector_destroy.argtypes = [P]
     lib.gt_selector_destroy.restype = None
@@ -341,6 +347,15 @@ class Plan:
         t = Timing()
         _check(self._lib.gt_plan_timing(self._h, ctypes.byref(t)), "gt_plan_timing")
         return t.as_dict()
+
+    def partition_times(self):
+        """Step 3's per-partition busy times (ms) of the last call (GT_FLAG_PARTITION_TIMES)."""
+        cnt = ctypes.c_uint32()
+        _check(self._lib.gt_plan_partition_times(self._h, None, 0, ctypes.byref(cnt)), "gt_plan_partition_times")
+        buf = (ctypes.c_float * max(1, cnt.value))()
+        _check(self._lib.gt_plan_partition_times(self._h, buf, cnt.value, ctypes.byref(cnt)),
+               "gt_plan_partition_times")
+        return [float(x) for x in buf[:cnt.value]]
 
     def workspace_bytes(self) -> int:
         return int(self._lib.gt_plan_workspace_bytes(self._h))
@@ -564,9 +579,9 @@ class Selector:
                "gt_selector_in_range")
         return bool(ok.value)
 
-    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
         _check(self._lib.gt_selector_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps),
-                                               _stream(stream)), "gt_selector_adam_step")
+                                               float(weight_decay), _stream(stream)), "gt_selector_adam_step")
 
     @classmethod
     def pretrained(cls):
@@ -586,6 +601,25 @@ class Selector:
             self.close()
         except Exception:
             pass
+
+
+def transpose_u64(row_ptr, col_idx, vals=None, n_cols=None, stream=None):
+    """gt_transpose_u64 on device tensors with 64-bit IDs (row_ptr int64[n_rows+1],
+    col_idx int64[m], vals float32[m] or None); allocates the outputs and
+    returns (col_ptr int64[n_cols+1], row_idx int64[m], vals_out or None).
+    Synchronous; raises GtError on any non-OK status."""
+    import torch
+    n_rows = row_ptr.numel() - 1
+    nc = n_rows if n_cols is None else int(n_cols)
+    m = col_idx.numel()
+    dev = row_ptr.device
+    col_ptr = torch.empty(nc + 1, dtype=torch.int64, device=dev)
+    row_idx = torch.empty(m, dtype=torch.int64, device=dev)
+    vals_out = torch.empty(m, dtype=torch.float32, device=dev) if vals is not None else None
+    rc = load().gt_transpose_u64(n_rows, nc, m, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(col_ptr),
+                                 _ptr(row_idx), _ptr(vals_out), _stream(stream))
+    _check(rc, "gt_transpose_u64")
+    return col_ptr, row_idx, vals_out
 
 
 def transpose_noalloc(row_ptr, col_idx, vals, col_ptr, row_idx, vals_out, stream=None):

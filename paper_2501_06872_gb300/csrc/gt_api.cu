@@ -104,6 +104,7 @@ bool config_valid(const gt_config &c) {
   if (c.sample_permille > 1000) return false;
   if (c.method > GT_METHOD_RADIX) return false;
   if (c.radix_tile != 0 && c.radix_tile != 2048 && c.radix_tile != 4096) return false;
+  if (c.radix_digit_bits != 0 && (c.radix_digit_bits < 4 || c.radix_digit_bits > 8)) return false;
   return true;
 }
 
@@ -143,6 +144,8 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   w.r_items = c.radix_tile == 2048 ? 8u : 16u;
   w.r_bulk = c.radix_tile == 0 ? 1 : 0;
   w.rG = (uint32_t)num_sms * c.ctas_per_sm;
+  w.r_dcap = c.radix_digit_bits ? c.radix_digit_bits : 8u;
+  w.ptimes = (c.flags & GT_FLAG_PARTITION_TIMES) ? 1 : 0;
   if (w.method == GT_METHOD_RADIX) {
     w.kmax = 0;
     w.tlog2 = 0;
@@ -223,6 +226,7 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(ties, (w.kmax ? gt::kTieCap : 1) * 4);
   GT_AL(biglist, (size_t)w.big_cap * 4);
   GT_AL(scratch, m * (w.has_vals ? 8 : 4));
+  if (w.ptimes) GT_AL(ptime, (size_t)w.P * 2 * 8);
 #undef GT_AL
   if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
   if (cudaMemset(w.meta, 0, gt::kMetaCount * 4) != cudaSuccess) return GT_ERR_CUDA;
@@ -407,6 +411,8 @@ static gt_status shape_for(gt_plan plan, uint32_t n_rows, uint32_t n, uint64_t m
   w.rG = t.rG;
   w.r_items = t.r_items;
   w.r_bulk = t.r_bulk;
+  w.r_dcap = t.r_dcap;
+  w.ptimes = t.ptimes;
   w.r_gap_cap = (uint32_t)(t.n / 1024 + 2) < w.r_gap_cap ? (uint32_t)(t.n / 1024 + 2) : w.r_gap_cap;
   return GT_OK;
 }
@@ -729,6 +735,83 @@ gt_status gt_transpose_host_async(gt_plan plan, const uint64_t *row_ptr, const u
   if (hev && (e = cudaEventRecord(hev->out1, c)) != cudaSuccess) return from_cuda(e);
   if ((e = cudaEventRecord(plan->ev_copied[k], c)) != cudaSuccess) return from_cuda(e);
   return GT_OK;
+}
+
+gt_status gt_plan_partition_times(gt_plan plan, float *busy_ms, uint32_t cap, uint32_t *count) {
+  if (!plan || (cap > 0 && !busy_ms)) return GT_ERR_INVALID_ARG;
+  if (count) *count = 0;
+  if (!plan->w.ptime) return GT_ERR_INVALID_ARG;  // the plan's configuration does not record them
+  cudaError_t e;
+  if (plan->last && (e = cudaStreamSynchronize(plan->last)) != cudaSuccess) return from_cuda(e);
+  const uint32_t P = plan->w.P;
+  std::vector<unsigned long long> t((size_t)P * 2);
+  if ((e = cudaMemcpy(t.data(), plan->w.ptime, t.size() * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return from_cuda(e);
+  for (uint32_t p = 0; p < P && p < cap; ++p)
+    busy_ms[p] = t[2 * (size_t)p + 1] >= t[2 * (size_t)p] ? (float)((t[2 * (size_t)p + 1] - t[2 * (size_t)p]) * 1e-6)
+                                                          : 0.f;
+  if (count) *count = P;
+  return GT_OK;
+}
+
+gt_status gt_transpose_u64(uint64_t n_rows, uint64_t n_cols, uint64_t n_edges, const uint64_t *row_ptr,
+                           const uint64_t *col_idx, const float *vals, uint64_t *col_ptr, uint64_t *row_idx,
+                           float *vals_out, void *stream) {
+  if (!row_ptr || !col_ptr) return GT_ERR_INVALID_ARG;
+  if (n_edges > 0 && (!col_idx || !row_idx)) return GT_ERR_INVALID_ARG;
+  if ((vals == nullptr) != (vals_out == nullptr)) return GT_ERR_INVALID_ARG;
+  if ((n_rows == 0 || n_cols == 0) && n_edges != 0) return GT_ERR_INVALID_ARG;
+  if (n_edges > 0xFFFFFFFFull || n_cols == ~0ull) return GT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n_rows == 0 || n_cols == 0) {
+    if ((e = cudaMemsetAsync(col_ptr, 0, (size_t)(n_cols + 1) * 8, s)) != cudaSuccess) return from_cuda(e);
+    return from_cuda(cudaStreamSynchronize(s));
+  }
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess || (e = gt::configure_kernels(dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+    gt_status st = from_cuda(e);
+    cudaGetLastError();
+    return st;
+  }
+  gt::U64Work w;
+  w.n_rows = n_rows;
+  w.n_cols = n_cols;
+  w.m = n_edges;
+  w.num_sms = sms;
+  w.row_ptr = row_ptr;
+  w.col_idx = col_idx;
+  w.vals = vals;
+  w.col_ptr = col_ptr;
+  w.row_idx = row_idx;
+  w.vals_out = vals_out;
+  // stream-ordered workspace, freed on the same stream
+  const size_t m = n_edges ? (size_t)n_edges : 1, rows = (size_t)sms * 8;
+  void *bufs[10] = {};
+  const size_t sizes[10] = {m * 4, m * 4, m * 4, m * 4, m * 4, m * 4, m * 8, rows * 256 * 4, rows * 256 * 8, 16};
+  gt_status st = GT_OK;
+  for (int i = 0; i < 10 && st == GT_OK; ++i)
+    if ((e = cudaMallocAsync(&bufs[i], sizes[i], s)) != cudaSuccess) st = from_cuda(e);
+  if (st == GT_OK) {
+    w.a_key = (uint32_t *)bufs[0], w.a_u = (uint32_t *)bufs[1], w.a_w = (uint32_t *)bufs[2];
+    w.b_key = (uint32_t *)bufs[3], w.b_u = (uint32_t *)bufs[4], w.b_w = (uint32_t *)bufs[5];
+    w.keys = (uint64_t *)bufs[6];
+    w.table = (uint32_t *)bufs[7];
+    w.offsets = (unsigned long long *)bufs[8];
+    w.status = (uint32_t *)bufs[9];
+    if ((e = cudaMemsetAsync(w.status, 0, 4, s)) != cudaSuccess || (e = gt::run_radix_u64(w, s)) != cudaSuccess)
+      st = from_cuda(e);
+  }
+  uint32_t dstat = 0;
+  if (st == GT_OK && (e = cudaMemcpyAsync(&dstat, w.status, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    st = from_cuda(e);
+  for (void *b : bufs)
+    if (b) cudaFreeAsync(b, s);
+  e = cudaStreamSynchronize(s);
+  if (st == GT_OK && e != cudaSuccess) st = from_cuda(e);
+  cudaGetLastError();
+  return st != GT_OK ? st : (gt_status)dstat;
 }
 
 gt_status gt_plan_host_timing(gt_plan plan, gt_host_timing *t) {

@@ -59,6 +59,8 @@ struct DevWork {
   uint32_t *cand = nullptr;                    // [kmax]
   uint32_t *ties = nullptr;                    // [kTieCap]
   uint32_t *biglist = nullptr;                 // [big_cap]
+  int ptimes = 0;                              // record Step 3's per-partition start/end times
+  unsigned long long *ptime = nullptr;         // [2 * P] global-timer ns (ptimes only)
   // HLH, [m] entries: weighted graphs keep LDV entries here as u64 (value bits
   // << 32 | source, bit 31 of the source tagging split rows) until the LDV sort
   // moves them to the outputs; the long-list radix sort uses it as its second buffer.
@@ -68,6 +70,7 @@ struct DevWork {
   uint32_t rG = 0;                            // persistent CTAs of the digit passes
   uint32_t r_items = 16;                      // elements per thread of a downsweep tile (8 or 16)
   int r_bulk = 0;                             // bulk-copy staged downsweep (two 256-thread CTAs per SM)
+  uint32_t r_dcap = 8;                        // widest digit of a pass (4..8)
   uint32_t *r_a_key = nullptr, *r_a_u = nullptr, *r_a_w = nullptr;  // [m] ping buffer
   uint32_t *r_b_key = nullptr;                // [m] keys of the pong buffer (u/w live in the outputs)
   uint32_t *r_long = nullptr;                 // rows longer than the window expansion handles
@@ -106,6 +109,25 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
 // from the sorted keys (w.r_nlong and the gap count must be zeroed).
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches,
                       StepEvents *events);
+
+// 64-bit vertex IDs: sizes, the caller's arrays and a stream-ordered
+// workspace (two sets of key-half / payload arrays, the sorted keys, the
+// digit tables and a status word).
+struct U64Work {
+  uint64_t n_rows = 0, n_cols = 0, m = 0;
+  int num_sms = 0;
+  const uint64_t *row_ptr = nullptr, *col_idx = nullptr;
+  const float *vals = nullptr;
+  uint64_t *col_ptr = nullptr, *row_idx = nullptr;
+  float *vals_out = nullptr;
+  uint32_t *a_key = nullptr, *a_u = nullptr, *a_w = nullptr, *b_key = nullptr, *b_u = nullptr, *b_w = nullptr;
+  uint64_t *keys = nullptr;
+  uint32_t *table = nullptr;
+  unsigned long long *offsets = nullptr;
+  uint32_t *status = nullptr;
+};
+
+cudaError_t run_radix_u64(const U64Work &w, cudaStream_t s);
 
 // The arguments of one batch call, in device memory (written by a small
 // kernel before the captured sequence, which reads them).

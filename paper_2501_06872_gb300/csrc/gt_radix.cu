@@ -8,7 +8,8 @@
 // graphs whose working set is far larger than L2.
 //
 // Per call: the row expansion writes the source of every edge; then per
-// digit pass (passes = ceil(bits(n-1) / 8) for n columns, digits split evenly):
+// digit pass (passes = ceil(bits(n-1) / the digit cap, 8 by default) for n
+// columns, digits split evenly):
 //   upsweep    per-CTA digit counts of the CTA's contiguous tile range
 //              (with the bulk downsweep, two upsweep CTAs per range)
 //   offsets    exclusive scan of the table in (digit, CTA) order
@@ -21,6 +22,8 @@
 // same passes over the union of their graphs (key = graph, destination).
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <utility>
 
 #include "gt_device.cuh"
 #include "gt_internal.h"
@@ -785,7 +788,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   uint32_t nl = 0;
   cudaError_t err;
   const uint32_t bits = key_bits_of(n);
-  const uint32_t passes = (bits + 7) / 8;
+  const uint32_t passes = (bits + w.r_dcap - 1) / w.r_dcap;
   const uint32_t dbits = (bits + passes - 1) / passes;
   const uint32_t items = w.r_items;
   // buffers: A = (a_key, a_u, a_w); B = (b_key, row_idx, vals_out).  Pass p
@@ -858,6 +861,141 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
 // ---------------------------------------------------------------------------
 // Batches (sub-batch of graphs laid out in union edge / vertex spaces)
 // ---------------------------------------------------------------------------
+
+// ---- 64-bit vertex IDs -------------------------------------------------------
+// The same stable sort of the CSR edge sequence by destination, for matrices
+// with more than 2^32 - 1 rows or columns: the 64-bit keys are sorted as two
+// 32-bit halves by the digit passes above (low half first, carrying the high
+// half and the edge index; then the high half, carrying the index), and the
+// sorted edge indices gather the source rows (a search of row_ptr) and the
+// values.  col_ptr comes from the sorted keys over the 64-bit column space.
+
+// row_ptr: row_ptr[0] = 0, non-decreasing, row_ptr[n_rows] = m.
+__global__ void k64_check_rows(const uint64_t *__restrict__ row_ptr, uint64_t n_rows, uint64_t m, uint32_t *status) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (u == 0 && (row_ptr[0] != 0 || row_ptr[n_rows] != m)) set_status(status, GT_ERR_BAD_ROW_PTR);
+  bool bad = false;
+  for (; u < n_rows; u += stride) bad |= row_ptr[u] > row_ptr[u + 1];
+  if (bad) set_status(status, GT_ERR_BAD_ROW_PTR);
+}
+
+// Key halves and the identity index; destinations >= n_cols are reported.
+__global__ void k64_prepare(const uint64_t *__restrict__ col_idx, uint64_t m, uint64_t n_cols, uint32_t *key_lo,
+                            uint32_t *key_hi, uint32_t *idx, uint32_t *status) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint64_t v = __ldcs(col_idx + e);
+    bad |= v >= n_cols;
+    key_lo[e] = (uint32_t)v;
+    key_hi[e] = (uint32_t)(v >> 32);
+    idx[e] = (uint32_t)e;
+  }
+  if (bad) set_status(status, GT_ERR_OUT_OF_RANGE);
+}
+
+// Slot i of the output takes edge perm[i]: its row (the last row whose
+// offset is <= the edge), its value and its destination.
+__global__ void k64_gather(const uint64_t *__restrict__ row_ptr, uint64_t n_rows, const uint64_t *__restrict__ col_idx,
+                           const float *__restrict__ vals, const uint32_t *__restrict__ perm, uint64_t m,
+                           uint64_t *row_idx, float *vals_out, uint64_t *keys) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += stride) {
+    const uint64_t e = perm[i];
+    uint64_t lo = 0, hi = n_rows;  // largest u < n_rows with row_ptr[u] <= e
+    while (hi - lo > 1) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if (row_ptr[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    row_idx[i] = lo;
+    if (vals) vals_out[i] = vals[e];
+    keys[i] = col_idx[e];
+  }
+}
+
+// col_ptr[v] = number of sorted keys < v, for v in [0, n_cols].  One warp per
+// chunk of 2048 consecutive entries: the keys that fall in the chunk are found
+// by two searches; a chunk without keys is one constant, else every entry
+// searches the chunk's keys.
+constexpr uint64_t k64Chunk = 2048;
+
+__device__ __forceinline__ uint64_t lower_bound64(const uint64_t *a, uint64_t lo, uint64_t hi, uint64_t x) {
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k64_colptr(const uint64_t *__restrict__ keys, uint64_t m, uint64_t n_cols, uint64_t *col_ptr) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t chunks = (n_cols + 1 + k64Chunk - 1) / k64Chunk;
+  for (uint64_t c = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); c < chunks; c += warps) {
+    const uint64_t v0 = c * k64Chunk;
+    const uint64_t v1 = v0 + k64Chunk < n_cols + 1 ? v0 + k64Chunk : n_cols + 1;
+    uint64_t lo = 0, hi = 0;
+    if (lane == 0) {
+      lo = lower_bound64(keys, 0, m, v0);
+      hi = lower_bound64(keys, lo, m, v1);
+    }
+    lo = __shfl_sync(kFull, lo, 0);
+    hi = __shfl_sync(kFull, hi, 0);
+    for (uint64_t v = v0 + lane; v < v1; v += 32) col_ptr[v] = lo == hi ? lo : lower_bound64(keys, lo, hi, v);
+  }
+}
+
+cudaError_t run_radix_u64(const U64Work &w, cudaStream_t s) {
+  cudaError_t err;
+  const uint64_t m = w.m;
+  const uint32_t g = (uint32_t)w.num_sms * 16;
+  k64_check_rows<<<g, 256, 0, s>>>(w.row_ptr, w.n_rows, m, w.status);
+  if (m > 0) {
+    k64_prepare<<<g, 256, 0, s>>>(w.col_idx, m, w.n_cols, w.a_key, w.a_u, w.a_w, w.status);
+    uint32_t bits = 0;
+    while (bits < 64 && ((w.n_cols - 1) >> bits)) ++bits;
+    if (bits == 0) bits = 1;
+    const uint32_t lo_bits = bits < 32 ? bits : 32, hi_bits = bits > 32 ? bits - 32 : 0;
+    const uint32_t Gb = (uint32_t)w.num_sms * kBCtasPerSm, sub = 2;
+    const uint32_t ntiles = (uint32_t)((m + kBTile - 1) / kBTile), tpc = (ntiles + Gb - 1) / Gb;
+    // current arrays: (key half, payload 1, payload 2)
+    uint32_t *ck = w.a_key, *cu = w.a_u, *cw = w.a_w, *nk = w.b_key, *nu = w.b_u, *nw = w.b_w;
+    auto pass = [&](uint32_t shift, uint32_t dbits, bool three) -> cudaError_t {
+      RadixArgs ra{nullptr, nullptr, nullptr, 0, m, ck, cu, three ? cw : nullptr, nk, nu, three ? nw : nullptr,
+                   shift, dbits, ntiles, tpc, kBTile, w.table, w.offsets, w.status, BatchView{nullptr, 0}, sub};
+      k_radix_up<false, kPlain><<<Gb * sub, kRThreads, 0, s>>>(ra);
+      k_radix_offsets<<<1, 1024, 0, s>>>(w.table, Gb * sub, w.offsets);
+      if (three) k_radix_down_bulk<true, kPlain><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+      else k_radix_down_bulk<false, kPlain><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+      std::swap(ck, nk);
+      std::swap(cu, nu);
+      std::swap(cw, nw);
+      return cudaGetLastError();
+    };
+    // low half: key = low 32 bits, carrying (high half, index)
+    const uint32_t pa = (lo_bits + 7) / 8, da = (lo_bits + pa - 1) / pa;
+    for (uint32_t p = 0; p < pa; ++p)
+      if ((err = pass(p * da, da, true)) != cudaSuccess) return err;
+    // high half: key = the carried high half, carrying the index
+    const uint32_t *perm = cw;
+    if (hi_bits) {
+      ck = cu;   // the high halves become the keys
+      cu = cw;   // the indices the payload
+      nk = nu;   // free arrays of the other set
+      nu = nw;
+      const uint32_t pb = (hi_bits + 7) / 8, db = (hi_bits + pb - 1) / pb;
+      for (uint32_t p = 0; p < pb; ++p)
+        if ((err = pass(p * db, db, false)) != cudaSuccess) return err;
+      perm = cu;
+    }
+    k64_gather<<<g, 256, 0, s>>>(w.row_ptr, w.n_rows, w.col_idx, w.vals, perm, m, w.row_idx, w.vals_out, w.keys);
+  }
+  k64_colptr<<<g, 256, 0, s>>>(w.keys, m, w.n_cols, w.col_ptr);
+  return cudaGetLastError();
+}
 
 // ---- layout of one batch call (device-side, read by every later kernel) ----
 

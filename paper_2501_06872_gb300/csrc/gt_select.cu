@@ -346,11 +346,13 @@ __global__ void k_dense_bwd_x(const float *__restrict__ dY, const float *__restr
 }
 
 // Adam (Kingma & Ba 2015) on params[lo, hi): bias-corrected moments.
+// Adam with an L2 penalty wd/2 |W|^2 on the trained entries: the gradient
+// seen by the moments is g + wd * p.
 __global__ void k_adam(float *p, const float *__restrict__ g, float *m1, float *m2, uint32_t lo, uint32_t hi,
-                       float lr, float b1, float b2, float eps, float bc1, float bc2) {
+                       float lr, float b1, float b2, float eps, float bc1, float bc2, float wd) {
   const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= hi) return;
-  const float gi = g[i];
+  const float gi = g[i] + wd * p[i];
   const float a = b1 * m1[i] + (1.f - b1) * gi;
   const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
   m1[i] = a;
@@ -586,15 +588,17 @@ gt_status gt_selector_backward(gt_selector sel, const float *features, const flo
   return cuda_status(e);
 }
 
-gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float beta2, float eps, void *stream) {
-  if (!sel || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+gt_status gt_selector_adam_step(gt_selector sel, float lr, float beta1, float beta2, float eps, float weight_decay,
+                                void *stream) {
+  if (!sel || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) ||
+      !(weight_decay >= 0.f))
     return GT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   sel->steps += 1;
   const float bc1 = (float)(1.0 - pow((double)beta1, (double)sel->steps));
   const float bc2 = (float)(1.0 - pow((double)beta2, (double)sel->steps));
   k_adam<<<blocks(kParams - kOffW1, 256), 256, 0, s>>>(sel->params, sel->grads, sel->m1, sel->m2, kOffW1, kParams, lr,
-                                                       beta1, beta2, eps, bc1, bc2);
+                                                       beta1, beta2, eps, bc1, bc2, weight_decay);
   return cuda_status(cudaGetLastError());
 }
 
@@ -629,20 +633,27 @@ gt_status gt_tune_grid_config(uint32_t index, uint32_t n_vertices, uint64_t n_ed
   cfg->flags = GT_FLAG_AGGREGATE;
   cfg->stage_edges = 0;
   cfg->radix_tile = 0;
+  cfg->radix_digit_bits = 0;
   uint32_t k = 0;
+  auto radix = [&](uint32_t tile, uint32_t ctas, uint32_t digit) {
+    cfg->method = GT_METHOD_RADIX;
+    cfg->radix_tile = tile;
+    cfg->ctas_per_sm = ctas;
+    cfg->radix_digit_bits = digit;
+  };
   switch (index) {
-    case 0: k = 0; break;                                    // Atomic GT (Algorithm 1)
-    case 1: k = 0; cfg->flags = 0; break;                    // Atomic GT without warp aggregation
-    case 2: k = 64; break;
-    case 3: k = 512; break;                                  // Eq. 1 sizing
-    case 4: k = 512; cfg->stage_edges = 1024; break;         // bulk-copy staged edge tiles
-    case 5: k = 2048; break;
-    case 6: k = 512; cfg->warp_edges = 1024; break;          // finer partitions
-    case 7: k = 512; cfg->block_threads = 512; cfg->ctas_per_sm = 2; break;
-    case 8: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 0; cfg->ctas_per_sm = 4; break;  // bulk-staged
-    case 9: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 4096; cfg->ctas_per_sm = 2; break;
-    case 10: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 4096; cfg->ctas_per_sm = 4; break;
-    default: cfg->method = GT_METHOD_RADIX; cfg->radix_tile = 2048; cfg->ctas_per_sm = 4; break;
+    case 0: k = 0; break;               // Atomic GT (Algorithm 1)
+    case 1: k = 512; break;             // HLH, Eq. 1 sizing
+    case 2: radix(0, 4, 8); break;      // bulk-staged tiles (two CTAs per SM whatever ctas_per_sm says)
+    case 3: radix(0, 4, 7); break;
+    case 4: radix(0, 4, 6); break;
+    case 5: radix(4096, 2, 8); break;   // register tiles
+    case 6: radix(4096, 2, 7); break;
+    case 7: radix(4096, 3, 6); break;
+    case 8: radix(2048, 4, 8); break;
+    case 9: radix(2048, 4, 7); break;
+    case 10: radix(2048, 6, 8); break;
+    default: radix(2048, 6, 6); break;
   }
   if (cfg->method == GT_METHOD_RADIX || k > n_vertices / 2) k = 0;
   cfg->hdv_k = k;
@@ -690,10 +701,10 @@ gt_status gt_tune_analytic(const float *features, uint32_t n_vertices, uint64_t 
   uint32_t best = 0;
   double t = atomic;
   if (hlh < t) {
-    best = 3;
+    best = 1;
     t = hlh;
   }
-  if (radix < t) best = 8;
+  if (radix < t) best = 2;
   (void)n_edges;
   *index = best;
   return GT_OK;
@@ -736,10 +747,25 @@ gt_status run_timed(gt_plan plan, const uint64_t *row_ptr, const uint32_t *col_i
   return GT_OK;
 }
 
-bool same_config(const gt_config &a, const gt_config &b) {
+// Grid points that run the same kernel sequence on an n-column matrix: radix
+// points whose digit caps give the same pass count (hence the same digits)
+// differ in nothing else, and the bulk-staged tile ignores ctas_per_sm.
+uint32_t radix_passes(const gt_config &c, uint32_t n) {
+  uint32_t bits = 0;
+  while (bits < 32 && ((n ? n - 1 : 0) >> bits)) ++bits;
+  if (bits == 0) bits = 1;
+  const uint32_t cap = c.radix_digit_bits ? c.radix_digit_bits : 8u;
+  return (bits + cap - 1) / cap;
+}
+
+bool same_config(const gt_config &a, const gt_config &b, uint32_t n) {
+  if (a.method != b.method) return false;
+  if (a.method == GT_METHOD_RADIX)
+    return a.radix_tile == b.radix_tile && (a.radix_tile == 0 || a.ctas_per_sm == b.ctas_per_sm) &&
+           radix_passes(a, n) == radix_passes(b, n);
   return a.hdv_k == b.hdv_k && a.table_log2 == b.table_log2 && a.block_threads == b.block_threads &&
          a.ctas_per_sm == b.ctas_per_sm && a.warp_edges == b.warp_edges && a.stage_edges == b.stage_edges &&
-         a.flags == b.flags && a.method == b.method && a.radix_tile == b.radix_tile;
+         a.flags == b.flags;
 }
 
 }  // namespace
@@ -777,7 +803,7 @@ extern "C" gt_status gt_plan_tune(gt_plan plan, int mode, gt_selector sel, const
       gt_status ei = GT_OK;
       uint32_t dup = i;
       for (uint32_t j = 0; j < i; ++j)
-        if (same_config(grid[i], grid[j])) {
+        if (same_config(grid[i], grid[j], n)) {
           dup = j;
           break;
         }

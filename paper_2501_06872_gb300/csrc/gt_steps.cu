@@ -647,7 +647,14 @@ struct ScatterArgs {
   uint32_t *status;
   int flag_mode;
   uint32_t stage_edges;
+  unsigned long long *ptime;  // optional [2 * P]: global-timer ns at the start and end of each partition
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 template <bool HDV, bool VALS, bool STAGED>
 __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
@@ -672,7 +679,11 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
   }
   __syncthreads();
   const uint64_t e0 = a.part[p], e1 = a.part[p + 1];
-  if (e0 >= e1) return;
+  if (a.ptime && lane == 0) a.ptime[2 * (size_t)p] = global_ns();
+  if (e0 >= e1) {
+    if (a.ptime && lane == 0) a.ptime[2 * (size_t)p + 1] = a.ptime[2 * (size_t)p];
+    return;
+  }
   uint32_t *mycur = cur + w * a.kmax;
 
   // rows at both ends of the partition (they may be shared with neighbours)
@@ -840,6 +851,10 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
       for (uint64_t i = waited; i < min64(waited + 2, ntile); ++i) mbar_wait(&bars[i & 1u], (uint32_t)((i >> 1) & 1u));
     }
   }
+  if (a.ptime) {
+    __syncwarp();
+    if (lane == 0) a.ptime[2 * (size_t)p + 1] = global_ns();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -987,10 +1002,11 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   mark(3);
 
   // Step 3
+  if (w.ptime && (err = cudaMemsetAsync(w.ptime, 0, (size_t)w.P * 16, s)) != cudaSuccess) return err;
   ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n, w.n_rows, w.m,       w.part,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
                  pb.col_ptr, pb.row_idx, pb.vals_out, unsorted ? nullptr : (unsigned long long *)w.scratch,
-                 w.status, flag_mode, w.stage_edges};
+                 w.status, flag_mode, w.stage_edges, w.ptime};
   const bool vals = pb.vals != nullptr;
 #define GT_SC(H, V, ST) k_scatter<H, V, ST><<<w.G, threads, w.smem_scatter, s>>>(sa)
   if (hdv) {

@@ -3,14 +3,17 @@
     python -m paper_2501_06872_gb300.selector_train --out DIR [--graphs 256 --train 192]
 
 1. Dataset: `graphs` seeded R-MAT graphs with a ~ U[0.25, 0.70],
-   b = c = (1 - a - d) / 2, d = 0.05, scale ~ U{18..26}, edge factor ~
-   U{8..32}, vertex order degree-sorted or seeded-random, weighted or not.
+   b = c = (1 - a - d) / 2, d = 0.05, scale ~ U{18..28}, edge factor ~
+   U{8..32} (at most 2^(32 - scale)), vertex order degree-sorted or
+   seeded-random, weighted or not.
    For each: the features (gt_graph_features) and the exhaustive autotuner's
    table (gt_plan_tune, every grid point timed with CUDA events, median of 3),
    plus the analytic model's and the default configuration's grid points.
-2. Training: targets are log-regrets ln(t_i / min_j t_j) per grid point; the
-   network (gt_selector, GPU forward/backward/Adam) fits them with a masked
-   MSE, full batch, on the first `train` graphs.
+2. Training: grid points that run the same kernel sequence on a graph (radix
+   digit caps with the same pass count) share one time; targets are
+   log-regrets ln(t_i / min_j t_j) per grid point; the network (gt_selector,
+   GPU forward/backward/Adam with an L2 penalty) fits them with a masked MSE,
+   full batch, on the first `train` graphs.
 3. Evaluation on the held-out graphs: time of the selected point over the
    best point (regret), for the learned, analytic and default choices.
 Writes dataset.npz, selector_params.f32 and selector_report.json into --out.
@@ -31,17 +34,23 @@ D_PARAM = 0.05
 
 
 def graph_spec(i: int, seed: int = 0x5EED0005):
+    """Scales 18-28 (the headline graph's scale included); edge factors 8-32,
+    capped so that m <= 2^32 (the weighted limit): at most 32 at scale 27 and
+    16 at scale 28."""
     rng = np.random.default_rng([seed, i])
     a = float(rng.uniform(0.25, 0.70))
     b = (1.0 - a - D_PARAM) / 2.0
-    return {"a": a, "b": b, "c": b, "scale": int(rng.integers(18, 27)), "edge_factor": int(rng.integers(8, 33)),
+    scale = int(rng.integers(18, 29))
+    ef = int(rng.integers(8, 33))
+    ef = min(ef, 1 << (32 - scale))
+    return {"a": a, "b": b, "c": b, "scale": scale, "edge_factor": ef,
             "order": "degree" if rng.random() < 0.5 else "random", "weighted": bool(rng.random() < 0.5),
             "seed": int(seed + 1000 + i)}
 
 
 def _norm(c: dict) -> tuple:
     if c["method"] == 1:  # the bulk-staged kernel (tile 0) runs two 256-thread CTAs per SM whatever ctas_per_sm says
-        return (1, c["radix_tile"], c["ctas_per_sm"] if c["radix_tile"] else 0)
+        return (1, c["radix_tile"], c["ctas_per_sm"] if c["radix_tile"] else 0, c.get("radix_digit_bits", 0) or 8)
     return (0, c["hdv_k"], c["table_log2"], c["block_threads"], c["ctas_per_sm"], c["warp_edges"],
             c["stage_edges"], c["flags"])
 
@@ -102,6 +111,36 @@ def build_dataset(count: int, reps: int = 3, log=print, path=None):
     return np.stack(feats), np.stack(times), meta
 
 
+def effective_point(i: int, n: int):
+    """What grid point i runs on an n-column matrix: radix points with the same
+    tile kind (and CTAs per SM for register tiles) whose digit caps give the
+    same pass count are one kernel sequence (gt_plan_tune times them once)."""
+    from . import binding
+    c = binding.grid_config(i, n, 1 << 24).as_dict()
+    if c["method"] != 1:
+        return ("hlh", c["hdv_k"], c["table_log2"], c["block_threads"], c["ctas_per_sm"], c["warp_edges"],
+                c["stage_edges"], c["flags"])
+    bits = max(1, int(n - 1).bit_length())
+    cap = c["radix_digit_bits"] or 8
+    return ("radix", c["radix_tile"], c["ctas_per_sm"] if c["radix_tile"] else 0, -(-bits // cap))
+
+
+def merge_equivalent(times: np.ndarray, meta) -> np.ndarray:
+    """Gives grid points that run the same kernel sequence on a graph the
+    time of the first of them (datasets timed before gt_plan_tune merged them
+    hold separate, noisy timings of identical runs)."""
+    out = np.array(times, dtype=np.float64, copy=True)
+    for r, mt in enumerate(meta):
+        seen = {}
+        for i in range(out.shape[1]):
+            e = effective_point(i, int(mt["n"]))
+            if e in seen:
+                out[r, i] = out[r, seen[e]]
+            else:
+                seen[e] = i
+    return out
+
+
 def targets(times: np.ndarray):
     valid = times > 0
     best = np.where(valid, times, np.inf).min(axis=1, keepdims=True)
@@ -115,10 +154,10 @@ def standardise(x: np.ndarray):
     return mu.astype(np.float32), sd.astype(np.float32)
 
 
-def train(feats, times, steps=4000, lr=3e-3, seed=7, val=None, every=250, log=print):
-    """Full-batch Adam on the masked MSE of log-regrets.  With val = (features,
-    times), keeps the checkpoint (every `every` steps) of lowest mean
-    validation regret."""
+def train(feats, times, steps=3000, lr=1e-3, weight_decay=1e-3, seed=7, val=None, every=250, log=print):
+    """Full-batch Adam (with an L2 penalty on the weights) on the masked MSE
+    of log-regrets.  With val = (features, times), keeps the checkpoint (every
+    `every` steps) of lowest mean validation regret."""
     import torch
     from . import binding
     sel = binding.Selector(seed=seed)
@@ -140,7 +179,7 @@ def train(feats, times, steps=4000, lr=3e-3, seed=7, val=None, every=250, log=pr
     best = (np.inf, 0, sel.params())
     for it in range(1, steps + 1):
         sel.backward(X, T, M, loss=loss)
-        sel.adam_step(lr=lr)
+        sel.adam_step(lr=lr, weight_decay=weight_decay)
         if it % every == 0 or it == steps:
             torch.cuda.synchronize()
             rec = {"step": it, "loss": float(loss.item())}
@@ -198,7 +237,9 @@ def main():
     ap.add_argument("--out", required=True)
     ap.add_argument("--graphs", type=int, default=256)
     ap.add_argument("--train", type=int, default=192)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--weight-decay", type=float, default=1e-3)
     ap.add_argument("--val", type=int, default=32, help="training graphs held out for checkpoint choice")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--dataset", default=None, help="reuse a dataset.npz instead of timing")
@@ -217,8 +258,10 @@ def main():
         d = np.load(args.dataset, allow_pickle=False)
         feats, times = d["features"], d["times"]
         meta = json.loads(str(d["meta"]))
+        save_dataset(os.path.join(args.out, "dataset.npz"), list(feats), list(times), meta)
     else:
         feats, times, meta = build_dataset(args.graphs, args.reps, log, os.path.join(args.out, "dataset.npz"))
+    times = merge_equivalent(times, meta)
     tr = slice(0, args.train)
     te = slice(args.train, len(feats))
     fit = slice(0, args.train - args.val)
@@ -232,7 +275,8 @@ def main():
                 prev = json.load(open(old))
                 hist, chosen_step = prev.get("loss", []), prev.get("chosen_step")
     else:
-        params, hist, chosen_step = train(feats[fit], times[fit], steps=args.steps,
+        params, hist, chosen_step = train(feats[fit], times[fit], steps=args.steps, lr=args.lr,
+                                          weight_decay=args.weight_decay,
                                           val=(feats[va], times[va]) if args.val else None, log=log)
     params.astype("<f4").tofile(os.path.join(args.out, "selector_params.f32"))
     an = np.array([m["analytic"] for m in meta])
@@ -241,7 +285,8 @@ def main():
     idx_tr, _ = picks(params, feats[tr], an[tr])
     report = {
         "graphs": len(feats), "n_train": args.train, "n_test": len(feats) - args.train, "steps": args.steps,
-        "n_val": args.val, "chosen_step": chosen_step, "loss": hist,
+        "n_val": args.val, "chosen_step": chosen_step, "loss": hist, "lr": args.lr,
+        "weight_decay": args.weight_decay, "equivalent_points_merged": True,
         "test": {"learned": summary(regrets(times[te], idx_te)),
                  "analytic": summary(regrets(times[te], an[te])),
                  "default": summary(regrets(times[te], de[te])),

@@ -106,3 +106,11 @@ def test_roofline_uses_the_method_bytes_per_call():
     own = bench.radix_down_bytes_per_edge(True, bench.radix_passes(n)) * m + 8 * (n + 1) / bench.radix_passes(n)
     assert r["kernel_own"]["bytes_per_launch"] == int(own)
     assert r["traffic"] is None and r["dram_over_algorithmic"] is None
+
+
+def test_step3_imbalance_summary():
+    import bench
+    r = bench.step3_imbalance([1.0, 1.0, 2.0, 0.0])
+    assert r["partitions"] == 4 and r["idle_share"] == pytest.approx(1 - 1.0 / 2.0)
+    assert r["cv"] == pytest.approx(np.std([1, 1, 2, 0]) / 1.0)
+    assert bench.step3_imbalance([]) is None

@@ -390,3 +390,29 @@ def test_gpu_generated_scale16(kind, order, weighted):
     got = (out[0].cpu().numpy().view(np.uint64), out[1].cpu().numpy().view(np.uint32),
            None if vv is None else out[2].cpu().numpy())
     assert_same(got, exp)
+
+
+def test_step3_partition_times_are_recorded_and_change_no_byte():
+    """GT_FLAG_PARTITION_TIMES records each warp partition's Step 3 (the
+    scatter) start and end; the output stays the oracle's."""
+    from paper_2501_06872_gb300 import binding
+    n, rp, ci, vv = inputs.rmat_csr(17, 16, seed=5, order="random", weighted=True)
+    exp = oracle.transpose(rp, ci, vv)
+    rpd, cid, vvd = _to_dev(rp, ci, vv)
+    m = len(ci)
+    cfg = config(hdv_k=512, warp_edges=2048, flags=binding.FLAG_AGGREGATE | binding.FLAG_PARTITION_TIMES)
+    plan = binding.Plan(n, m, True, cfg)
+    cp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    ri = torch.empty(m, dtype=torch.int32, device="cuda")
+    vo = torch.empty(m, dtype=torch.float32, device="cuda")
+    plan.transpose(rpd, cid, vvd, cp, ri, vo)
+    plan.check()
+    t = np.array(plan.partition_times())
+    assert t.size == plan.stats()["partitions"] and (t >= 0).all() and t.max() > 0
+    assert_same((cp.cpu().numpy().view(np.uint64), ri.cpu().numpy().view(np.uint32), vo.cpu().numpy()), exp)
+    plan.close()
+    plan = binding.Plan(n, m, True, config(hdv_k=512))
+    with pytest.raises(binding.GtError) as e:
+        plan.partition_times()
+    assert e.value.code == 1
+    plan.close()

@@ -24,16 +24,13 @@ def test_grid_points_follow_the_documented_table(binding):
     n, m = 1 << 24, 16 << 24
     g = [binding.grid_config(i, n, m).as_dict() for i in range(binding.TUNE_GRID)]
     assert g[0]["method"] == 0 and g[0]["hdv_k"] == 0 and g[0]["flags"] & binding.FLAG_AGGREGATE
-    assert g[1]["hdv_k"] == 0 and not g[1]["flags"] & binding.FLAG_AGGREGATE
-    assert [g[i]["hdv_k"] for i in (2, 3, 5)] == [64, 512, 2048]
-    assert g[4]["hdv_k"] == 512 and g[4]["stage_edges"] == 1024
-    assert g[6]["warp_edges"] == 1024 and (g[7]["block_threads"], g[7]["ctas_per_sm"]) == (512, 2)
-    for i in range(2, 8):
-        assert g[i]["method"] == 0 and (1 << g[i]["table_log2"]) >= 2 * g[i]["hdv_k"]
-    assert [(g[i]["method"], g[i]["radix_tile"]) for i in range(8, 12)] == [(1, 0), (1, 4096), (1, 4096), (1, 2048)]
-    assert [g[i]["ctas_per_sm"] for i in (9, 10, 11)] == [2, 4, 4]
+    assert g[1]["method"] == 0 and g[1]["hdv_k"] == 512 and (1 << g[1]["table_log2"]) >= 2 * 512
+    radix = [(g[i]["method"], g[i]["radix_tile"], g[i]["ctas_per_sm"], g[i]["radix_digit_bits"]) for i in range(2, 12)]
+    assert radix == [(1, 0, 4, 8), (1, 0, 4, 7), (1, 0, 4, 6), (1, 4096, 2, 8), (1, 4096, 2, 7), (1, 4096, 3, 6),
+                     (1, 2048, 4, 8), (1, 2048, 4, 7), (1, 2048, 6, 8), (1, 2048, 6, 6)]
+    assert all(g[i]["hdv_k"] == 0 for i in range(2, 12))
     # an HDV count above n / 2 becomes 0 (the point equals Atomic GT)
-    assert binding.grid_config(5, 3000, 50000).hdv_k == 0
+    assert binding.grid_config(1, 1000, 50000).hdv_k == 0
     with pytest.raises(binding.GtError) as ei:
         binding.grid_config(binding.TUNE_GRID, n, m)
     assert ei.value.code == 1
@@ -56,16 +53,16 @@ def _features(coverage, same_line=0.0, weighted=True):
 def test_analytic_choice(binding):
     # far beyond L2 (scale 28): at the coverage R-MAT gives (a few % to ~40 %) streaming wins
     for c in (0.0, 0.25, 0.5):
-        assert binding.analytic_index(_features(c), 1 << 28, 1 << 32) == 8
+        assert binding.analytic_index(_features(c), 1 << 28, 1 << 32) == 2
     # an L2-resident graph: the HDV split pays once the HDVs cover most edges ...
-    assert binding.analytic_index(_features(0.9), 1000, 20000) == 3
+    assert binding.analytic_index(_features(0.9), 1000, 20000) == 1
     # ... and with no coverage its hash probes only add to Atomic GT, so the choice leaves HLH
-    assert binding.analytic_index(_features(0.0), 1000, 20000) != 3
+    assert binding.analytic_index(_features(0.0), 1000, 20000) != 1
     # more coverage never moves the choice from HLH back to another method
     picks = [binding.analytic_index(_features(c), 5000, 100000) for c in np.linspace(0, 1, 21)]
-    assert picks[-1] == 3 and picks[0] != 3
-    first = picks.index(3)
-    assert all(p == 3 for p in picks[first:])
+    assert picks[-1] == 1 and picks[0] != 1
+    first = picks.index(1)
+    assert all(p == 1 for p in picks[first:])
     lib = binding.load()
     idx = ctypes.c_uint32()
     assert lib.gt_tune_analytic(None, 10, 10, ctypes.byref(idx)) == 1

@@ -212,6 +212,11 @@ def test_adam_first_step_closed_form():
     assert np.allclose(p1, p - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
     p2, _, _ = so.adam(p, g, z, z, 1, lr, first=10)
     assert np.array_equal(p2[:10], p[:10])
+    # with an L2 penalty the step-1 direction is that of g + wd * p
+    wd = 0.3
+    p3, _, _ = so.adam(p, g, z, z, 1, lr, eps=eps, wd=wd)
+    gw = g + wd * p
+    assert np.allclose(p3, p - lr * gw / (np.abs(gw) + eps), rtol=0, atol=1e-15)
 
 
 def test_shipped_selector_report_reproduces_in_fp64():
@@ -225,7 +230,9 @@ def test_shipped_selector_report_reproduces_in_fp64():
     p = np.fromfile(os.path.join(root, "selector_params.f32"), dtype="<f4").astype(np.float64)
     assert p.size == so.layout()["total"]
     n_train = rep["n_train"]
-    f, t = d["features"][n_train:].astype(np.float64), d["times"][n_train:]
+    from paper_2501_06872_gb300 import selector_train as st
+    t_all = st.merge_equivalent(d["times"], json.loads(str(d["meta"])))
+    f, t = d["features"][n_train:].astype(np.float64), t_all[n_train:]
     y, _ = so.forward(p, f)
     idx = y.argmin(axis=1)
     # outside the trained range (widened by 5 % of its width) the analytic choice stands
@@ -263,8 +270,8 @@ def test_trainer_graph_specs_follow_the_stated_ranges():
     specs = [st.graph_spec(i) for i in range(256)]
     assert all(0.25 <= s["a"] <= 0.70 for s in specs)
     assert all(abs(s["b"] - (1 - s["a"] - 0.05) / 2) < 1e-12 and s["b"] == s["c"] for s in specs)
-    assert {s["scale"] for s in specs} <= set(range(18, 27))
-    assert all(8 <= s["edge_factor"] <= 32 for s in specs)
+    assert {s["scale"] for s in specs} <= set(range(18, 29)) and 28 in {s["scale"] for s in specs}
+    assert all(8 <= s["edge_factor"] <= 32 and s["edge_factor"] << s["scale"] <= 1 << 32 for s in specs)
     assert {s["order"] for s in specs} == {"degree", "random"}
     assert specs[3] == st.graph_spec(3)  # seeded
 
