@@ -495,15 +495,18 @@ def step3_imbalance(busy_ms):
             "cv": float(busy.std() / busy.mean()), "max_ms": float(busy.max()), "mean_ms": float(busy.mean())}
 
 
-def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1):
+def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, steal=False):
     """PoTra's own method (Algorithm 2, k = 512 HDVs, with the LDV list sort)
     on the same resident graph: per-step device time, per-step stage times,
-    and whether its output equals the default method's bytes."""
+    and whether its output equals the default method's bytes.  steal: the
+    two-phase Step 3 of Sec. V-F."""
     import torch
     from paper_2501_06872_gb300 import binding
     cfg = binding.default_config(n_cols, m)
     cfg.method, cfg.hdv_k, cfg.table_log2 = 0, 512, 10
-    cfg.flags |= binding.FLAG_PARTITION_TIMES  # Step 3's per-partition busy times (Sec. V-F imbalance)
+    cfg.flags |= binding.FLAG_PARTITION_TIMES  # Step 3's per-warp busy times (Sec. V-F imbalance)
+    if steal:
+        cfg.flags |= binding.FLAG_STEAL_TAILS
     plan = binding.Plan(n, m, weighted, cfg, n_cols=n_cols)
     cp = torch.empty(n_cols + 1, dtype=torch.int64, device="cuda")
     ri = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -662,6 +665,7 @@ def main():
     hlh = None
     if not args.no_hlh and rank == 0 and world == 1 and method == 1:
         hlh = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo))
+        hlh["two_phase_step3"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo), steal=True)
 
     e2e = None
     if not args.no_e2e and rank == 0:

@@ -107,6 +107,14 @@ typedef struct gt_config {
  * partition in Step 3, read with gt_plan_partition_times (Sec. V-F measures
  * Step 3's load imbalance between the threads' partitions). */
 #define GT_FLAG_PARTITION_TIMES 8u
+/* GT_METHOD_HLH: two-phase Step 3 (Sec. V-F).  Every warp partition is split
+ * into a head (80 % of its edges) and a tail whose HDV counts and insertion
+ * points Steps 1-2 keep apart; in Step 3 each warp scatters its own head, then
+ * warps claim the tails one at a time from an atomic counter, so warps that
+ * finish early take over the work of slow ones.  HDV slots stay deterministic
+ * (each range keeps its own insertion points); the output bytes do not change.
+ * Needs stage_edges == 0. */
+#define GT_FLAG_STEAL_TAILS 16u
 
 /* GT_METHOD_HLH: PoTra's hash-based LDV-HDV method (Algorithm 2; hdv_k = 0 is
  *   Atomic GT, Algorithm 1) with the LDV list sort.

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgt.so")
 GT_OK = 0
 STATUS = {0: "GT_OK", 1: "GT_ERR_INVALID_ARG", 2: "GT_ERR_OUT_OF_RANGE", 3: "GT_ERR_BAD_ROW_PTR",
           4: "GT_ERR_NO_MEMORY", 5: "GT_ERR_CUDA", 6: "GT_ERR_TIMEOUT", 7: "GT_ERR_UNSUPPORTED"}
-FLAG_AGGREGATE, FLAG_NO_GRAPH, FLAG_UNSORTED, FLAG_PARTITION_TIMES = 1, 2, 4, 8
+FLAG_AGGREGATE, FLAG_NO_GRAPH, FLAG_UNSORTED, FLAG_PARTITION_TIMES, FLAG_STEAL_TAILS = 1, 2, 4, 8, 16
 METHOD_HLH = 0
 METHOD_RADIX = 1
 

@@ -105,6 +105,7 @@ bool config_valid(const gt_config &c) {
   if (c.method > GT_METHOD_RADIX) return false;
   if (c.radix_tile != 0 && c.radix_tile != 2048 && c.radix_tile != 4096) return false;
   if (c.radix_digit_bits != 0 && (c.radix_digit_bits < 4 || c.radix_digit_bits > 8)) return false;
+  if ((c.flags & GT_FLAG_STEAL_TAILS) && c.stage_edges != 0) return false;  // the two phases use direct loads
   return true;
 }
 
@@ -146,6 +147,7 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   w.rG = (uint32_t)num_sms * c.ctas_per_sm;
   w.r_dcap = c.radix_digit_bits ? c.radix_digit_bits : 8u;
   w.ptimes = (c.flags & GT_FLAG_PARTITION_TIMES) ? 1 : 0;
+  w.steal = (c.flags & GT_FLAG_STEAL_TAILS) ? 1 : 0;
   if (w.method == GT_METHOD_RADIX) {
     w.kmax = 0;
     w.tlog2 = 0;
@@ -213,7 +215,7 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(deg, n * 4);
   GT_AL(scan_state, (size_t)w.ntiles * 8);
   GT_AL(cursor, n * 8);
-  GT_AL(hdv_cnt, (size_t)w.P * (w.kmax ? w.kmax : 1) * 4);
+  GT_AL(hdv_cnt, (size_t)w.P * (w.steal ? 2 : 1) * (w.kmax ? w.kmax : 1) * 4);
   GT_AL(hdv_ids, (w.kmax ? w.kmax : 1) * 4);
   GT_AL(hdv_start, (w.kmax ? w.kmax : 1) * 8);
   GT_AL(hkeys, T * 4);
@@ -227,6 +229,10 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(biglist, (size_t)w.big_cap * 4);
   GT_AL(scratch, m * (w.has_vals ? 8 : 4));
   if (w.ptimes) GT_AL(ptime, (size_t)w.P * 2 * 8);
+  if (w.steal) {
+    GT_AL(part2, ((size_t)w.P * 2 + 1) * 8);
+    GT_AL(steal_next, 4);
+  }
 #undef GT_AL
   if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
   if (cudaMemset(w.meta, 0, gt::kMetaCount * 4) != cudaSuccess) return GT_ERR_CUDA;
@@ -413,6 +419,7 @@ static gt_status shape_for(gt_plan plan, uint32_t n_rows, uint32_t n, uint64_t m
   w.r_bulk = t.r_bulk;
   w.r_dcap = t.r_dcap;
   w.ptimes = t.ptimes;
+  w.steal = t.steal;
   w.r_gap_cap = (uint32_t)(t.n / 1024 + 2) < w.r_gap_cap ? (uint32_t)(t.n / 1024 + 2) : w.r_gap_cap;
   return GT_OK;
 }

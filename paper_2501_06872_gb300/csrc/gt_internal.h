@@ -59,6 +59,9 @@ struct DevWork {
   uint32_t *cand = nullptr;                    // [kmax]
   uint32_t *ties = nullptr;                    // [kTieCap]
   uint32_t *biglist = nullptr;                 // [big_cap]
+  int steal = 0;                               // two-phase Step 3: heads, then tails claimed by free warps
+  unsigned long long *part2 = nullptr;         // [2P + 1] head / tail bounds (steal only)
+  uint32_t *steal_next = nullptr;              // [1] next tail to claim (steal only)
   int ptimes = 0;                              // record Step 3's per-partition start/end times
   unsigned long long *ptime = nullptr;         // [2 * P] global-timer ns (ptimes only)
   // HLH, [m] entries: weighted graphs keep LDV entries here as u64 (value bits

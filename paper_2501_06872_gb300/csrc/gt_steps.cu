@@ -270,6 +270,35 @@ __global__ void k_partition(const uint64_t *__restrict__ row_ptr, uint32_t n_row
   part[p] = b;
 }
 
+// Two-phase Step 3 (Sec. V-F): warp p's partition [part[p], part[p+1]) is
+// split into a head of 80 % of its edges and a tail, part2[2p], part2[2p+1],
+// part2[2p+2].  Where rows may not be split, the split moves to a row start
+// inside the partition.
+__global__ void k_split_tails(const uint64_t *__restrict__ row_ptr, uint32_t n_rows,
+                              const unsigned long long *__restrict__ part, uint32_t P, int allow_split,
+                              unsigned long long *part2) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > P) return;
+  if (p == P) {
+    part2[2 * (size_t)P] = part[P];
+    return;
+  }
+  const uint64_t e0 = part[p], e1 = part[p + 1];
+  uint64_t b = e1 > e0 ? e0 + ((e1 - e0) * 4) / 5 : e0;
+  if (!allow_split && b > e0 && b < e1) {
+    uint32_t lo = 0, hi = n_rows;  // the row holding edge b
+    while (hi - lo > 1) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      if (row_ptr[mid] <= b) lo = mid;
+      else hi = mid;
+    }
+    const uint64_t rs = row_ptr[lo];
+    b = rs >= e0 ? rs : min64(row_ptr[lo + 1], e1);
+  }
+  part2[2 * (size_t)p] = e0;
+  part2[2 * (size_t)p + 1] = b;
+}
+
 // ---------------------------------------------------------------------------
 // Step 1: in-degree count (Algorithm 2, Step 1).
 // ---------------------------------------------------------------------------
@@ -288,6 +317,7 @@ struct CountArgs {
   uint32_t *status;
   uint32_t stage_edges;
   int vec_ok;  // col_idx is 16-byte aligned
+  int steal;   // part holds 2P + 1 bounds: warp p counts ranges 2p and 2p + 1 separately
 };
 
 template <bool HDV, bool AGG>
@@ -330,9 +360,14 @@ __global__ void __launch_bounds__(1024) k_count(CountArgs a) {
   }
   __syncthreads();
   const uint32_t p = blockIdx.x * W + w;
-  const uint64_t e0 = a.part[p], e1 = a.part[p + 1];
   uint32_t *mycnt = cnt + w * a.kmax;
   uint32_t hdv_local = 0;
+  // the warp's partition, or with the two-phase Step 3 its head (80 %) and
+  // tail (20 %) as two ranges with separate HDV counts
+  const uint32_t nsub = a.steal ? 2u : 1u;
+  for (uint32_t sub = 0; sub < nsub; ++sub) {
+  const uint32_t sp = a.steal ? 2u * p + sub : p;
+  const uint64_t e0 = a.part[sp], e1 = a.part[sp + 1];
 
   if (!STAGED && !a.vec_ok) {
     for (uint64_t c = e0; c < e1; c += 32) {
@@ -426,7 +461,14 @@ __global__ void __launch_bounds__(1024) k_count(CountArgs a) {
   }
   __syncwarp();
   if (HDV) {
-    for (uint32_t h = lane; h < K; h += 32) a.hdv_cnt[(size_t)p * a.kmax + h] = mycnt[h];
+    for (uint32_t h = lane; h < K; h += 32) {
+      a.hdv_cnt[(size_t)sp * a.kmax + h] = mycnt[h];
+      mycnt[h] = 0u;
+    }
+    __syncwarp();
+  }
+  }  // ranges of the warp
+  if (HDV) {
     for (int o = 16; o > 0; o >>= 1) hdv_local += __shfl_xor_sync(kFull, hdv_local, o);
     if (lane == 0 && hdv_local) atomicAdd(&a.meta64[0], (unsigned long long)hdv_local);
   }
@@ -647,7 +689,13 @@ struct ScatterArgs {
   uint32_t *status;
   int flag_mode;
   uint32_t stage_edges;
-  unsigned long long *ptime;  // optional [2 * P]: global-timer ns at the start and end of each partition
+  unsigned long long *ptime;  // optional [2 * P]: global-timer ns at the start and end of each warp's work
+  // two-phase Step 3 (Sec. V-F): part holds the 2P + 1 head / tail bounds,
+  // hdv_off their insertion points; each warp does its head, then claims
+  // tails from *steal_next until all P are taken
+  int steal;
+  uint32_t P;
+  uint32_t *steal_next;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -675,16 +723,20 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
       hv[i] = a.hvals[i];
     }
     for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) hstart[i] = a.hdv_start[i];
-    for (uint32_t h = lane; h < K; h += 32) cur[w * a.kmax + h] = a.hdv_off[(size_t)p * a.kmax + h];
   }
   __syncthreads();
-  const uint64_t e0 = a.part[p], e1 = a.part[p + 1];
   if (a.ptime && lane == 0) a.ptime[2 * (size_t)p] = global_ns();
-  if (e0 >= e1) {
-    if (a.ptime && lane == 0) a.ptime[2 * (size_t)p + 1] = a.ptime[2 * (size_t)p];
-    return;
-  }
   uint32_t *mycur = cur + w * a.kmax;
+
+  // Range sp of the edge sequence, [part[sp], part[sp + 1]), with its own HDV
+  // insertion points: the warp's partition, or a head or tail of one.
+  auto process = [&](uint32_t sp) {
+  const uint64_t e0 = a.part[sp], e1 = a.part[sp + 1];
+  if (HDV) {
+    for (uint32_t h = lane; h < K; h += 32) mycur[h] = a.hdv_off[(size_t)sp * a.kmax + h];
+    __syncwarp();
+  }
+  if (e0 >= e1) return;
 
   // rows at both ends of the partition (they may be shared with neighbours)
   uint32_t row_first, row_last;
@@ -851,6 +903,20 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
       for (uint64_t i = waited; i < min64(waited + 2, ntile); ++i) mbar_wait(&bars[i & 1u], (uint32_t)((i >> 1) & 1u));
     }
   }
+  };  // process
+
+  if (!a.steal) {
+    process(p);
+  } else {
+    process(2 * p);  // phase 1: the head of the warp's own partition
+    for (;;) {       // phase 2: tails, claimed one at a time by whichever warp is free
+      uint32_t t = 0;
+      if (lane == 0) t = atomicAdd(a.steal_next, 1u);
+      t = __shfl_sync(kFull, t, 0);
+      if (t >= a.P) break;
+      process(2 * t + 1);
+    }
+  }
   if (a.ptime) {
     __syncwarp();
     if (lane == 0) a.ptime[2 * (size_t)p + 1] = global_ns();
@@ -960,14 +1026,21 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // unsorted output (GT_FLAG_UNSORTED): no LDV sort, no split-row tags
   const bool unsorted = (cfg.flags & GT_FLAG_UNSORTED) != 0;
   const int flag_mode = unsorted ? 0 : w.flag_mode;
-  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n_rows, w.m, w.P, w.psize,
-                                                    unsorted || w.flag_mode || !w.has_vals,
-                                                     w.part, w.status);
+  const int allow_split = unsorted || w.flag_mode || !w.has_vals;
+  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n_rows, w.m, w.P, w.psize, allow_split, w.part,
+                                                    w.status);
   nl += 2;  // partition + count
+  // two-phase Step 3: every partition split into a head and a tail, counted apart
+  const unsigned long long *ranges = w.part;
+  if (w.steal) {
+    k_split_tails<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n_rows, w.part, w.P, allow_split, w.part2);
+    ranges = w.part2;
+    ++nl;
+  }
 
   // Step 1
-  CountArgs ca{pb.col_idx, w.n, w.m, w.part, w.hkeys, w.hvals, w.tlog2, w.kmax, w.meta, w.deg, w.hdv_cnt,
-               w.meta64, w.status, w.stage_edges, (((uintptr_t)pb.col_idx) & 15u) == 0};
+  CountArgs ca{pb.col_idx, w.n, w.m, ranges, w.hkeys, w.hvals, w.tlog2, w.kmax, w.meta, w.deg, w.hdv_cnt,
+               w.meta64, w.status, w.stage_edges, (((uintptr_t)pb.col_idx) & 15u) == 0, w.steal};
   const uint32_t threads = w.W * 32;
   if (hdv) {
     if (w.staged) {
@@ -992,7 +1065,8 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // Step 2
   if (hdv) {
     dim3 b(32, 32);
-    k_hdv_colscan<<<(w.kmax + 31) / 32, b, 0, s>>>(w.hdv_cnt, w.P, w.kmax, w.meta, w.hdv_ids, w.deg, w.status);
+    k_hdv_colscan<<<(w.kmax + 31) / 32, b, 0, s>>>(w.hdv_cnt, w.steal ? 2 * w.P : w.P, w.kmax, w.meta, w.hdv_ids,
+                                                   w.deg, w.status);
   }
   k_scan<<<w.ntiles, kScanThreads, 0, s>>>(w.deg, w.n, w.n_rows, w.m, pb.row_ptr, pb.col_ptr, w.cursor,
                                            w.scan_state, w.meta, w.status);
@@ -1003,10 +1077,11 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
 
   // Step 3
   if (w.ptime && (err = cudaMemsetAsync(w.ptime, 0, (size_t)w.P * 16, s)) != cudaSuccess) return err;
-  ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n, w.n_rows, w.m,       w.part,   w.hkeys,
+  if (w.steal && (err = cudaMemsetAsync(w.steal_next, 0, 4, s)) != cudaSuccess) return err;
+  ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n, w.n_rows, w.m,       ranges,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
                  pb.col_ptr, pb.row_idx, pb.vals_out, unsorted ? nullptr : (unsigned long long *)w.scratch,
-                 w.status, flag_mode, w.stage_edges, w.ptime};
+                 w.status, flag_mode, w.stage_edges, w.ptime, w.steal, w.P, w.steal_next};
   const bool vals = pb.vals != nullptr;
 #define GT_SC(H, V, ST) k_scatter<H, V, ST><<<w.G, threads, w.smem_scatter, s>>>(sa)
   if (hdv) {

@@ -67,6 +67,8 @@ CONFIGS = {
     "hdv4096_w1024": dict(hdv_k=4096, table_log2=13, block_threads=128, ctas_per_sm=1, warp_edges=2048),
     "noagg_staged": dict(hdv_k=16, flags=0, stage_edges=128),
     "big_blocks": dict(hdv_k=128, block_threads=1024, ctas_per_sm=1, warp_edges=64),
+    "steal": dict(hdv_k=512, flags=1 | 16, warp_edges=512),  # two-phase Step 3 (GT_FLAG_STEAL_TAILS)
+    "steal_atomic": dict(hdv_k=0, flags=1 | 16, warp_edges=256),
     "radix": dict(method=1),  # bulk-copy staged downsweep
     "radix4096": dict(method=1, radix_tile=4096, ctas_per_sm=3),
     "radix2048": dict(method=1, radix_tile=2048, ctas_per_sm=6),
@@ -142,7 +144,7 @@ def test_long_parallel_edge_runs_in_split_rows():
     ci = np.concatenate(rows).astype(np.uint32)
     vv = rng.standard_normal(len(ci)).astype(np.float32)
     exp = oracle.transpose(rp, ci, vv)
-    for name in ["atomic", "hdv64", "noagg_staged", "radix"]:
+    for name in ["atomic", "hdv64", "noagg_staged", "radix", "steal", "steal_atomic"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**dict(CONFIGS[name], warp_edges=2048))), exp)
 
 
@@ -262,7 +264,7 @@ def _column_multisets(cp, ri, vo, n):
     return cols[o], ri[o], vb[o]
 
 
-@pytest.mark.parametrize("name", ["atomic", "hdv64", "hdv512_staged", "noagg_staged"])
+@pytest.mark.parametrize("name", ["atomic", "hdv64", "hdv512_staged", "noagg_staged", "steal"])
 def test_unsorted_mode_keeps_every_list_as_a_multiset(name):
     """GT_FLAG_UNSORTED (the paper's output, no LDV sort): col_ptr is exact and
     every list holds the oracle's (source, value) multiset."""
@@ -416,3 +418,24 @@ def test_step3_partition_times_are_recorded_and_change_no_byte():
         plan.partition_times()
     assert e.value.code == 1
     plan.close()
+
+
+@pytest.mark.parametrize("weighted", [True, False])
+def test_two_phase_step3_on_skewed_graphs(weighted):
+    """Two-phase Step 3 (heads by their own warps, tails claimed by free
+    warps) on R-MAT graphs in all vertex orders, with HDVs and without:
+    bit-exact, and its busy times are recorded per warp."""
+    from paper_2501_06872_gb300 import binding
+    for order in ("natural", "degree", "random"):
+        n, rp, ci, vv = inputs.rmat_csr(16, 16, seed=31, order=order, weighted=weighted)
+        exp = oracle.transpose(rp, ci, vv if weighted else None)
+        for k in (0, 512):
+            cfg = config(hdv_k=k, warp_edges=1024, flags=binding.FLAG_AGGREGATE | binding.FLAG_STEAL_TAILS)
+            assert_same(gpu_transpose(rp, ci, vv if weighted else None, cfg), exp)
+
+
+def test_two_phase_step3_rejects_staging():
+    from paper_2501_06872_gb300 import binding
+    with pytest.raises(binding.GtError) as e:
+        binding.Plan(1000, 20000, True, config(hdv_k=64, stage_edges=256, flags=1 | 16))
+    assert e.value.code == 1
