@@ -105,28 +105,30 @@ def kernel_source_sha(kernel):
     return h.hexdigest()[:16]
 
 
-def record_traffic(csv_path, kernel, workload, note):
+def record_traffic(csv_path, kernel, workload, note, scale=1.0):
     """Writes profiles/traffic.json's entry for (kernel, workload) from an ncu
     --csv capture of dram__bytes_read.sum and dram__bytes_write.sum (one or
-    more launches of the kernel): their per-launch average, stamped with the
-    hash of the kernel's current sources."""
+    more launches of the kernel): their per-launch average times `scale` (a
+    smaller case's capture scaled to the workload by the edges a launch
+    processes), stamped with the hash of the kernel's current sources."""
     import csv
     rows = [r for r in csv.reader(line for line in open(csv_path) if line.startswith('"'))]
     h = rows[0]
     ki, mi, ui, vi = h.index("ID"), h.index("Metric Name"), h.index("Metric Unit"), h.index("Metric Value")
     ni = h.index("Kernel Name")
-    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    units = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     per = {}
     for r in rows[1:]:
         if kernel in r[ni] and r[mi].startswith("dram__bytes"):
-            per[r[ki]] = per.get(r[ki], 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
+            per[r[ki]] = per.get(r[ki], 0.0) + float(r[vi].replace(",", "")) * units[r[ui]]
     if not per:
         raise SystemExit(f"no dram__bytes rows for {kernel} in {csv_path}")
-    vals = list(per.values())
+    vals = [v * scale for v in per.values()]
     out = os.path.join(ROOT, "profiles", "traffic.json")
     d = json.load(open(out)) if os.path.exists(out) else {}
     d[f"{kernel}@{workload}"] = {"dram_bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
-                                 "per_launch": vals, "source_sha": kernel_source_sha(kernel), "capture": note}
+                                 "per_launch": vals, "scale": scale, "source_sha": kernel_source_sha(kernel),
+                                 "capture": note}
     with open(out, "w") as fh:
         json.dump(d, fh, indent=1)
     print(json.dumps(d[f"{kernel}@{workload}"]))
@@ -563,9 +565,12 @@ def main():
     ap.add_argument("--ref-sample-edges", type=int, default=1 << 24)
     ap.add_argument("--record-traffic", nargs=3, metavar=("CSV", "KERNEL", "NOTE"), default=None,
                     help="write profiles/traffic.json's entry for KERNEL on --workload from an ncu CSV and exit")
+    ap.add_argument("--traffic-scale", type=float, default=1.0,
+                    help="with --record-traffic: scale factor from the captured case to --workload")
     args = ap.parse_args()
     if args.record_traffic:
-        record_traffic(args.record_traffic[0], args.record_traffic[1], args.workload, args.record_traffic[2])
+        record_traffic(args.record_traffic[0], args.record_traffic[1], args.workload, args.record_traffic[2],
+                       args.traffic_scale)
         return
 
     rank = int(os.environ.get("RANK", "0"))
