@@ -497,11 +497,20 @@ def step3_imbalance(busy_ms):
             "cv": float(busy.std() / busy.mean()), "max_ms": float(busy.max()), "mean_ms": float(busy.mean())}
 
 
-def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, steal=False):
+def partition_bits_for(n_cols):
+    """Bucket width of the partitioned (two-level) form: destination ranges of
+    at most 2^20 columns, whose in-degree counters, cursors and one partly
+    written sector per list (about 44 MB) stay in L2."""
+    kb = max(1, int(n_cols - 1).bit_length())
+    return min(8, max(1, kb - 20))
+
+
+def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, steal=False, partition_bits=0):
     """PoTra's own method (Algorithm 2, k = 512 HDVs, with the LDV list sort)
     on the same resident graph: per-step device time, per-step stage times,
     and whether its output equals the default method's bytes.  steal: the
-    two-phase Step 3 of Sec. V-F."""
+    two-phase Step 3 of Sec. V-F.  partition_bits: the partitioned
+    (two-level) form, bucketed by that many top destination bits first."""
     import torch
     from paper_2501_06872_gb300 import binding
     cfg = binding.default_config(n_cols, m)
@@ -509,6 +518,8 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, stea
     cfg.flags |= binding.FLAG_PARTITION_TIMES  # Step 3's per-warp busy times (Sec. V-F imbalance)
     if steal:
         cfg.flags |= binding.FLAG_STEAL_TAILS
+    if partition_bits:
+        cfg.partition_bits = partition_bits
     plan = binding.Plan(n, m, weighted, cfg, n_cols=n_cols)
     cp = torch.empty(n_cols + 1, dtype=torch.int64, device="cuda")
     ri = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -539,7 +550,8 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, stea
     torch.cuda.empty_cache()
     return {"method": "hlh", "value": m / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "warmup": warmup, "gt_config": cfg.as_dict(),
-            "stage_ms": {k: t[k] for k in ("sample_ms", "count_ms", "scan_ms", "scatter_ms", "sort_ms")},
+            "stage_ms": {k: t[k] for k in ("partition_ms", "sample_ms", "count_ms", "scan_ms", "scatter_ms",
+                                           "sort_ms")},
             "scatter_launch_ms": t["dominant_ms"], "hdv_selected": st["hdv_selected"],
             "step3_imbalance": step3_imbalance(pt),
             "coverage": st["hdv_edges"] / max(1, m), "identical_output": same,
@@ -642,6 +654,7 @@ def main():
 
     peak, peak_kind = load_peaks()
     method = plan.config().method
+    gt_config = plan.config().as_dict()
     stage_ms = {"count": timing["count_ms"], "scan": timing["scan_ms"], "scatter": timing["scatter_ms"],
                 "sort": timing["sort_ms"], "sample": timing["sample_ms"]}
     lit, withv = algorithmic_bytes(n, m, weighted, n_cols)
@@ -669,17 +682,27 @@ def main():
 
     hlh = None
     if not args.no_hlh and rank == 0 and world == 1 and method == 1:
+        # the legs need room next to the resident graph: the main plan's
+        # workspace is freed here and the end-to-end leg gets a fresh plan
+        plan.close()
+        plan = None
+        torch.cuda.empty_cache()
         hlh = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo))
         hlh["two_phase_step3"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo), steal=True)
+        hlh["partitioned"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo),
+                                     partition_bits=partition_bits_for(n_cols))
 
     e2e = None
     if not args.no_e2e and rank == 0:
         host = host_inputs(rp, ci, vv, n, m, weighted, n_cols)
         del rp, ci, vv, cp, ri, vo  # the end-to-end leg works from host memory only
+        if plan is None:
+            torch.cuda.empty_cache()
+            plan = binding.Plan(n, m, weighted, cfg, n_cols=n_cols)
         e2e = run_e2e(plan, host, n, m, weighted, args, n_cols)
         del host
-    gt_config = plan.config().as_dict()
-    plan.close()
+    if plan is not None:
+        plan.close()
     try:
         del rp, ci, vv, cp, ri, vo
     except NameError:

@@ -92,6 +92,17 @@ typedef struct gt_config {
                                  0 = 31                                                          */
     uint32_t radix_digit_bits;/* GT_METHOD_RADIX: widest digit of a pass, 4..8 (0 = 8): the
                                  passes are ceil(key bits / radix_digit_bits) equal digits   */
+    uint32_t partition_bits;  /* GT_METHOD_HLH: 0 = Steps 0-3 on the CSR as given; 1..8 = the
+                                 partitioned (two-level) form: the edges are first bucketed,
+                                 stably, by the top partition_bits bits of the destination
+                                 (2^partition_bits destination ranges, capped at the column
+                                 bits), then Steps 0-3 and the LDV sort run over the bucketed
+                                 edge list in ranges of warp_edges edges taken in order, so the
+                                 counters, cursors and partly written lists the GPU touches at
+                                 any time belong to a few destination ranges and stay in L2.
+                                 Needs stage_edges == 0 and no GT_FLAG_STEAL_TAILS; uses 12-16
+                                 more bytes per edge of workspace.  Same output bytes.
+                                 Weighted matrices with more than 2^31 rows run unpartitioned. */
 } gt_config;
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
@@ -150,6 +161,9 @@ typedef struct gt_timing {
     float dominant_ms; /* average duration of one launch of the dominant
                           kernel: the scatter (HLH) or a digit downsweep (radix) */
     uint32_t dominant_launches; /* launches averaged                        */
+    float partition_ms; /* partitioned HLH (gt_config.partition_bits > 0): the row
+                           expansion and the destination bucketing pass, which run
+                           before Step 0 (included in total_ms); else 0        */
 } gt_timing;
 
 typedef struct gt_plan_s *gt_plan;

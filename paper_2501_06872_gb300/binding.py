@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
                 ("sample_permille", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("method", ctypes.c_uint32), ("radix_tile", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("batch_key_bits", ctypes.c_uint32),
-                ("batch_edges_log2", ctypes.c_uint32), ("radix_digit_bits", ctypes.c_uint32)]
+                ("batch_edges_log2", ctypes.c_uint32), ("radix_digit_bits", ctypes.c_uint32),
+                ("partition_bits", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -60,7 +61,7 @@ class Timing(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_uint32), ("sample_ms", ctypes.c_float), ("count_ms", ctypes.c_float),
                 ("scan_ms", ctypes.c_float), ("scatter_ms", ctypes.c_float), ("sort_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("dominant_ms", ctypes.c_float),
-                ("dominant_launches", ctypes.c_uint32)]
+                ("dominant_launches", ctypes.c_uint32), ("partition_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

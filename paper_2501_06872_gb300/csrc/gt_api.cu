@@ -75,6 +75,7 @@ void drop_events(gt_plan p) {
   for (auto &e : p->events) {
     for (int i = 0; i < 6; ++i) cudaEventDestroy(e.ev[i]);
     for (int i = 0; i < 8; ++i) cudaEventDestroy(e.down[i]);
+    for (int i = 0; i < 2; ++i) cudaEventDestroy(e.part[i]);
   }
   p->events.clear();
   for (auto &h : p->host_events)
@@ -106,6 +107,10 @@ bool config_valid(const gt_config &c) {
   if (c.radix_tile != 0 && c.radix_tile != 2048 && c.radix_tile != 4096) return false;
   if (c.radix_digit_bits != 0 && (c.radix_digit_bits < 4 || c.radix_digit_bits > 8)) return false;
   if ((c.flags & GT_FLAG_STEAL_TAILS) && c.stage_edges != 0) return false;  // the two phases use direct loads
+  if (c.partition_bits > 8) return false;
+  // the partitioned form reads the bucketed arrays with direct loads, in ranges taken in order
+  if (c.partition_bits && c.method == GT_METHOD_HLH && (c.stage_edges != 0 || (c.flags & GT_FLAG_STEAL_TAILS)))
+    return false;
   return true;
 }
 
@@ -115,8 +120,19 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   w.kmax = (w.m > 0) ? c.hdv_k : 0;
   w.tlog2 = w.kmax ? c.table_log2 : 0;
   w.W = c.block_threads / 32;
+  // partitioned form: the top bits of the destination, at most all of them
+  w.part_bits = 0;
+  // (weighted matrices with more than 2^31 rows cannot tag split rows: they run unpartitioned)
+  if (c.method == GT_METHOD_HLH && c.partition_bits && w.m > 0 && !(w.has_vals && w.n_rows > 0x80000000u)) {
+    uint32_t kb = 0;
+    while (kb < 32 && (w.n - 1) >> kb) ++kb;
+    w.part_bits = c.partition_bits < kb ? c.partition_bits : kb;
+  }
   uint64_t want = (w.m + (uint64_t)w.W * c.warp_edges - 1) / ((uint64_t)w.W * c.warp_edges);
-  uint64_t cap = (uint64_t)num_sms * c.ctas_per_sm;
+  // one wave of warp partitions, except in the partitioned form: there every
+  // range of warp_edges edges is a partition of its own, and CTAs launched in
+  // order walk the bucketed edges front to back
+  uint64_t cap = w.part_bits ? ((1ull << 31) - 1) / w.W : (uint64_t)num_sms * c.ctas_per_sm;
   if (want < 1) want = 1;
   if (want > cap) want = cap;
   w.G = (uint32_t)want;
@@ -232,6 +248,17 @@ gt_status plan_alloc_ws(gt_plan p) {
   if (w.steal) {
     GT_AL(part2, ((size_t)w.P * 2 + 1) * 8);
     GT_AL(steal_next, 4);
+  }
+  if (w.part_bits) {  // bucketing pass: row sources, bucketed triples, digit tables
+    GT_AL(r_a_u, m * 4);
+    GT_AL(q_key, m * 4);
+    GT_AL(q_u, m * 4);
+    if (w.has_vals) GT_AL(q_w, m * 4);
+    GT_AL(r_long, (m / 2049 + 1) * 4);
+    GT_AL(r_nlong, 4);
+    const size_t rows = (size_t)w.num_sms * 8u;
+    GT_AL(r_table, rows * 256 * 4);
+    GT_AL(r_offsets, rows * 256 * 8);
   }
 #undef GT_AL
   if (cudaMemset(w.status, 0, 4) != cudaSuccess) return GT_ERR_CUDA;
@@ -420,6 +447,7 @@ static gt_status shape_for(gt_plan plan, uint32_t n_rows, uint32_t n, uint64_t m
   w.r_dcap = t.r_dcap;
   w.ptimes = t.ptimes;
   w.steal = t.steal;
+  w.part_bits = t.part_bits;
   w.r_gap_cap = (uint32_t)(t.n / 1024 + 2) < w.r_gap_cap ? (uint32_t)(t.n / 1024 + 2) : w.r_gap_cap;
   return GT_OK;
 }
@@ -454,7 +482,10 @@ static gt_status transpose_impl(gt_plan plan, uint32_t n_rows, uint32_t n, uint6
       if (cudaEventCreate(&e.ev[i]) != cudaSuccess) return GT_ERR_CUDA;
     for (int i = 0; i < 8; ++i)
       if (cudaEventCreate(&e.down[i]) != cudaSuccess) return GT_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreate(&e.part[i]) != cudaSuccess) return GT_ERR_CUDA;
     e.ndown = 0;
+    e.has_part = 0;
     plan->events.push_back(e);
     ev = &plan->events.back();
   }
@@ -497,6 +528,7 @@ gt_status gt_plan_timing(gt_plan plan, gt_timing *t) {
   if (plan->events.empty()) return GT_OK;
   if (cudaEventSynchronize(plan->events.back().ev[5]) != cudaSuccess) return GT_ERR_CUDA;
   double acc[5] = {0, 0, 0, 0, 0};
+  double part = 0;
   double dom = 0;
   uint32_t ndom = 0;
   for (auto &e : plan->events) {
@@ -504,6 +536,11 @@ gt_status gt_plan_timing(gt_plan plan, gt_timing *t) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, e.ev[i], e.ev[i + 1]) != cudaSuccess) return GT_ERR_CUDA;
       acc[i] += ms;
+    }
+    if (e.has_part) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.part[0], e.part[1]) != cudaSuccess) return GT_ERR_CUDA;
+      part += ms;
     }
     if (e.ndown) {
       for (uint32_t i = 0; i + 1 < e.ndown; i += 2) {
@@ -528,7 +565,8 @@ gt_status gt_plan_timing(gt_plan plan, gt_timing *t) {
   t->sort_ms = (float)(acc[4] / c);
   t->dominant_ms = ndom ? (float)(dom / ndom) : 0.f;
   t->dominant_launches = ndom;
-  t->total_ms = (float)((acc[0] + acc[1] + acc[2] + acc[3] + acc[4]) / c);
+  t->partition_ms = (float)(part / c);
+  t->total_ms = (float)((acc[0] + acc[1] + acc[2] + acc[3] + acc[4] + part) / c);
   return GT_OK;
 }
 

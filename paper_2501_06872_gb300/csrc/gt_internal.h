@@ -82,6 +82,13 @@ struct DevWork {
   uint32_t *r_nlong = nullptr;                // [1] (zeroed per call)
   uint32_t *r_table = nullptr;                // [rG][256]
   unsigned long long *r_offsets = nullptr;    // [rG][256]
+  // partitioned HLH (part_bits > 0): the edges bucketed stably by the top
+  // part_bits bits of the destination, as (destination, source, value) arrays
+  // [m]; Steps 0-3 and the LDV sort read them in place of the CSR.  The row
+  // expansion writes its sources to r_a_u; r_long / r_nlong / r_table /
+  // r_offsets serve the bucketing pass.
+  uint32_t part_bits = 0;
+  uint32_t *q_key = nullptr, *q_u = nullptr, *q_w = nullptr;
 };
 
 struct Problem {
@@ -101,6 +108,8 @@ struct StepEvents {
   cudaEvent_t ev[6];
   cudaEvent_t down[8];  // radix: around each downsweep launch (up to 4 passes)
   uint32_t ndown = 0;
+  cudaEvent_t part[2];  // partitioned HLH: around the expansion and bucketing pass
+  int has_part = 0;
 };
 
 // Enqueues the whole transposition on `stream`.  Returns cudaSuccess or the
@@ -110,6 +119,11 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
 
 // Radix method: enqueues the row expansion, the digit passes and col_ptr
 // from the sorted keys (w.r_nlong and the gap count must be zeroed).
+// Partitioned HLH: expands the rows into w.r_a_u and buckets the edges stably
+// by the top w.part_bits bits of the destination (one digit pass of the radix
+// method) into w.q_key / w.q_u / w.q_w.  Reports bad row pointers and
+// out-of-range destinations in w.status.
+cudaError_t run_partition(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches);
 cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t stream, uint32_t *launches,
                       StepEvents *events);
 

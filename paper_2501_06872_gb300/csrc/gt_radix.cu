@@ -857,6 +857,48 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   return cudaGetLastError();
 }
 
+// Partitioned HLH: the destination-range bucketing of the two-level form.
+// One digit pass of the radix method on the top part_bits bits of the
+// destination, from the CSR (destinations, expanded sources, values) into
+// the bucketed arrays; being a stable counting sort on those bits, it keeps
+// every bucket in CSR order.
+cudaError_t run_partition(const DevWork &w, const Problem &pb, cudaStream_t s, uint32_t *launches) {
+  const uint64_t m = w.m;
+  const bool vals = pb.vals != nullptr;
+  uint32_t nl = 0;
+  const uint32_t bits = key_bits_of(w.n);
+  const uint32_t dbits = w.part_bits < bits ? w.part_bits : bits;
+  {  // source of every edge: rows [0, n_rows)
+    uint64_t warps = ((uint64_t)w.n_rows + 31) / 32;
+    uint32_t g = (uint32_t)min64((warps + 7) / 8, (uint64_t)w.num_sms * 16);
+    if (g == 0) g = 1;
+    const uint32_t long_cap = (uint32_t)(m / (kLongRow + 1) + 1);
+    k_expand_rows<<<g, 256, 0, s>>>(pb.row_ptr, w.n_rows, m, w.r_a_u, w.r_long, w.r_nlong, long_cap, w.status);
+    k_expand_long<<<w.num_sms * 4, 256, 0, s>>>(pb.row_ptr, w.r_long, w.r_nlong, long_cap, w.r_a_u);
+    nl += 2;
+  }
+  auto al16 = [](const void *p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
+  const bool bulk = al16(pb.col_idx) && al16(pb.vals);  // the plan's own arrays come from cudaMalloc
+  const uint32_t tile = bulk ? kBTile : kRThreads * 16u;
+  const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
+  const uint32_t G = (uint32_t)w.num_sms * 2u;  // the digit tables hold num_sms * 8 rows
+  const uint32_t sub = bulk ? 2u : 1u;
+  const uint32_t tpc = (ntiles + G - 1) / G;
+  RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, w.n, m, pb.col_idx, w.r_a_u, (const uint32_t *)pb.vals,
+               w.q_key, w.q_u, w.q_w, bits - dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status,
+               BatchView{}, sub};
+  k_radix_up<true, kPlain><<<G * sub, kRThreads, 0, s>>>(ra);
+  k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G * sub, w.r_offsets);
+  if (bulk) {
+    if (vals) k_radix_down_bulk<true, kPlain><<<G, kBThreads, bulk_dyn_smem(true), s>>>(ra);
+    else k_radix_down_bulk<false, kPlain><<<G, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+  } else {
+    launch_down(vals, 16u, G, (size_t)tile * 4 * (vals ? 3 : 2), s, ra);
+  }
+  nl += 3;
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // Batches (sub-batch of graphs laid out in union edge / vertex spaces)

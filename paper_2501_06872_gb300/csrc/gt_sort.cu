@@ -43,6 +43,9 @@ struct SortArgs {
   uint32_t *status;
   int flag_mode;
   uint32_t key_bits;  // bits of a row ID, the sort key (ceil(log2 n_rows))
+  // partitioned form: tagged entries carry their position in the bucketed
+  // edge list, whose values are qvals (null: a position inside the CSR row)
+  const float *qvals = nullptr;
 };
 
 struct WarpSync {
@@ -54,13 +57,18 @@ struct CtaSync {
 
 __device__ __forceinline__ uint32_t umask_of(const SortArgs &a) { return a.flag_mode ? ~kSplitFlag : 0xFFFFFFFFu; }
 
+// Value bits of a tagged entry of source u whose value slot holds pos.
+__device__ __forceinline__ uint32_t tagged_value(const SortArgs &a, uint32_t u, uint32_t pos) {
+  return __float_as_uint(a.qvals ? a.qvals[pos] : a.vals[a.row_ptr[u] + pos]);
+}
+
 // Writes one finished weighted entry (packed) to the outputs.
 __device__ __forceinline__ void emit_packed(const SortArgs &a, uint64_t slot, unsigned long long ent) {
   uint32_t u = (uint32_t)ent;
   uint32_t wb = (uint32_t)(ent >> 32);
   if (a.flag_mode && (u & kSplitFlag)) {
     u &= ~kSplitFlag;
-    wb = __float_as_uint(a.vals[a.row_ptr[u] + wb]);
+    wb = tagged_value(a, u, wb);
   }
   a.row_idx[slot] = u;
   a.vals_out[slot] = __uint_as_float(wb);
@@ -560,7 +568,7 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
       uint32_t wb = src.w[i];
       if (a.flag_mode && (u & kSplitFlag)) {
         u &= ~kSplitFlag;
-        wb = __float_as_uint(a.vals[a.row_ptr[u] + wb]);
+        wb = tagged_value(a, u, wb);
       }
       a.row_idx[s0 + i] = u;
       a.vals_out[s0 + i] = __uint_as_float(wb);
@@ -635,6 +643,7 @@ cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &p
   sa.status = w.status;
   sa.flag_mode = w.flag_mode;
   sa.key_bits = bits;
+  sa.qvals = w.part_bits ? (const float *)w.q_w : nullptr;
   // worklist regions inside biglist: mid | big | large
   sa.mid_cap = (uint32_t)(w.m / (kWarpSortCap + 1) + 1);
   sa.big_cap = (uint32_t)(w.m / (kMidCap + 1) + 1);

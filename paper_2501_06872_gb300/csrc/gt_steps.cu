@@ -270,6 +270,14 @@ __global__ void k_partition(const uint64_t *__restrict__ row_ptr, uint32_t n_row
   part[p] = b;
 }
 
+// Partitioned form: the bucketed edge list has no rows to respect, so warp p
+// owns the equal range [p * psize, (p + 1) * psize) (clipped to m); rows cut
+// by a boundary are handled as split rows.
+__global__ void k_partition_even(uint32_t P, uint64_t m, uint64_t psize, unsigned long long *part) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p <= P) part[p] = min64((uint64_t)p * psize, m);
+}
+
 // Two-phase Step 3 (Sec. V-F): warp p's partition [part[p], part[p+1]) is
 // split into a head of 80 % of its edges and a tail, part2[2p], part2[2p+1],
 // part2[2p+2].  Where rows may not be split, the split moves to a row start
@@ -696,6 +704,10 @@ struct ScatterArgs {
   int steal;
   uint32_t P;
   uint32_t *steal_next;
+  // partitioned form: the source of edge e is src[e] (the edge list is
+  // bucketed by destination, so there are no rows to search); split-row tags
+  // carry the edge's position e in the bucketed list
+  const uint32_t *src = nullptr;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -740,7 +752,10 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
 
   // rows at both ends of the partition (they may be shared with neighbours)
   uint32_t row_first, row_last;
-  {
+  if (a.src) {
+    row_first = a.src[e0];
+    row_last = a.src[e1 - 1];
+  } else {
     uint32_t lo = 0, hi = a.n_rows;
     while (hi - lo > 1) {
       uint32_t mid = lo + (hi - lo) / 2;
@@ -757,15 +772,24 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
     }
     row_last = lo;
   }
-  const uint64_t rs_first = a.row_ptr[row_first], rs_last = a.row_ptr[row_last];
-  const bool split_first = VALS && a.flag_mode && rs_first < e0;
-  const bool split_last = VALS && a.flag_mode && a.row_ptr[row_last + 1] > e1;
+  // a row run continues past an end of the range: in the bucketed list, the
+  // row's edges into one destination range are consecutive
+  const uint64_t rs_first = a.src ? 0 : a.row_ptr[row_first], rs_last = a.src ? 0 : a.row_ptr[row_last];
+  const bool split_first =
+      VALS && a.flag_mode && (a.src ? (e0 > 0 && a.src[e0 - 1] == row_first) : rs_first < e0);
+  const bool split_last =
+      VALS && a.flag_mode && (a.src ? (e1 < a.m && a.src[e1] == row_last) : a.row_ptr[row_last + 1] > e1);
   uint32_t u_lo = row_first;
 
   auto step = [&](uint64_t e, bool act, uint32_t v, float wv) {
-    uint32_t my_u = find_row(a.row_ptr, a.n_rows, u_lo, e, act, lane, a.status);
-    uint32_t last_lane = 31u - __clz(__ballot_sync(kFull, act) | 1u);
-    u_lo = __shfl_sync(kFull, my_u, last_lane);
+    uint32_t my_u;
+    if (a.src) {
+      my_u = act ? __ldcs(a.src + e) : 0u;
+    } else {
+      my_u = find_row(a.row_ptr, a.n_rows, u_lo, e, act, lane, a.status);
+      uint32_t last_lane = 31u - __clz(__ballot_sync(kFull, act) | 1u);
+      u_lo = __shfl_sync(kFull, my_u, last_lane);
+    }
     bool valid = act && v < a.n;
     int h = -1;
     if (HDV && valid && K) h = hdv_lookup(keys, hv, a.tlog2, v);
@@ -798,7 +822,7 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
         // LDV sort orders tagged duplicates by it and re-reads the value.
         if (a.col_ptr[v + 1] - a.col_ptr[v] >= 2) {
           uu |= kSplitFlag;
-          wbits = (uint32_t)(e - (my_u == row_first ? rs_first : rs_last));
+          wbits = a.src ? (uint32_t)e : (uint32_t)(e - (my_u == row_first ? rs_first : rs_last));
         }
       }
       if (VALS && ldv && a.ldv64) {  // sorted output: LDV entries wait in the scratch for the list sort
@@ -999,6 +1023,27 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   if ((err = cudaMemsetAsync(w.scan_state, 0, (size_t)w.ntiles * sizeof(unsigned long long), s)) != cudaSuccess)
     return err;
 
+  // Partitioned form: bucket the edges by destination range first; the steps
+  // below then read the bucketed (destination, source, value) list.
+  const uint32_t *e_dst = pb.col_idx;
+  const float *e_val = pb.vals;
+  const uint32_t *e_src = nullptr;
+  if (w.part_bits) {
+    if (ev) {
+      cudaEventRecord(ev->part[0], s);
+      ev->has_part = 1;
+    }
+    if ((err = cudaMemsetAsync(w.r_nlong, 0, 4, s)) != cudaSuccess) return err;
+    if ((err = run_partition(w, pb, s, &nl)) != cudaSuccess) return err;
+    if (ev) {
+      cudaEventRecord(ev->part[1], s);
+      cudaEventRecord(ev->ev[0], s);  // Step 0 starts here: sample_ms leaves the bucketing out
+    }
+    e_dst = w.q_key;
+    e_val = (const float *)w.q_w;
+    e_src = w.q_u;
+  }
+
   // Step 0
   if (hdv) {
     const uint32_t ts = 1u << w.ts_log2;
@@ -1008,7 +1053,7 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
     if (w.ns > 0) {
       uint32_t g = (w.ns + 255) / 256;
       if (g > 4096) g = 4096;
-      k_sample<<<g, 256, 0, s>>>(pb.col_idx, w.n, w.m, w.ns, cfg.seed, w.skeys, w.scnt, w.ts_log2);
+      k_sample<<<g, 256, 0, s>>>(e_dst, w.n, w.m, w.ns, cfg.seed, w.skeys, w.scnt, w.ts_log2);
     }
     uint32_t g2 = (ts + 255) / 256;
     if (g2 > 4096) g2 = 4096;
@@ -1027,8 +1072,11 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   const bool unsorted = (cfg.flags & GT_FLAG_UNSORTED) != 0;
   const int flag_mode = unsorted ? 0 : w.flag_mode;
   const int allow_split = unsorted || w.flag_mode || !w.has_vals;
-  k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n_rows, w.m, w.P, w.psize, allow_split, w.part,
-                                                    w.status);
+  if (w.part_bits)
+    k_partition_even<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(w.P, w.m, w.psize, w.part);
+  else
+    k_partition<<<(w.P + 1 + 255) / 256, 256, 0, s>>>(pb.row_ptr, w.n_rows, w.m, w.P, w.psize, allow_split, w.part,
+                                                      w.status);
   nl += 2;  // partition + count
   // two-phase Step 3: every partition split into a head and a tail, counted apart
   const unsigned long long *ranges = w.part;
@@ -1039,8 +1087,8 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   }
 
   // Step 1
-  CountArgs ca{pb.col_idx, w.n, w.m, ranges, w.hkeys, w.hvals, w.tlog2, w.kmax, w.meta, w.deg, w.hdv_cnt,
-               w.meta64, w.status, w.stage_edges, (((uintptr_t)pb.col_idx) & 15u) == 0, w.steal};
+  CountArgs ca{e_dst, w.n, w.m, ranges, w.hkeys, w.hvals, w.tlog2, w.kmax, w.meta, w.deg, w.hdv_cnt,
+               w.meta64, w.status, w.stage_edges, (((uintptr_t)e_dst) & 15u) == 0, w.steal};
   const uint32_t threads = w.W * 32;
   if (hdv) {
     if (w.staged) {
@@ -1078,10 +1126,10 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // Step 3
   if (w.ptime && (err = cudaMemsetAsync(w.ptime, 0, (size_t)w.P * 16, s)) != cudaSuccess) return err;
   if (w.steal && (err = cudaMemsetAsync(w.steal_next, 0, 4, s)) != cudaSuccess) return err;
-  ScatterArgs sa{pb.row_ptr, pb.col_idx, pb.vals,  w.n, w.n_rows, w.m,       ranges,   w.hkeys,
+  ScatterArgs sa{pb.row_ptr, e_dst, e_val,  w.n, w.n_rows, w.m,       ranges,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
                  pb.col_ptr, pb.row_idx, pb.vals_out, unsorted ? nullptr : (unsigned long long *)w.scratch,
-                 w.status, flag_mode, w.stage_edges, w.ptime, w.steal, w.P, w.steal_next};
+                 w.status, flag_mode, w.stage_edges, w.ptime, w.steal, w.P, w.steal_next, e_src};
   const bool vals = pb.vals != nullptr;
 #define GT_SC(H, V, ST) k_scatter<H, V, ST><<<w.G, threads, w.smem_scatter, s>>>(sa)
   if (hdv) {

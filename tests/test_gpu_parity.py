@@ -72,6 +72,11 @@ CONFIGS = {
     "radix": dict(method=1),  # bulk-copy staged downsweep
     "radix4096": dict(method=1, radix_tile=4096, ctas_per_sm=3),
     "radix2048": dict(method=1, radix_tile=2048, ctas_per_sm=6),
+    # partitioned (two-level) form: bucket by the top destination bits first
+    "part_atomic": dict(hdv_k=0, partition_bits=4),
+    "part_hdv64": dict(hdv_k=64, partition_bits=8, warp_edges=128),
+    "part_big": dict(hdv_k=512, partition_bits=2, block_threads=1024, ctas_per_sm=1, warp_edges=64),
+    "part_noagg": dict(hdv_k=16, flags=0, partition_bits=6),
 }
 
 
@@ -112,7 +117,8 @@ def test_random_graphs_all_configs(name, seed):
 def test_rmat_numpy_scale14(order):
     n, rp, ci, vv = inputs.rmat_csr(14, 16, seed=3, order=order, weighted=True)
     exp = oracle.transpose(rp, ci, vv)
-    for name in ["atomic", "hdv512_staged", "big_blocks", "radix", "radix4096", "radix2048"]:
+    for name in ["atomic", "hdv512_staged", "big_blocks", "radix", "radix4096", "radix2048", "part_atomic",
+                 "part_hdv64", "part_big"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
     assert_same(gpu_transpose(rp, ci, vv), exp)  # default configuration
 
@@ -144,7 +150,7 @@ def test_long_parallel_edge_runs_in_split_rows():
     ci = np.concatenate(rows).astype(np.uint32)
     vv = rng.standard_normal(len(ci)).astype(np.float32)
     exp = oracle.transpose(rp, ci, vv)
-    for name in ["atomic", "hdv64", "noagg_staged", "radix", "steal", "steal_atomic"]:
+    for name in ["atomic", "hdv64", "noagg_staged", "radix", "steal", "steal_atomic", "part_atomic", "part_hdv64"]:
         assert_same(gpu_transpose(rp, ci, vv, config(**dict(CONFIGS[name], warp_edges=2048))), exp)
 
 
@@ -191,7 +197,8 @@ def test_split_rows_with_parallel_edges():
     vv = rng.standard_normal(ci.size).astype(np.float32)
     exp = oracle.transpose(rp, ci, vv)
     for cfg in [config(hdv_k=0, warp_edges=64), config(hdv_k=8, warp_edges=128, stage_edges=128),
-                config(hdv_k=0, warp_edges=4096, block_threads=64), config(method=1)]:
+                config(hdv_k=0, warp_edges=4096, block_threads=64), config(method=1),
+                config(hdv_k=0, warp_edges=64, partition_bits=5), config(hdv_k=8, warp_edges=128, partition_bits=8)]:
         assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
 
 
@@ -207,7 +214,8 @@ def test_split_hub_rows_into_radix_lists():
     ci = np.concatenate(rows).astype(np.uint32)
     vv = rng.standard_normal(ci.size).astype(np.float32)
     exp = oracle.transpose(rp, ci, vv)
-    for cfg in [config(hdv_k=0, warp_edges=256), config(hdv_k=4, warp_edges=512, stage_edges=256), config(method=1)]:
+    for cfg in [config(hdv_k=0, warp_edges=256), config(hdv_k=4, warp_edges=512, stage_edges=256), config(method=1),
+                config(hdv_k=0, warp_edges=256, partition_bits=3), config(hdv_k=4, warp_edges=512, partition_bits=8)]:
         assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
     assert_same(gpu_transpose(rp, ci, None, config(hdv_k=0, warp_edges=256)), oracle.transpose(rp, ci, None))
 
@@ -221,11 +229,11 @@ def test_ragged_edge_counts_and_empty_rows():
         rp, ci, _ = inputs.csr_from_edges(n, src.astype(np.uint32), dst.astype(np.uint32))
         vv = key.standard_normal(m).astype(np.float32)
         exp = oracle.transpose(rp, ci, vv)
-        for name in ["atomic", "noagg_staged", "hdv512_staged", "radix"]:
+        for name in ["atomic", "noagg_staged", "hdv512_staged", "radix", "part_atomic", "part_hdv64"]:
             assert_same(gpu_transpose(rp, ci, vv, config(**CONFIGS[name])), exp)
 
 
-@pytest.mark.parametrize("name", ["atomic", "hdv64", "radix", "radix4096"])
+@pytest.mark.parametrize("name", ["atomic", "hdv64", "radix", "radix4096", "part_atomic", "part_hdv64"])
 def test_errors_are_reported_not_faulted(name):
     from paper_2501_06872_gb300 import binding
     cfg = config(**CONFIGS[name])
@@ -264,7 +272,8 @@ def _column_multisets(cp, ri, vo, n):
     return cols[o], ri[o], vb[o]
 
 
-@pytest.mark.parametrize("name", ["atomic", "hdv64", "hdv512_staged", "noagg_staged", "steal"])
+@pytest.mark.parametrize("name", ["atomic", "hdv64", "hdv512_staged", "noagg_staged", "steal", "part_atomic",
+                                  "part_hdv64"])
 def test_unsorted_mode_keeps_every_list_as_a_multiset(name):
     """GT_FLAG_UNSORTED (the paper's output, no LDV sort): col_ptr is exact and
     every list holds the oracle's (source, value) multiset."""
@@ -439,3 +448,47 @@ def test_two_phase_step3_rejects_staging():
     with pytest.raises(binding.GtError) as e:
         binding.Plan(1000, 20000, True, config(hdv_k=64, stage_edges=256, flags=1 | 16))
     assert e.value.code == 1
+
+
+def test_partitioned_form_rejects_staging_and_steal():
+    from paper_2501_06872_gb300 import binding
+    for bad in (dict(hdv_k=64, partition_bits=4, stage_edges=256), dict(hdv_k=64, partition_bits=4, flags=1 | 16),
+                dict(hdv_k=0, partition_bits=9)):
+        with pytest.raises(binding.GtError) as e:
+            binding.Plan(1000, 20000, True, config(**bad))
+        assert e.value.code == 1
+
+
+@pytest.mark.parametrize("weighted", [True, False])
+def test_partitioned_form_across_bucket_widths(weighted):
+    """The two-level form (bucket by the top destination bits, then Steps
+    0-3 over the bucketed list in ranges taken in order) on R-MAT graphs in
+    every vertex order, for every bucket width up to all the key bits: the
+    oracle's bytes, the bucketing time reported apart, and as many
+    partitions as ranges of warp_edges edges."""
+    from paper_2501_06872_gb300 import binding
+    for order in ("natural", "degree", "random"):
+        n, rp, ci, vv = inputs.rmat_csr(15, 16, seed=41, order=order, weighted=weighted)
+        vals = vv if weighted else None
+        exp = oracle.transpose(rp, ci, vals)
+        m = ci.size
+        for bits in (1, 5, 8):
+            for k in (0, 256):
+                cfg = config(hdv_k=k, warp_edges=512, partition_bits=bits)
+                assert_same(gpu_transpose(rp, ci, vals, cfg), exp)
+        # the timing split and the partition count through a plan
+        rpd, cid, vvd = _to_dev(rp, ci, vals)
+        plan = binding.Plan(n, m, weighted, config(hdv_k=256, warp_edges=512, partition_bits=8))
+        cp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        ri = torch.empty(m, dtype=torch.int32, device="cuda")
+        vo = torch.empty(m, dtype=torch.float32, device="cuda") if weighted else None
+        plan.enable_timing(True)
+        plan.transpose(rpd, cid, vvd, cp, ri, vo)
+        plan.check()
+        t = plan.timing()
+        st = plan.stats()
+        plan.close()
+        assert t["partition_ms"] > 0 and t["total_ms"] >= t["partition_ms"]
+        assert st["partitions"] >= m // 512  # one partition per range of warp_edges edges
+        assert_same((cp.cpu().numpy().view(np.uint64), ri.cpu().numpy().view(np.uint32),
+                     None if vo is None else vo.cpu().numpy()), exp)

@@ -51,6 +51,7 @@ CONFIGS = {
     "radix": dict(method=1),
     "radix4096": dict(method=1, radix_tile=4096, ctas_per_sm=3),
     "radix2048": dict(method=1, radix_tile=2048, ctas_per_sm=6),
+    "part_hdv64": dict(hdv_k=64, warp_edges=128, partition_bits=6),
 }
 
 
