@@ -29,6 +29,7 @@ WORKLOADS = {
     "rmat28-degree": ("rmat", 28, 16, "degree", True),
     "rmat28-random": ("rmat", 28, 16, "random", True),
     "rmat24-random": ("rmat", 24, 16, "random", False),
+    "rmat24-random-weighted": ("rmat", 24, 16, "random", True),
     "er24-random": ("er", 24, 16, "random", False),
     "rmat16": ("rmat", 16, 16, "natural", False),
     "rmat20-degree": ("rmat", 20, 16, "degree", True),
@@ -38,6 +39,7 @@ WORKLOADS = {
     "rmat25-degree": ("rmat", 25, 16, "degree", True),
     "rmat26-degree": ("rmat", 26, 16, "degree", True),
     "rmat27-degree": ("rmat", 27, 16, "degree", True),
+    "rmat26-random": ("rmat", 26, 16, "random", True),
     # rectangular sparse matrices from the scale-28 graph: rows merged by 2^r, columns by 2^c
     "rmat28-tall": ("rmat", 28, 16, "degree", True),   # 2^28 rows x 2^20 columns
     "rmat28-wide": ("rmat", 28, 16, "degree", True),   # 2^20 rows x 2^28 columns

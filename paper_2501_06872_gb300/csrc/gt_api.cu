@@ -137,6 +137,13 @@ gt_status derive_shape(gt::DevWork &w, const gt_config &c, int num_sms) {
   if (want > cap) want = cap;
   w.G = (uint32_t)want;
   w.P = w.G * w.W;
+  // more than 32 K partitions: the HDV insertion points are scanned in slices
+  // of at least 1024 partitions (at most 1024 slices)
+  w.hdv_q = 1;
+  if (w.P > 32768u) {
+    const uint32_t q = (w.P + 1023) / 1024;
+    w.hdv_q = q < 1024 ? q : 1024;
+  }
   w.psize = w.m ? (w.m + w.P - 1) / w.P : 1;
   if (w.psize == 0) w.psize = 1;
   w.staged = c.stage_edges ? 1 : 0;
@@ -233,6 +240,7 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(cursor, n * 8);
   GT_AL(hdv_cnt, (size_t)w.P * (w.steal ? 2 : 1) * (w.kmax ? w.kmax : 1) * 4);
   GT_AL(hdv_ids, (w.kmax ? w.kmax : 1) * 4);
+  if (w.hdv_q > 1 && w.kmax) GT_AL(hdv_psum, (size_t)w.hdv_q * w.kmax * 8);
   GT_AL(hdv_start, (w.kmax ? w.kmax : 1) * 8);
   GT_AL(hkeys, T * 4);
   GT_AL(hvals, T * 2);
@@ -448,6 +456,7 @@ static gt_status shape_for(gt_plan plan, uint32_t n_rows, uint32_t n, uint64_t m
   w.ptimes = t.ptimes;
   w.steal = t.steal;
   w.part_bits = t.part_bits;
+  w.hdv_q = t.hdv_q < w.hdv_q ? t.hdv_q : w.hdv_q;
   w.r_gap_cap = (uint32_t)(t.n / 1024 + 2) < w.r_gap_cap ? (uint32_t)(t.n / 1024 + 2) : w.r_gap_cap;
   return GT_OK;
 }

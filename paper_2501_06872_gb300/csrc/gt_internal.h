@@ -89,6 +89,11 @@ struct DevWork {
   // r_offsets serve the bucketing pass.
   uint32_t part_bits = 0;
   uint32_t *q_key = nullptr, *q_u = nullptr, *q_w = nullptr;
+  // HDV insertion points over many partitions: hdv_q > 1 slices of
+  // partitions, each slice's per-HDV total and then starting point in
+  // hdv_psum [hdv_q][kmax]
+  uint32_t hdv_q = 1;
+  unsigned long long *hdv_psum = nullptr;
 };
 
 struct Problem {

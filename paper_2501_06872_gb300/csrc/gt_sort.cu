@@ -81,20 +81,59 @@ __device__ __forceinline__ unsigned long long packed_key(const SortArgs &a, unsi
   return ((unsigned long long)(u & umask_of(a)) << 32) | (tag ? (uint32_t)(ent >> 32) : i);
 }
 
-template <typename K, typename P>
-__device__ __forceinline__ void warp_bitonic32(K &key, P &pay, uint32_t lane) {
+// Bitonic sort of S (a power of two, <= 32) keys in each aligned group of S
+// lanes: the groups sort independently (every exchange distance is < S), and
+// the last merge runs ascending in every group.
+template <uint32_t S, typename K, typename P>
+__device__ __forceinline__ void warp_bitonic_groups(K &key, P &pay, uint32_t lane) {
 #pragma unroll
-  for (uint32_t k = 2; k <= 32; k <<= 1) {
+  for (uint32_t k = 2; k <= S; k <<= 1) {
 #pragma unroll
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       K ok = __shfl_xor_sync(kFull, key, j);
       P op = __shfl_xor_sync(kFull, pay, j);
-      bool up = (lane & k) == 0;
+      bool up = (k == S) || (lane & k) == 0;
       bool lower = (lane & j) == 0;
       if ((lower == up) ? (ok < key) : (ok > key)) {
         key = ok;
         pay = op;
       }
+    }
+  }
+}
+
+// Sorts the lists of this warp's 32 destinations whose length L satisfies
+// lo < L <= S (2 <= L), 32 / S lists per step, one group of S lanes each.
+// todo: the lanes (destinations) whose list qualifies.
+template <bool VALS, uint32_t S>
+__device__ __forceinline__ void sort_short_lists(const SortArgs &a, uint32_t todo, uint64_t c0, uint64_t len,
+                                                 uint32_t lane) {
+  constexpr uint32_t G = 32 / S;
+  const uint32_t grp = lane / S, e = lane % S;
+  while (todo) {
+    uint32_t myj = 32;  // the destination lane whose list this group sorts (32: none)
+#pragma unroll
+    for (uint32_t q = 0; q < G; ++q) {
+      if (todo) {
+        const uint32_t j = __ffs(todo) - 1;
+        todo &= todo - 1;
+        if (grp == q) myj = j;
+      }
+    }
+    const uint64_t s0 = __shfl_sync(kFull, c0, myj & 31u);
+    uint32_t L = (uint32_t)__shfl_sync(kFull, len, myj & 31u);
+    if (myj == 32) L = 0;
+    const bool act = e < L;
+    if (VALS) {
+      unsigned long long ent = act ? a.ldv64[s0 + e] : 0ull;
+      unsigned long long key = act ? packed_key(a, ent, e) : ~0ull;
+      warp_bitonic_groups<S>(key, ent, lane);
+      if (act) emit_packed(a, s0 + e, ent);
+    } else {
+      uint32_t key = act ? a.row_idx[s0 + e] : 0xFFFFFFFFu;
+      uint32_t dummy = 0;
+      warp_bitonic_groups<S>(key, dummy, lane);
+      if (act) a.row_idx[s0 + e] = key;
     }
   }
 }
@@ -149,26 +188,12 @@ __global__ void __launch_bounds__(256) k_sort_small(SortArgs a) {
         else set_status(a.status, GT_ERR_UNSUPPORTED);
       }
     }
-    uint32_t todo = __ballot_sync(kFull, need && len <= kWarpSortCap);
     sorted_local += __popc(__ballot_sync(kFull, need));
-    while (todo) {
-      const uint32_t j = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint64_t s0 = __shfl_sync(kFull, c0, j);
-      const uint32_t L = (uint32_t)__shfl_sync(kFull, len, j);
-      const bool act = lane < L;
-      if (VALS) {
-        unsigned long long ent = act ? a.ldv64[s0 + lane] : 0ull;
-        unsigned long long key = act ? packed_key(a, ent, lane) : ~0ull;
-        warp_bitonic32(key, ent, lane);
-        if (act) emit_packed(a, s0 + lane, ent);
-      } else {
-        uint32_t key = act ? a.row_idx[s0 + lane] : 0xFFFFFFFFu;
-        uint32_t dummy = 0;
-        warp_bitonic32(key, dummy, lane);
-        if (act) a.row_idx[s0 + lane] = key;
-      }
-    }
+    // short lists several to a warp: groups of 4, 8, 16 or 32 lanes
+    sort_short_lists<VALS, 4>(a, __ballot_sync(kFull, need && len <= 4), c0, len, lane);
+    sort_short_lists<VALS, 8>(a, __ballot_sync(kFull, need && len > 4 && len <= 8), c0, len, lane);
+    sort_short_lists<VALS, 16>(a, __ballot_sync(kFull, need && len > 8 && len <= 16), c0, len, lane);
+    sort_short_lists<VALS, 32>(a, __ballot_sync(kFull, need && len > 16 && len <= kWarpSortCap), c0, len, lane);
   }
   if (lane == 0 && sorted_local) atomicAdd(&a.meta[kMetaSorted], sorted_local);
 }
@@ -182,7 +207,8 @@ __device__ __forceinline__ void smem_bitonic(unsigned long long *key, unsigned l
   for (uint32_t k = 2; k <= cap; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       for (uint32_t i = tid; i < cap / 2; i += nthreads) {
-        const uint32_t lo = 2 * j * (i / j) + (i % j);
+        // j is a power of two: the pair's lower index inserts a 0 bit at j
+        const uint32_t lo = ((i & ~(j - 1u)) << 1) | (i & (j - 1u));
         const uint32_t hi = lo + j;
         const bool up = (lo & k) == 0;
         if (VALS) {
@@ -495,11 +521,24 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
     const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
     const uint32_t nshift = shift + dbits;
     const bool more = ps + 1 < passes;
+    // pos / chunk by a multiply-high with a reciprocal rounded up (at most one
+    // too large, corrected below)
+    const uint32_t cmag = chunk > 1u ? 0xFFFFFFFFu / chunk + 1u : 0u;
+    // the next 32 entries are loaded while this step ranks and scatters
+    uint32_t u_n = 0u, w_n = 0u;
+    if (r0 + lane < r1) {
+      u_n = src.getu(r0 + lane);
+      if (VALS) w_n = src.getw(r0 + lane);
+    }
     for (uint32_t c = r0; c < r1; c += 32) {
       const uint32_t i = c + lane;
       const bool act = i < r1;
-      const uint32_t u = act ? src.getu(i) : 0u;
-      const uint32_t wv = (VALS && act) ? src.getw(i) : 0u;
+      const uint32_t u = u_n;
+      const uint32_t wv = w_n;
+      if (i + 32 < r1) {
+        u_n = src.getu(i + 32);
+        if (VALS) w_n = src.getw(i + 32);
+      }
       const uint32_t d = act ? (((u & umask) >> shift) & (nb - 1)) : nb;
       const uint32_t mm = __match_any_sync(kFull, d);
       const uint32_t rank = __popc(mm & lanemask_lt());
@@ -512,7 +551,11 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
         const uint32_t pos = base + rank;
         dst.u[pos] = u;
         if (VALS) dst.w[pos] = wv;
-        if (more) atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * 32 + min(pos / chunk, 31u)], 1u);
+        if (more) {
+          uint32_t q = chunk > 1u ? __umulhi(pos, cmag) : pos;
+          if (q * chunk > pos) --q;
+          atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * 32 + min(q, 31u)], 1u);
+        }
       }
     }
     __syncthreads();

@@ -525,6 +525,86 @@ __global__ void k_hdv_colscan(uint32_t *hdv_cnt, uint32_t P, uint32_t kmax, cons
   }
 }
 
+// The same scan for many partitions (the partitioned form has one per range
+// of warp_edges edges): grid (HDV groups of 32, Q slices of partitions).
+// k_hdv_slicesum writes each slice's total per HDV to psum[q][h];
+// k_hdv_slicescan turns them into slice starting points (one thread per HDV)
+// and writes the totals; k_hdv_sliceapply rewrites each slice's counts as
+// insertion points from its starting point.
+__device__ __forceinline__ void hdv_slice(uint32_t P, uint32_t Q, uint32_t &p0, uint32_t &p1) {
+  const uint32_t cq = (P + Q - 1) / Q;
+  const uint32_t q0 = min(blockIdx.y * cq, P), q1 = min(q0 + cq, P);
+  const uint32_t chunk = (q1 - q0 + 31) / 32;
+  p0 = min(q0 + threadIdx.y * chunk, q1);
+  p1 = min(p0 + chunk, q1);
+}
+
+__global__ void k_hdv_slicesum(const uint32_t *__restrict__ hdv_cnt, uint32_t P, uint32_t Q, uint32_t kmax,
+                               const uint32_t *__restrict__ meta, unsigned long long *psum) {
+  __shared__ uint64_t s[32][33];
+  const uint32_t x = threadIdx.x, y = threadIdx.y, h = blockIdx.x * 32 + x;
+  const bool act = h < meta[kMetaK];
+  uint32_t p0, p1;
+  hdv_slice(P, Q, p0, p1);
+  uint64_t sum = 0;
+  if (act)
+    for (uint32_t p = p0; p < p1; ++p) sum += hdv_cnt[(size_t)p * kmax + h];
+  s[y][x] = sum;
+  __syncthreads();
+  if (y == 0 && act) {
+    uint64_t t = 0;
+    for (uint32_t i = 0; i < 32; ++i) t += s[i][x];
+    psum[(size_t)blockIdx.y * kmax + h] = t;
+  }
+}
+
+__global__ void k_hdv_slicescan(unsigned long long *psum, uint32_t Q, uint32_t kmax, const uint32_t *__restrict__ meta,
+                                const uint32_t *__restrict__ hdv_ids, uint32_t *deg, uint32_t *status) {
+  const uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= meta[kMetaK]) return;
+  uint64_t run = 0;
+  for (uint32_t q = 0; q < Q; ++q) {
+    const size_t i = (size_t)q * kmax + h;
+    const uint64_t t = psum[i];
+    psum[i] = run;
+    run += t;
+  }
+  if (run > 0xFFFFFFFFull) set_status(status, GT_ERR_UNSUPPORTED);
+  deg[hdv_ids[h]] = (uint32_t)run;
+}
+
+__global__ void k_hdv_sliceapply(uint32_t *hdv_cnt, uint32_t P, uint32_t Q, uint32_t kmax,
+                                 const uint32_t *__restrict__ meta, const unsigned long long *__restrict__ psum) {
+  __shared__ uint64_t s[32][33];
+  const uint32_t x = threadIdx.x, y = threadIdx.y, h = blockIdx.x * 32 + x;
+  const bool act = h < meta[kMetaK];
+  uint32_t p0, p1;
+  hdv_slice(P, Q, p0, p1);
+  uint64_t sum = 0;
+  if (act)
+    for (uint32_t p = p0; p < p1; ++p) sum += hdv_cnt[(size_t)p * kmax + h];
+  s[y][x] = sum;
+  __syncthreads();
+  if (y == 0) {
+    uint64_t run = act ? psum[(size_t)blockIdx.y * kmax + h] : 0;
+    for (uint32_t i = 0; i < 32; ++i) {
+      const uint64_t t = s[i][x];
+      s[i][x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  if (act) {
+    uint64_t run = s[y][x];
+    for (uint32_t p = p0; p < p1; ++p) {
+      const size_t idx = (size_t)p * kmax + h;
+      const uint32_t c = hdv_cnt[idx];
+      hdv_cnt[idx] = (uint32_t)run;
+      run += c;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step 2b: single-pass decoupled look-back exclusive scan deg -> col_ptr
 // (Merrill & Garland 2016).  Tile status words pack a 2-bit flag (1 =
@@ -1113,8 +1193,17 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // Step 2
   if (hdv) {
     dim3 b(32, 32);
-    k_hdv_colscan<<<(w.kmax + 31) / 32, b, 0, s>>>(w.hdv_cnt, w.steal ? 2 * w.P : w.P, w.kmax, w.meta, w.hdv_ids,
-                                                   w.deg, w.status);
+    const uint32_t nranges = w.steal ? 2 * w.P : w.P;
+    if (w.hdv_q > 1) {  // many partitions: slice totals, their scan, then the slices
+      dim3 g((w.kmax + 31) / 32, w.hdv_q);
+      k_hdv_slicesum<<<g, b, 0, s>>>(w.hdv_cnt, nranges, w.hdv_q, w.kmax, w.meta, w.hdv_psum);
+      k_hdv_slicescan<<<(w.kmax + 255) / 256, 256, 0, s>>>(w.hdv_psum, w.hdv_q, w.kmax, w.meta, w.hdv_ids, w.deg,
+                                                          w.status);
+      k_hdv_sliceapply<<<g, b, 0, s>>>(w.hdv_cnt, nranges, w.hdv_q, w.kmax, w.meta, w.hdv_psum);
+      nl += 2;
+    } else {
+      k_hdv_colscan<<<(w.kmax + 31) / 32, b, 0, s>>>(w.hdv_cnt, nranges, w.kmax, w.meta, w.hdv_ids, w.deg, w.status);
+    }
   }
   k_scan<<<w.ntiles, kScanThreads, 0, s>>>(w.deg, w.n, w.n_rows, w.m, pb.row_ptr, pb.col_ptr, w.cursor,
                                            w.scan_state, w.meta, w.status);

@@ -492,3 +492,24 @@ def test_partitioned_form_across_bucket_widths(weighted):
         assert st["partitions"] >= m // 512  # one partition per range of warp_edges edges
         assert_same((cp.cpu().numpy().view(np.uint64), ri.cpu().numpy().view(np.uint32),
                      None if vo is None else vo.cpu().numpy()), exp)
+
+
+@pytest.mark.parametrize("steal", [False, True])
+def test_hdv_insertion_points_over_many_partitions(steal):
+    """More than 32 K warp partitions (the partitioned form's ranges of
+    warp_edges edges, or many small unpartitioned ones): the HDV insertion
+    points are scanned in slices of partitions, with the same bytes."""
+    from paper_2501_06872_gb300 import binding
+    n, rp, ci, vv = inputs.rmat_csr(16, 32, seed=43, order="degree", weighted=True)
+    exp = oracle.transpose(rp, ci, vv)
+    if steal:  # unpartitioned: 32 CTAs of 32 warps per SM, two ranges per warp
+        cfg = config(hdv_k=256, warp_edges=32, block_threads=1024, ctas_per_sm=32,
+                     flags=binding.FLAG_AGGREGATE | binding.FLAG_STEAL_TAILS)
+    else:
+        cfg = config(hdv_k=256, warp_edges=32, partition_bits=6)
+    from paper_2501_06872_gb300 import binding as b
+    plan = b.Plan(n, ci.size, True, cfg)
+    P = plan.stats()["partitions"]
+    plan.close()
+    assert P > 32768
+    assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
