@@ -277,6 +277,51 @@ __global__ void __launch_bounds__(kWarpThreads) k_sort_warp(SortArgs a) {
   }
 }
 
+// kMidCap+1..kCtaBitonicCap: one CTA per list, bitonic in shared memory
+// (longer big lists: k_sort_cta, a radix sort in shared memory).
+constexpr uint32_t kCtaBitonicCap = 1024;
+constexpr int kCtaThreads = 512;
+
+template <bool VALS>
+__global__ void __launch_bounds__(kCtaThreads) k_sort_cta_bitonic(SortArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (cta_status_set(a.status)) return;
+  __shared__ uint32_t s_item;
+  unsigned long long *key = (unsigned long long *)smem;
+  unsigned long long *pay = key + kCtaBitonicCap;
+  uint32_t *key32 = (uint32_t *)smem;
+  const uint32_t nbig = min(a.meta[kMetaBig], a.big_cap);
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaTicket], 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    __syncthreads();
+    if (it >= nbig) break;
+    const uint32_t v = a.biglist[it];
+    const uint64_t s0 = a.col_ptr[v];
+    const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
+    if (L > kCtaBitonicCap) continue;  // uniform: the radix kernel takes it
+    uint32_t cap = 512;
+    while (cap < L) cap <<= 1;
+    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+      if (VALS) {
+        unsigned long long ent = i < L ? a.ldv64[s0 + i] : 0ull;
+        key[i] = i < L ? packed_key(a, ent, i) : ~0ull;
+        pay[i] = ent;
+      } else {
+        key32[i] = i < L ? a.row_idx[s0 + i] : 0xFFFFFFFFu;
+      }
+    }
+    __syncthreads();
+    smem_bitonic<VALS>(key, pay, key32, cap, threadIdx.x, blockDim.x, CtaSync{});
+    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
+      if (VALS) emit_packed(a, s0 + i, pay[i]);
+      else a.row_idx[s0 + i] = key32[i];
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // > kSortSmemCap: stable LSD radix sort on the (tag-masked) source ID, one
 // CTA per list.  The list is cut into 32 contiguous warp ranges; per pass
@@ -610,10 +655,11 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
   }
 }
 
-// kMidCap+1..kSortSmemCap: one CTA of 1024 threads per list, the same stable
-// LSD radix sort on the source as the longest lists, with both buffers in
-// shared memory (about 1 warp instruction per entry and pass, against some
-// 35 per entry for a bitonic network over up to 2048 64-bit keys).
+// kCtaBitonicCap+1..kSortSmemCap: one CTA of 1024 threads per list, the same
+// stable LSD radix sort on the source as the longest lists, with both buffers
+// in shared memory (about 1 warp instruction per entry and pass, against some
+// 35 per entry for a bitonic network over 2048 64-bit keys; for lists up to
+// kCtaBitonicCap the network's lower fixed cost wins).
 template <bool VALS>
 __global__ void __launch_bounds__(kRadixThreads) k_sort_cta(SortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -625,7 +671,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_cta(SortArgs a) {
   uint32_t *by = bx + (VALS ? 2 : 1) * kSortSmemCap;  // buffer y
   const uint32_t nbig = min(a.meta[kMetaBig], a.big_cap);
   while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaTicket], 1u);
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaBigTicket2], 1u);
     __syncthreads();
     const uint32_t it = s_item;
     __syncthreads();
@@ -633,6 +679,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_cta(SortArgs a) {
     const uint32_t v = a.biglist[it];
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
+    if (L <= kCtaBitonicCap) continue;  // uniform: the bitonic kernel takes it
     const Buf x{bx, VALS ? bx + L : nullptr, nullptr}, y{by, VALS ? by + L : nullptr, nullptr};
     if (VALS) {
       sort_list<VALS>(a, s0, L, Buf{nullptr, nullptr, a.ldv64 + s0}, x, y, words, sh);
@@ -643,6 +690,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_cta(SortArgs a) {
 }
 
 static size_t warp_smem_bytes(bool vals) { return (size_t)(kWarpThreads / 32) * kMidCap * (vals ? 16 : 4); }
+static size_t bitonic_smem_bytes(bool vals) { return (size_t)kCtaBitonicCap * (vals ? 16 : 4); }
 static size_t cta_smem_bytes(bool vals) { return (size_t)2 * 256 * 32 * 4 + (size_t)2 * kSortSmemCap * (vals ? 8 : 4); }
 static size_t radix_smem_bytes() { return (size_t)2 * 256 * 32 * 4; }
 
@@ -697,7 +745,10 @@ cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &p
   const uint32_t gw = (uint32_t)w.num_sms * 4u;
   if (vals) k_sort_warp<true><<<gw, kWarpThreads, warp_smem_bytes(true), s>>>(sa);
   else k_sort_warp<false><<<gw, kWarpThreads, warp_smem_bytes(false), s>>>(sa);
+  const uint32_t gb = (uint32_t)w.num_sms * 4u;
   const uint32_t gc = (uint32_t)w.num_sms * 2u;  // 2 CTAs of 1024 threads fit an SM
+  if (vals) k_sort_cta_bitonic<true><<<gb, kCtaThreads, bitonic_smem_bytes(true), s>>>(sa);
+  else k_sort_cta_bitonic<false><<<gb, kCtaThreads, bitonic_smem_bytes(false), s>>>(sa);
   if (vals) k_sort_cta<true><<<gc, kRadixThreads, cta_smem_bytes(true), s>>>(sa);
   else k_sort_cta<false><<<gc, kRadixThreads, cta_smem_bytes(false), s>>>(sa);
   const uint32_t gr = (uint32_t)w.num_sms * 2u;
