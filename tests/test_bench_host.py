@@ -114,3 +114,17 @@ def test_step3_imbalance_summary():
     assert r["partitions"] == 4 and r["idle_share"] == pytest.approx(1 - 1.0 / 2.0)
     assert r["cv"] == pytest.approx(np.std([1, 1, 2, 0]) / 1.0)
     assert bench.step3_imbalance([]) is None
+
+
+def test_partition_bits_keep_ranges_of_at_most_2_20_columns():
+    """The two-level form's bucket width: destination ranges of 2^20 columns,
+    between 1 and 8 bits (one digit pass)."""
+    assert bench.partition_bits_for(1 << 28) == 8
+    assert bench.partition_bits_for(1 << 24) == 4
+    assert bench.partition_bits_for((1 << 24) + 1) == 5
+    assert bench.partition_bits_for(1 << 20) == 1
+    assert bench.partition_bits_for(1000) == 1
+    assert bench.partition_bits_for(1 << 32) == 8
+    for n in (1 << 21, 3 << 22, 1 << 26):
+        d = bench.partition_bits_for(n)
+        assert (n - 1) >> d < (1 << 20) or d == 8
