@@ -30,7 +30,6 @@ enum MetaIdx : int {
   kMetaMidTicket = 11,
   kMetaLargeN = 12,      // lists for the radix sort
   kMetaLargeTicket = 13,
-  kMetaBigTicket2 = 14,  // work ticket of the shared-memory radix sort of big lists
   kMetaCount = 16
 };
 

@@ -201,9 +201,9 @@ __global__ void __launch_bounds__(256) k_sort_small(SortArgs a) {
 // ---------------------------------------------------------------------------
 // Bitonic network in shared memory over cap (power of two) elements.
 // ---------------------------------------------------------------------------
-template <bool VALS, typename Sync>
-__device__ __forceinline__ void smem_bitonic(unsigned long long *key, unsigned long long *pay, uint32_t *key32,
-                                             uint32_t cap, uint32_t tid, uint32_t nthreads, Sync sync) {
+template <typename K, bool PAY, typename Sync>
+__device__ __forceinline__ void smem_bitonic(K *key, unsigned long long *pay, uint32_t cap, uint32_t tid,
+                                             uint32_t nthreads, Sync sync) {
   for (uint32_t k = 2; k <= cap; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       for (uint32_t i = tid; i < cap / 2; i += nthreads) {
@@ -211,26 +211,195 @@ __device__ __forceinline__ void smem_bitonic(unsigned long long *key, unsigned l
         const uint32_t lo = ((i & ~(j - 1u)) << 1) | (i & (j - 1u));
         const uint32_t hi = lo + j;
         const bool up = (lo & k) == 0;
-        if (VALS) {
-          unsigned long long ka = key[lo], kb = key[hi];
-          if ((ka > kb) == up) {
-            key[lo] = kb;
-            key[hi] = ka;
-            unsigned long long t = pay[lo];
+        const K ka = key[lo], kb = key[hi];
+        if ((ka > kb) == up) {
+          key[lo] = kb;
+          key[hi] = ka;
+          if (PAY) {
+            const unsigned long long t = pay[lo];
             pay[lo] = pay[hi];
             pay[hi] = t;
-          }
-        } else {
-          uint32_t ka = key32[lo], kb = key32[hi];
-          if ((ka > kb) == up) {
-            key32[lo] = kb;
-            key32[hi] = ka;
           }
         }
       }
       sync();
     }
   }
+}
+
+// Sort key of an untagged weighted entry at list index i (< 2048): the
+// source above the index.  Sorting these keys alone leaves the entries in
+// place, to be picked up by index: half the shared-memory traffic of
+// moving (key, entry) pairs.
+constexpr uint32_t kIndexBits = 11;
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+__device__ __forceinline__ unsigned long long index_key(const SortArgs &a, unsigned long long ent, uint32_t i) {
+  return ((unsigned long long)((uint32_t)ent & umask_of(a)) << kIndexBits) | i;
+}
+
+// Compare-exchange of two elements, a at the lower index.
+template <typename K>
+__device__ __forceinline__ void ce_pair(K &a, K &b, bool up) {
+  const K lo = a < b ? a : b, hi = a < b ? b : a;
+  a = up ? lo : hi;
+  b = up ? hi : lo;
+}
+
+// The steps of bitonic merge k whose exchange distance stays inside one
+// warp's chunk of 32R consecutive elements, held as x[r] = element
+// ebase + 32r (ebase = chunk start + lane): distances >= 32 swap registers
+// of the lane, shorter ones shuffle between lanes.
+template <typename K, uint32_t R>
+__device__ __forceinline__ void reg_merge(K (&x)[R], uint32_t k, uint32_t ebase, uint32_t lane) {
+#pragma unroll
+  for (uint32_t j = 16 * R; j >= 1; j >>= 1) {
+    if (j >= k) continue;  // merge k has the steps k/2 ... 1
+    if (j >= 32) {
+#pragma unroll
+      for (uint32_t r = 0; r < R; ++r)
+        if ((r & (j >> 5)) == 0) ce_pair(x[r], x[r | (j >> 5)], ((ebase + 32 * r) & k) == 0);
+    } else {
+      const bool lower = (lane & j) == 0;
+#pragma unroll
+      for (uint32_t r = 0; r < R; ++r) {
+        const K o = __shfl_xor_sync(kFull, x[r], j);
+        const bool up = ((ebase + 32 * r) & k) == 0;
+        x[r] = (lower == up) ? (o < x[r] ? o : x[r]) : (o > x[r] ? o : x[r]);
+      }
+    }
+  }
+}
+
+// Bitonic sort of NW * 32R keys held by NW warps in registers (warp w holds
+// elements w * 32R ...).  Merge steps with distances of a whole chunk or
+// more (NW > 1 only) go through sk[] in shared memory, one barrier each; the
+// rest stay in registers.  On return x[r] holds sorted element w * 32R +
+// 32r + lane.
+template <typename K, uint32_t NW, uint32_t R, typename Sync>
+__device__ __forceinline__ void reg_bitonic(K (&x)[R], K *sk, uint32_t w, uint32_t lane, Sync sync) {
+  constexpr uint32_t C = 32 * R, N = NW * C;
+  const uint32_t ebase = w * C + lane;
+#pragma unroll 1
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    if (NW > 1 && k > C) {
+#pragma unroll
+      for (uint32_t r = 0; r < R; ++r) sk[ebase + 32 * r] = x[r];
+      sync();
+      for (uint32_t j = k >> 1; j >= C; j >>= 1) {
+        for (uint32_t i = w * 32 + lane; i < N / 2; i += NW * 32) {
+          const uint32_t lo = ((i & ~(j - 1u)) << 1) | (i & (j - 1u)), hi = lo + j;
+          const K ka = sk[lo], kb = sk[hi];
+          if ((ka > kb) == ((lo & k) == 0)) {
+            sk[lo] = kb;
+            sk[hi] = ka;
+          }
+        }
+        sync();
+      }
+#pragma unroll
+      for (uint32_t r = 0; r < R; ++r) x[r] = sk[ebase + 32 * r];
+    }
+    reg_merge<K, R>(x, k, ebase, lane);
+  }
+}
+
+// Sorts one list of L <= NW * 32R entries with the calling NW warps (warp w,
+// lane) and writes it to the outputs.  Weighted lists without split-row
+// tags sort (source, index) keys in registers and pick their entries from
+// pay[] by index; lists with tags order (key, entry) pairs in shared memory
+// (the tag's position breaks ties).  key / pay: NW * 32R u64 slots each.
+template <bool VALS, uint32_t NW, uint32_t R, typename Sync, typename AnyTag>
+__device__ __forceinline__ void reg_sort_list(const SortArgs &a, uint64_t s0, uint32_t L, unsigned long long *key,
+                                              unsigned long long *pay, uint32_t w, uint32_t lane, Sync sync,
+                                              AnyTag any_tag) {
+  constexpr uint32_t C = 32 * R, N = NW * C;
+  const uint32_t ebase = w * C + lane;
+  if (!VALS) {
+    uint32_t x[R];
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t e = ebase + 32 * r;
+      x[r] = e < L ? a.row_idx[s0 + e] : 0xFFFFFFFFu;
+    }
+    reg_bitonic<uint32_t, NW, R>(x, (uint32_t *)key, w, lane, sync);
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t e = ebase + 32 * r;
+      if (e < L) a.row_idx[s0 + e] = x[r];
+    }
+    sync();
+    return;
+  }
+  unsigned long long x[R];
+  bool tag = false;
+#pragma unroll
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t e = ebase + 32 * r;
+    x[r] = ~0ull;
+    if (e < L) {
+      const unsigned long long ent = a.ldv64[s0 + e];
+      pay[e] = ent;
+      tag |= a.flag_mode && ((uint32_t)ent & kSplitFlag);
+      x[r] = index_key(a, ent, e);
+    }
+  }
+  const bool any = any_tag(tag);
+  sync();
+  reg_bitonic<unsigned long long, NW, R>(x, key, w, lane, sync);
+  if (!any) {
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t e = ebase + 32 * r;
+      if (e < L) emit_packed(a, s0 + e, pay[(uint32_t)x[r] & kIndexMask]);
+    }
+    sync();
+    return;
+  }
+  // Split rows: the entries of one tagged source are parallel edges whose
+  // order is their position (value slot), not their slot index.  Each run of
+  // them in the sorted keys is put in position order by the thread at its
+  // start; a list with a run longer than 64 takes (key, entry) pairs through
+  // a shared-memory network instead.
+#pragma unroll
+  for (uint32_t r = 0; r < R; ++r) key[ebase + 32 * r] = x[r];
+  sync();
+  const uint32_t t = w * 32 + lane;
+  bool longrun = false;
+  for (uint32_t e = t; e < L; e += NW * 32) {
+    const uint64_t src_e = key[e] >> kIndexBits;
+    const unsigned long long ent = pay[(uint32_t)key[e] & kIndexMask];
+    if (!((uint32_t)ent & kSplitFlag) || (e > 0 && (key[e - 1] >> kIndexBits) == src_e)) continue;
+    uint32_t f = e + 1;
+    while (f < L && f - e <= 64 && (key[f] >> kIndexBits) == src_e) ++f;
+    if (f - e > 64) {
+      longrun = true;
+      continue;
+    }
+    for (uint32_t q = e + 1; q < f; ++q) {  // insertion sort by position
+      const unsigned long long kq = key[q];
+      const uint32_t pq = (uint32_t)(pay[(uint32_t)kq & kIndexMask] >> 32);
+      uint32_t z = q;
+      while (z > e && (uint32_t)(pay[(uint32_t)key[z - 1] & kIndexMask] >> 32) > pq) {
+        key[z] = key[z - 1];
+        --z;
+      }
+      key[z] = kq;
+    }
+  }
+  if (!any_tag(longrun)) {
+    sync();
+    for (uint32_t e = t; e < L; e += NW * 32) emit_packed(a, s0 + e, pay[(uint32_t)key[e] & kIndexMask]);
+  } else {
+    sync();
+    for (uint32_t i = t; i < N; i += NW * 32) {
+      key[i] = i < L ? packed_key(a, pay[i], i) : ~0ull;
+      if (i >= L) pay[i] = 0ull;
+    }
+    sync();
+    smem_bitonic<unsigned long long, true>(key, pay, N, t, NW * 32, sync);
+    for (uint32_t i = t; i < L; i += NW * 32) emit_packed(a, s0 + i, pay[i]);
+  }
+  sync();
 }
 
 constexpr int kWarpThreads = 256;
@@ -246,7 +415,6 @@ __global__ void __launch_bounds__(kWarpThreads) k_sort_warp(SortArgs a) {
   unsigned char *mine = smem + (size_t)w * kMidCap * per;
   unsigned long long *key = (unsigned long long *)mine;
   unsigned long long *pay = key + kMidCap;
-  uint32_t *key32 = (uint32_t *)mine;
   const uint32_t nmid = min(a.meta[kMetaMid], a.mid_cap);
   while (true) {
     uint32_t it = 0;
@@ -256,40 +424,26 @@ __global__ void __launch_bounds__(kWarpThreads) k_sort_warp(SortArgs a) {
     const uint32_t v = a.midlist[it];
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
-    uint32_t cap = 64;
-    while (cap < L) cap <<= 1;
-    for (uint32_t i = lane; i < cap; i += 32) {
-      if (VALS) {
-        unsigned long long ent = i < L ? a.ldv64[s0 + i] : 0ull;
-        key[i] = i < L ? packed_key(a, ent, i) : ~0ull;
-        pay[i] = ent;
-      } else {
-        key32[i] = i < L ? a.row_idx[s0 + i] : 0xFFFFFFFFu;
-      }
-    }
-    __syncwarp();
-    smem_bitonic<VALS>(key, pay, key32, cap, lane, 32, WarpSync{});
-    for (uint32_t i = lane; i < L; i += 32) {
-      if (VALS) emit_packed(a, s0 + i, pay[i]);
-      else a.row_idx[s0 + i] = key32[i];
-    }
-    __syncwarp();
+    auto any = [](bool x) { return __any_sync(kFull, x) != 0; };
+    if (L <= 64) reg_sort_list<VALS, 1, 2>(a, s0, L, key, pay, 0, lane, WarpSync{}, any);
+    else if (L <= 128) reg_sort_list<VALS, 1, 4>(a, s0, L, key, pay, 0, lane, WarpSync{}, any);
+    else reg_sort_list<VALS, 1, 8>(a, s0, L, key, pay, 0, lane, WarpSync{}, any);
   }
 }
 
-// kMidCap+1..kCtaBitonicCap: one CTA per list, bitonic in shared memory
-// (longer big lists: k_sort_cta, a radix sort in shared memory).
-constexpr uint32_t kCtaBitonicCap = 1024;
+// kMidCap+1..kSortSmemCap: one CTA of 16 warps per list, the bitonic
+// network in registers (2 or 4 keys per lane) with the cross-warp steps in
+// shared memory.
 constexpr int kCtaThreads = 512;
 
 template <bool VALS>
-__global__ void __launch_bounds__(kCtaThreads) k_sort_cta_bitonic(SortArgs a) {
+__global__ void __launch_bounds__(kCtaThreads) k_sort_cta(SortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (cta_status_set(a.status)) return;
   __shared__ uint32_t s_item;
   unsigned long long *key = (unsigned long long *)smem;
-  unsigned long long *pay = key + kCtaBitonicCap;
-  uint32_t *key32 = (uint32_t *)smem;
+  unsigned long long *pay = key + kSortSmemCap;
+  const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t nbig = min(a.meta[kMetaBig], a.big_cap);
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaTicket], 1u);
@@ -300,25 +454,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_sort_cta_bitonic(SortArgs a) {
     const uint32_t v = a.biglist[it];
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
-    if (L > kCtaBitonicCap) continue;  // uniform: the radix kernel takes it
-    uint32_t cap = 512;
-    while (cap < L) cap <<= 1;
-    for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
-      if (VALS) {
-        unsigned long long ent = i < L ? a.ldv64[s0 + i] : 0ull;
-        key[i] = i < L ? packed_key(a, ent, i) : ~0ull;
-        pay[i] = ent;
-      } else {
-        key32[i] = i < L ? a.row_idx[s0 + i] : 0xFFFFFFFFu;
-      }
-    }
-    __syncthreads();
-    smem_bitonic<VALS>(key, pay, key32, cap, threadIdx.x, blockDim.x, CtaSync{});
-    for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-      if (VALS) emit_packed(a, s0 + i, pay[i]);
-      else a.row_idx[s0 + i] = key32[i];
-    }
-    __syncthreads();
+    auto any = [](bool x) { return __syncthreads_or(x) != 0; };
+    if (L <= 1024) reg_sort_list<VALS, 16, 2>(a, s0, L, key, pay, w, lane, CtaSync{}, any);
+    else reg_sort_list<VALS, 16, 4>(a, s0, L, key, pay, w, lane, CtaSync{}, any);
   }
 }
 
@@ -453,11 +591,13 @@ __device__ void cta_sort_run(uint32_t *a, uint32_t *tmp, uint32_t len, uint32_t 
 // reads `src`; the passes then alternate between the views x and y.  Tagged
 // runs (split rows) are then ordered by their position in the row: a run of
 // <= 64 entries by the thread at its start, longer ones by the whole CTA.
-// words: the hist / next tables, [256][32] words each.
+// words: the hist / next tables, [256][kHistStride] words each.
 struct SortShared {
   uint32_t tagged, nlong;
   uint32_t long_i[kRadixThreads], long_n[kRadixThreads];
 };
+
+constexpr uint32_t kHistStride = 33;
 
 template <bool VALS>
 __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, const Buf x, const Buf y,
@@ -469,10 +609,12 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
   const uint32_t dbits = (bits + passes - 1) / passes;
   const uint32_t nb = 1u << dbits;
   const uint32_t chunk = (L + 31) / 32;
-  uint32_t *hist = words;             // [256][32]
-  uint32_t *next = words + 256 * 32;  // [256][32]
+  // per-(digit, warp) counters at d * kHistStride + w: lanes of one warp
+  // with different digits, and lanes of one digit row, fall in different banks
+  uint32_t *hist = words;                       // [256][kHistStride]
+  uint32_t *next = words + 256 * kHistStride;  // [256][kHistStride]
   // first pass's per-warp counts; notes whether any entry is tagged
-  for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) hist[i] = 0;
+  for (uint32_t i = threadIdx.x; i < 256 * kHistStride; i += blockDim.x) hist[i] = 0;
   if (threadIdx.x == 0) sh.tagged = 0;
   __syncthreads();
   {
@@ -481,7 +623,7 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
     for (uint32_t i = r0 + lane; i < r1; i += 32) {
       const uint32_t u = src.getu(i);
       anytag |= u & ~umask;
-      atomicAdd(&hist[(u & umask & (nb - 1)) * 32 + w], 1u);
+      atomicAdd(&hist[(u & umask & (nb - 1)) * kHistStride + w], 1u);
     }
     if (anytag) sh.tagged = 1;
   }
@@ -492,14 +634,14 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
     // exclusive scan over (digit, warp), digit-major: per-digit prefix over
     // warps, per-digit totals, prefix over digits, then combine
     for (uint32_t d = w; d < nb; d += 32) {
-      uint32_t xv = hist[d * 32 + lane];
+      uint32_t xv = hist[d * kHistStride + lane];
       uint32_t inc = xv;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         uint32_t yv = __shfl_up_sync(kFull, inc, o);
         if (lane >= (uint32_t)o) inc += yv;
       }
-      hist[d * 32 + lane] = inc - xv;
+      hist[d * kHistStride + lane] = inc - xv;
       if (lane == 31) next[d] = inc;  // digit total (next[] is cleared below)
     }
     __syncthreads();
@@ -518,9 +660,9 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
       }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nb * 32; i += blockDim.x) hist[i] += next[i >> 5];
+    for (uint32_t i = threadIdx.x; i < nb * 32; i += blockDim.x) hist[(i >> 5) * kHistStride + (i & 31u)] += next[i >> 5];
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) next[i] = 0;
+    for (uint32_t i = threadIdx.x; i < 256 * kHistStride; i += blockDim.x) next[i] = 0;
     __syncthreads();
     const uint32_t r0 = min(w * chunk, L), r1 = min(r0 + chunk, L);
     const uint32_t nshift = shift + dbits;
@@ -547,9 +689,9 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
       const uint32_t mm = __match_any_sync(kFull, d);
       const uint32_t rank = __popc(mm & lanemask_lt());
       uint32_t base = 0;
-      if (act) base = hist[d * 32 + w];
+      if (act) base = hist[d * kHistStride + w];
       __syncwarp();
-      if (act && rank == 0) hist[d * 32 + w] = base + __popc(mm);
+      if (act && rank == 0) hist[d * kHistStride + w] = base + __popc(mm);
       __syncwarp();
       if (act) {
         const uint32_t pos = base + rank;
@@ -558,7 +700,7 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
         if (more) {
           uint32_t q = chunk > 1u ? __umulhi(pos, cmag) : pos;
           if (q * chunk > pos) --q;
-          atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * 32 + min(q, 31u)], 1u);
+          atomicAdd(&next[(((u & umask) >> nshift) & (nb - 1)) * kHistStride + min(q, 31u)], 1u);
         }
       }
     }
@@ -655,44 +797,9 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
   }
 }
 
-// kCtaBitonicCap+1..kSortSmemCap: one CTA of 1024 threads per list, the same
-// stable LSD radix sort on the source as the longest lists, with both buffers
-// in shared memory (about 1 warp instruction per entry and pass, against some
-// 35 per entry for a bitonic network over 2048 64-bit keys; for lists up to
-// kCtaBitonicCap the network's lower fixed cost wins).
-template <bool VALS>
-__global__ void __launch_bounds__(kRadixThreads) k_sort_cta(SortArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  if (cta_status_set(a.status)) return;
-  __shared__ uint32_t s_item;
-  __shared__ SortShared sh;
-  uint32_t *words = (uint32_t *)smem;                // hist / next tables, 2 x [256][32]
-  uint32_t *bx = words + 2 * 256 * 32;               // buffer x: u[cap] (w[cap])
-  uint32_t *by = bx + (VALS ? 2 : 1) * kSortSmemCap;  // buffer y
-  const uint32_t nbig = min(a.meta[kMetaBig], a.big_cap);
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&a.meta[kMetaBigTicket2], 1u);
-    __syncthreads();
-    const uint32_t it = s_item;
-    __syncthreads();
-    if (it >= nbig) break;
-    const uint32_t v = a.biglist[it];
-    const uint64_t s0 = a.col_ptr[v];
-    const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
-    if (L <= kCtaBitonicCap) continue;  // uniform: the bitonic kernel takes it
-    const Buf x{bx, VALS ? bx + L : nullptr, nullptr}, y{by, VALS ? by + L : nullptr, nullptr};
-    if (VALS) {
-      sort_list<VALS>(a, s0, L, Buf{nullptr, nullptr, a.ldv64 + s0}, x, y, words, sh);
-    } else {
-      sort_list<VALS>(a, s0, L, Buf{a.row_idx + s0, nullptr, nullptr}, x, y, words, sh);
-    }
-  }
-}
-
 static size_t warp_smem_bytes(bool vals) { return (size_t)(kWarpThreads / 32) * kMidCap * (vals ? 16 : 4); }
-static size_t bitonic_smem_bytes(bool vals) { return (size_t)kCtaBitonicCap * (vals ? 16 : 4); }
-static size_t cta_smem_bytes(bool vals) { return (size_t)2 * 256 * 32 * 4 + (size_t)2 * kSortSmemCap * (vals ? 8 : 4); }
-static size_t radix_smem_bytes() { return (size_t)2 * 256 * 32 * 4; }
+static size_t cta_smem_bytes(bool vals) { return (size_t)kSortSmemCap * (vals ? 16 : 4); }
+static size_t radix_smem_bytes() { return (size_t)2 * 256 * kHistStride * 4; }
 
 cudaError_t configure_sort() {
   cudaError_t e[8] = {allow_max_dynamic_smem(k_sort_warp<true>),  allow_max_dynamic_smem(k_sort_warp<false>),
@@ -745,12 +852,9 @@ cudaError_t launch_sort(const DevWork &w, const gt_config &cfg, const Problem &p
   const uint32_t gw = (uint32_t)w.num_sms * 4u;
   if (vals) k_sort_warp<true><<<gw, kWarpThreads, warp_smem_bytes(true), s>>>(sa);
   else k_sort_warp<false><<<gw, kWarpThreads, warp_smem_bytes(false), s>>>(sa);
-  const uint32_t gb = (uint32_t)w.num_sms * 4u;
-  const uint32_t gc = (uint32_t)w.num_sms * 2u;  // 2 CTAs of 1024 threads fit an SM
-  if (vals) k_sort_cta_bitonic<true><<<gb, kCtaThreads, bitonic_smem_bytes(true), s>>>(sa);
-  else k_sort_cta_bitonic<false><<<gb, kCtaThreads, bitonic_smem_bytes(false), s>>>(sa);
-  if (vals) k_sort_cta<true><<<gc, kRadixThreads, cta_smem_bytes(true), s>>>(sa);
-  else k_sort_cta<false><<<gc, kRadixThreads, cta_smem_bytes(false), s>>>(sa);
+  const uint32_t gc = (uint32_t)w.num_sms * 4u;
+  if (vals) k_sort_cta<true><<<gc, kCtaThreads, cta_smem_bytes(true), s>>>(sa);
+  else k_sort_cta<false><<<gc, kCtaThreads, cta_smem_bytes(false), s>>>(sa);
   const uint32_t gr = (uint32_t)w.num_sms * 2u;
   if (vals) k_sort_radix<true><<<gr, kRadixThreads, radix_smem_bytes(), s>>>(sa);
   else k_sort_radix<false><<<gr, kRadixThreads, radix_smem_bytes(), s>>>(sa);

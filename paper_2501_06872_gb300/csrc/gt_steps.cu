@@ -1246,7 +1246,7 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   // LDV sort (it re-reads row_ptr, col_idx and vals for split rows)
   if (!unsorted) {
     err = launch_sort(w, cfg, pb, s);
-    nl += 5;
+    nl += 4;
   }
   if (err == cudaSuccess && pb.inputs_read) err = cudaEventRecord(pb.inputs_read, s);
   mark(5);
