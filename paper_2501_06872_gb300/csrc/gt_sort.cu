@@ -240,9 +240,10 @@ __device__ __forceinline__ unsigned long long index_key(const SortArgs &a, unsig
 // Compare-exchange of two elements, a at the lower index.
 template <typename K>
 __device__ __forceinline__ void ce_pair(K &a, K &b, bool up) {
-  const K lo = a < b ? a : b, hi = a < b ? b : a;
-  a = up ? lo : hi;
-  b = up ? hi : lo;
+  const bool sw = (b < a) == up;  // keys are distinct (padding aside, where either order is right)
+  const K t = a;
+  a = sw ? b : a;
+  b = sw ? t : b;
 }
 
 // The steps of bitonic merge k whose exchange distance stays inside one
@@ -263,8 +264,8 @@ __device__ __forceinline__ void reg_merge(K (&x)[R], uint32_t k, uint32_t ebase,
 #pragma unroll
       for (uint32_t r = 0; r < R; ++r) {
         const K o = __shfl_xor_sync(kFull, x[r], j);
-        const bool up = ((ebase + 32 * r) & k) == 0;
-        x[r] = (lower == up) ? (o < x[r] ? o : x[r]) : (o > x[r] ? o : x[r]);
+        const bool keep_min = lower == (((ebase + 32 * r) & k) == 0);
+        x[r] = ((o < x[r]) == keep_min) ? o : x[r];
       }
     }
   }
@@ -455,7 +456,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_sort_cta(SortArgs a) {
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
     auto any = [](bool x) { return __syncthreads_or(x) != 0; };
-    if (L <= 1024) reg_sort_list<VALS, 16, 2>(a, s0, L, key, pay, w, lane, CtaSync{}, any);
+    if (L <= 512) reg_sort_list<VALS, 16, 1>(a, s0, L, key, pay, w, lane, CtaSync{}, any);
+    else if (L <= 1024) reg_sort_list<VALS, 16, 2>(a, s0, L, key, pay, w, lane, CtaSync{}, any);
     else reg_sort_list<VALS, 16, 4>(a, s0, L, key, pay, w, lane, CtaSync{}, any);
   }
 }
