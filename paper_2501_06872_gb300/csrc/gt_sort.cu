@@ -81,23 +81,32 @@ __device__ __forceinline__ unsigned long long packed_key(const SortArgs &a, unsi
   return ((unsigned long long)(u & umask_of(a)) << 32) | (tag ? (uint32_t)(ent >> 32) : i);
 }
 
+// Sort key of an untagged weighted entry at list index i (< 2048): the
+// source above the index.  Sorting these keys alone leaves the entries in
+// place, to be picked up by index: half the shared-memory traffic of
+// moving (key, entry) pairs.
+constexpr uint32_t kIndexBits = 11;
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+__device__ __forceinline__ unsigned long long index_key(const SortArgs &a, unsigned long long ent, uint32_t i) {
+  return ((unsigned long long)((uint32_t)ent & umask_of(a)) << kIndexBits) | i;
+}
+
 // Bitonic sort of S (a power of two, <= 32) keys in each aligned group of S
 // lanes: the groups sort independently (every exchange distance is < S), and
 // the last merge runs ascending in every group.
-template <uint32_t S, typename K, typename P>
+template <uint32_t S, bool PAY, typename K, typename P>
 __device__ __forceinline__ void warp_bitonic_groups(K &key, P &pay, uint32_t lane) {
 #pragma unroll
   for (uint32_t k = 2; k <= S; k <<= 1) {
 #pragma unroll
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      K ok = __shfl_xor_sync(kFull, key, j);
-      P op = __shfl_xor_sync(kFull, pay, j);
-      bool up = (k == S) || (lane & k) == 0;
-      bool lower = (lane & j) == 0;
-      if ((lower == up) ? (ok < key) : (ok > key)) {
-        key = ok;
-        pay = op;
-      }
+      const K ok = __shfl_xor_sync(kFull, key, j);
+      P op = pay;
+      if (PAY) op = __shfl_xor_sync(kFull, pay, j);
+      const bool keep_min = ((lane & j) == 0) == ((k == S) || (lane & k) == 0);
+      const bool take = (ok < key) == keep_min;  // keys are distinct (padding aside)
+      key = take ? ok : key;
+      if (PAY) pay = take ? op : pay;
     }
   }
 }
@@ -126,13 +135,24 @@ __device__ __forceinline__ void sort_short_lists(const SortArgs &a, uint32_t tod
     const bool act = e < L;
     if (VALS) {
       unsigned long long ent = act ? a.ldv64[s0 + e] : 0ull;
-      unsigned long long key = act ? packed_key(a, ent, e) : ~0ull;
-      warp_bitonic_groups<S>(key, ent, lane);
-      if (act) emit_packed(a, s0 + e, ent);
+      const bool tagged = act && a.flag_mode && ((uint32_t)ent & kSplitFlag);
+      if (!__any_sync(kFull, tagged)) {
+        // sort (source, index) keys; each lane then fetches its entry from
+        // the lane that loaded it
+        unsigned long long key = act ? index_key(a, ent, e) : ~0ull;
+        uint32_t dummy = 0;
+        warp_bitonic_groups<S, false>(key, dummy, lane);
+        const unsigned long long got = __shfl_sync(kFull, ent, grp * S + ((uint32_t)key & (S - 1u)));
+        if (act) emit_packed(a, s0 + e, got);
+      } else {
+        unsigned long long key = act ? packed_key(a, ent, e) : ~0ull;
+        warp_bitonic_groups<S, true>(key, ent, lane);
+        if (act) emit_packed(a, s0 + e, ent);
+      }
     } else {
       uint32_t key = act ? a.row_idx[s0 + e] : 0xFFFFFFFFu;
       uint32_t dummy = 0;
-      warp_bitonic_groups<S>(key, dummy, lane);
+      warp_bitonic_groups<S, false>(key, dummy, lane);
       if (act) a.row_idx[s0 + e] = key;
     }
   }
@@ -227,15 +247,6 @@ __device__ __forceinline__ void smem_bitonic(K *key, unsigned long long *pay, ui
   }
 }
 
-// Sort key of an untagged weighted entry at list index i (< 2048): the
-// source above the index.  Sorting these keys alone leaves the entries in
-// place, to be picked up by index: half the shared-memory traffic of
-// moving (key, entry) pairs.
-constexpr uint32_t kIndexBits = 11;
-constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
-__device__ __forceinline__ unsigned long long index_key(const SortArgs &a, unsigned long long ent, uint32_t i) {
-  return ((unsigned long long)((uint32_t)ent & umask_of(a)) << kIndexBits) | i;
-}
 
 // Compare-exchange of two elements, a at the lower index.
 template <typename K>
