@@ -219,8 +219,10 @@ gt_status plan_alloc_ws(gt_plan p) {
   GT_AL(meta64, 4 * 8);
   if (w.method == GT_METHOD_RADIX) {  // col_ptr comes from the sorted keys: no degree array, no scan state
     GT_AL(r_a_key, m * 4);
-    GT_AL(r_a_u, m * 4);
-    if (w.has_vals) GT_AL(r_a_w, m * 4);
+    // weighted: one block, either (sources | values) as two u32 arrays or the
+    // interleaved (source, value) pairs of the bulk-staged passes
+    GT_AL(r_a_u, m * (w.has_vals ? 8 : 4));
+    if (w.has_vals) w.r_a_w = w.r_a_u + m;
     GT_AL(r_b_key, m * 4);
     GT_AL(r_long, (m / 2049 + 1) * 4);
     w.r_gap_cap = (uint32_t)(n / 1024 + 2);

@@ -445,9 +445,14 @@ constexpr uint32_t kBCtasPerSm = 2;  // registers (~120 x 256 threads) and 2 x ~
 __host__ __device__ constexpr uint32_t bulk_arrays(bool vals) { return vals ? 3u : 2u; }
 __host__ constexpr size_t bulk_dyn_smem(bool vals) { return (size_t)2 * bulk_arrays(vals) * kBTile * 4; }
 
-template <bool VALS, int MODE>
+// SVI / SVO (weighted plain passes only): the pass reads / writes (source,
+// value) as one interleaved u64 array at in_u / out_u instead of two u32
+// arrays: one bulk copy and one 8-byte store per edge for the pair.
+template <bool VALS, int MODE, bool SVI = false, bool SVO = false>
 __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(RadixArgs a) {
   static_assert(!loads_batch(MODE), "the bulk downsweep reads plain arrays");
+  static_assert(VALS || (!SVI && !SVO), "interleaved pairs carry values");
+  static_assert(MODE == kPlain || !SVO, "batches store through their descriptors");
   constexpr uint32_t NA = bulk_arrays(VALS);
   extern __shared__ __align__(128) uint32_t dsm[];  // buf[2][NA][TILE]
   __shared__ __align__(8) uint64_t bar[2];
@@ -476,8 +481,12 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
     const uint64_t e = t * kBTile;
     mbar_arrive_expect_tx(&bar[b], NA * kBTile * 4u);
     bulk_g2s(dst, a.in_key + e, kBTile * 4u, &bar[b]);
-    bulk_g2s(dst + kBTile, a.in_u + e, kBTile * 4u, &bar[b]);
-    if (VALS) bulk_g2s(dst + 2 * kBTile, a.in_w + e, kBTile * 4u, &bar[b]);
+    if (SVI) {
+      bulk_g2s(dst + kBTile, a.in_u + 2 * e, kBTile * 8u, &bar[b]);  // pairs land interleaved
+    } else {
+      bulk_g2s(dst + kBTile, a.in_u + e, kBTile * 4u, &bar[b]);
+      if (VALS) bulk_g2s(dst + 2 * kBTile, a.in_w + e, kBTile * 4u, &bar[b]);
+    }
   };
   if (tid == 0 && full(t0)) issue(t0, 0);
   // bit b: parity of buffer b's next phase
@@ -497,8 +506,12 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
     } else {  // the ragged last tile: plain loads (its buffer held tile t - 2, written out long ago)
       for (uint32_t j = tid; j < tcount; j += kBThreads) {
         bk[j] = __ldcs(a.in_key + tbase + j);
-        bu[j] = __ldcs(a.in_u + tbase + j);
-        if (VALS) bw[j] = __ldcs(a.in_w + tbase + j);
+        if (SVI) {
+          reinterpret_cast<uint2 *>(bu)[j] = __ldcs(reinterpret_cast<const uint2 *>(a.in_u) + tbase + j);
+        } else {
+          bu[j] = __ldcs(a.in_u + tbase + j);
+          if (VALS) bw[j] = __ldcs(a.in_w + tbase + j);
+        }
       }
       __syncthreads();
     }
@@ -514,8 +527,14 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
       const uint32_t j = w * (kBItems * 32) + i * 32 + lane;
       const bool act = j < tcount;
       key[i] = act ? bk[j] : 0u;
-      uu[i] = act ? bu[j] : 0u;
-      ww[i] = (VALS && act) ? bw[j] : 0u;
+      if (SVI) {
+        const uint2 p = act ? reinterpret_cast<const uint2 *>(bu)[j] : make_uint2(0u, 0u);
+        uu[i] = p.x;
+        ww[i] = p.y;
+      } else {
+        uu[i] = act ? bu[j] : 0u;
+        ww[i] = (VALS && act) ? bw[j] : 0u;
+      }
     }
 #pragma unroll
     for (int i = 0; i < kBItems; ++i) {
@@ -605,6 +624,8 @@ __global__ void __launch_bounds__(kBThreads, kBCtasPerSm) k_radix_down_bulk(Radi
         const uint64_t lp = sl.e0 + pos - sl.eoff[g];
         gd.row_idx[lp] = u;
         if (VALS) gd.vals_out[lp] = __uint_as_float(wv);
+      } else if (SVO) {
+        reinterpret_cast<uint2 *>(a.out_u)[pos] = make_uint2(u, wv);
       } else {
         a.out_u[pos] = u;
         if (VALS) a.out_w[pos] = wv;
@@ -762,10 +783,13 @@ cudaError_t configure_radix() {
   cudaError_t e[2] = {allow_down<8>(), allow_down<16>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
-  cudaError_t b[4] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
+  cudaError_t b[7] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
                       allow_max_dynamic_smem(k_radix_down_bulk<false, kPlain>),
                       allow_max_dynamic_smem(k_radix_down_bulk<true, kBatchLast>),
-                      allow_max_dynamic_smem(k_radix_down_bulk<false, kBatchLast>)};
+                      allow_max_dynamic_smem(k_radix_down_bulk<false, kBatchLast>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, false, true>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, true, false>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, true, true>)};
   for (cudaError_t x : b)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
@@ -793,6 +817,9 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   const uint32_t items = w.r_items;
   // buffers: A = (a_key, a_u, a_w); B = (b_key, row_idx, vals_out).  Pass p
   // writes B when (passes - p) is even, so the last pass writes the outputs.
+  // Weighted bulk passes keep A's (source, value) pairs interleaved in the
+  // a_u block (2m words): one 8-byte store per edge instead of two 4-byte
+  // ones, and one bulk copy per tile for the pair.
   uint32_t *b_u = pb.row_idx, *b_w = (uint32_t *)pb.vals_out;
   // bulk-staged downsweep: every array a pass reads must be 16-byte aligned
   auto al16 = [](const void *p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
@@ -821,8 +848,11 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     return cudaGetLastError();
   }
   const uint32_t *in_key = pb.col_idx, *in_u = src_rows, *in_w = (const uint32_t *)pb.vals;
+  const bool sv = bulk && vals;
+  bool in_sv = false;
   for (uint32_t p = 1; p <= passes; ++p) {
     const bool toB = ((passes - p) % 2) == 0;
+    const bool out_sv = sv && !toB;
     uint32_t *ok = toB ? w.r_b_key : w.r_a_key, *ou = toB ? b_u : w.r_a_u, *ow = toB ? b_w : w.r_a_w;
     RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, in_key, in_u, in_w, ok, ou, ow,
                  (p - 1) * dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status, BatchView{}, sub};
@@ -831,8 +861,12 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     k_radix_offsets<<<1, 1024, 0, s>>>(w.r_table, G * sub, w.r_offsets);
     if (ev && ev->ndown + 2 <= 8) cudaEventRecord(ev->down[ev->ndown], s);
     if (bulk) {
-      if (vals) k_radix_down_bulk<true, kPlain><<<G, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-      else k_radix_down_bulk<false, kPlain><<<G, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+      const size_t dsm = bulk_dyn_smem(vals);
+      if (!vals) k_radix_down_bulk<false, kPlain><<<G, kBThreads, dsm, s>>>(ra);
+      else if (in_sv && out_sv) k_radix_down_bulk<true, kPlain, true, true><<<G, kBThreads, dsm, s>>>(ra);
+      else if (in_sv) k_radix_down_bulk<true, kPlain, true, false><<<G, kBThreads, dsm, s>>>(ra);
+      else if (out_sv) k_radix_down_bulk<true, kPlain, false, true><<<G, kBThreads, dsm, s>>>(ra);
+      else k_radix_down_bulk<true, kPlain><<<G, kBThreads, dsm, s>>>(ra);
     } else {
       const size_t dsm = (size_t)tile * 4 * (vals ? 3 : 2);
       launch_down(vals, items, G, dsm, s, ra);
@@ -848,6 +882,7 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
     in_key = ok;
     in_u = ou;
     in_w = ow;
+    in_sv = out_sv;
   }
   uint32_t g = (uint32_t)min64((m + 255) / 256, (uint64_t)w.num_sms * 16);
   k_radix_colptr<false><<<g, 256, 0, s>>>(w.r_b_key, m, n, pb.col_ptr, w.r_gaps, w.r_gap_cap, w.status, BatchView{});
