@@ -220,9 +220,11 @@ gt_status plan_alloc_ws(gt_plan p) {
   if (w.method == GT_METHOD_RADIX) {  // col_ptr comes from the sorted keys: no degree array, no scan state
     GT_AL(r_a_key, m * 4);
     // weighted: one block, either (sources | values) as two u32 arrays or the
-    // interleaved (source, value) pairs of the bulk-staged passes
-    GT_AL(r_a_u, m * (w.has_vals ? 8 : 4));
-    if (w.has_vals) w.r_a_w = w.r_a_u + m;
+    // interleaved (source, value) pairs of the bulk-staged passes; the values
+    // start on a 16-byte boundary (bulk copies read them)
+    const size_t m4 = (m + 3) & ~(size_t)3;
+    GT_AL(r_a_u, w.has_vals ? m4 * 8 : m * 4);
+    if (w.has_vals) w.r_a_w = w.r_a_u + m4;
     GT_AL(r_b_key, m * 4);
     GT_AL(r_long, (m / 2049 + 1) * 4);
     w.r_gap_cap = (uint32_t)(n / 1024 + 2);

@@ -158,13 +158,17 @@ gt_status plan_build(gt_batch_plan p, int has_vals) {
   do {                                                                       \
     if ((st = balloc(p, (void **)&bw.field, (bytes))) != GT_OK) return st; \
   } while (0)
+  // weighted: each side is one block, (sources | values) as two u32 arrays
+  // or the interleaved (source, value) pairs of the middle passes
+  // (the value halves start on a 16-byte boundary: bulk copies read them)
+  const size_t M4 = (M + 3) & ~(size_t)3;
   GT_BA(a_key, M * 4);
-  GT_BA(a_u, M * 4);
+  GT_BA(a_u, has_vals ? M4 * 8 : M * 4);
   GT_BA(b_key, M * 4);
-  GT_BA(b_u, M * 4);
+  GT_BA(b_u, has_vals ? M4 * 8 : M * 4);
   if (has_vals) {
-    GT_BA(a_w, M * 4);
-    GT_BA(b_w, M * 4);
+    bw.a_w = bw.a_u + M4;
+    bw.b_w = bw.b_u + M4;
   }
   GT_BA(ucp, (NV + 1) * 8);
   const size_t rows = (size_t)bw.num_sms * 8u;  // bulk passes: 2 CTAs per SM x 2 upsweep CTAs (up to 4 x 2)

@@ -783,13 +783,14 @@ cudaError_t configure_radix() {
   cudaError_t e[2] = {allow_down<8>(), allow_down<16>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
-  cudaError_t b[7] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
+  cudaError_t b[8] = {allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain>),
                       allow_max_dynamic_smem(k_radix_down_bulk<false, kPlain>),
                       allow_max_dynamic_smem(k_radix_down_bulk<true, kBatchLast>),
                       allow_max_dynamic_smem(k_radix_down_bulk<false, kBatchLast>),
                       allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, false, true>),
                       allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, true, false>),
-                      allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, true, true>)};
+                      allow_max_dynamic_smem(k_radix_down_bulk<true, kPlain, true, true>),
+                      allow_max_dynamic_smem(k_radix_down_bulk<true, kBatchLast, true, false>)};
   for (cudaError_t x : b)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
@@ -1354,8 +1355,12 @@ cudaError_t run_radix_batch(const BatchWork &bw, uint32_t slot, cudaStream_t s, 
   const uint32_t ntb = (uint32_t)((M + kBTile - 1) / kBTile), tpcb = (ntb + Gb - 1) / Gb;
   uint32_t *gk = first_to_b ? bw.a_key : bw.b_key, *gw = vals ? (first_to_b ? bw.a_w : bw.b_w) : nullptr;
   const uint32_t *in_key = gk, *in_u = src_rows, *in_w = gw;
+  // weighted: the passes between the first and the last keep (source,
+  // value) pairs interleaved on both sides
+  bool in_sv = false;
   for (uint32_t p = 1; p <= passes; ++p) {
     const bool toB = ((passes - p) % 2) == 0;
+    const bool out_sv = vals && p < passes;
     uint32_t *ok = toB ? bw.b_key : bw.a_key, *ou = toB ? bw.b_u : bw.a_u, *ow = toB ? bw.b_w : bw.a_w;
     RadixArgs ra{nullptr, nullptr, nullptr, 0, M, in_key, in_u, in_w, ok, ou, ow,
                  (p - 1) * dbits, dbits, ntb, tpcb, kBTile, bw.table, bw.offsets, bw.status, bv, subb,
@@ -1364,15 +1369,19 @@ cudaError_t run_radix_batch(const BatchWork &bw, uint32_t slot, cudaStream_t s, 
     if (p == 1) k_radix_up<true, kBatchFirst><<<rows, kRThreads, 0, s>>>(ra);
     else k_radix_up<false, kPlain><<<rows, kRThreads, 0, s>>>(ra);
     k_radix_offsets<<<1, 1024, 0, s>>>(bw.table, rows, bw.offsets);
-    if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-    else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
-    else if (vals) k_radix_down_bulk<true, kPlain><<<Gb, kBThreads, bulk_dyn_smem(true), s>>>(ra);
-    else k_radix_down_bulk<false, kPlain><<<Gb, kBThreads, bulk_dyn_smem(false), s>>>(ra);
+    const size_t dsm = bulk_dyn_smem(vals);
+    if (p == passes && vals && in_sv) k_radix_down_bulk<true, kBatchLast, true, false><<<Gb, kBThreads, dsm, s>>>(ra);
+    else if (p == passes && vals) k_radix_down_bulk<true, kBatchLast><<<Gb, kBThreads, dsm, s>>>(ra);
+    else if (p == passes) k_radix_down_bulk<false, kBatchLast><<<Gb, kBThreads, dsm, s>>>(ra);
+    else if (vals && in_sv) k_radix_down_bulk<true, kPlain, true, true><<<Gb, kBThreads, dsm, s>>>(ra);
+    else if (vals) k_radix_down_bulk<true, kPlain, false, true><<<Gb, kBThreads, dsm, s>>>(ra);
+    else k_radix_down_bulk<false, kPlain><<<Gb, kBThreads, dsm, s>>>(ra);
     nl += 3;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     in_key = ok;
     in_u = ou;
     in_w = ow;
+    in_sv = out_sv;
   }
   // union col_ptr straight from the sorted keys (compact column space)
   const uint32_t gr = (uint32_t)min64((M + 255) / 256, (uint64_t)bw.num_sms * 16);
