@@ -226,6 +226,7 @@ gt_status plan_alloc_ws(gt_plan p) {
     GT_AL(r_a_u, w.has_vals ? m4 * 8 : m * 4);
     if (w.has_vals) w.r_a_w = w.r_a_u + m4;
     GT_AL(r_b_key, m * 4);
+    if (w.has_vals) GT_AL(r_b_sv, m4 * 8);
     GT_AL(r_long, (m / 2049 + 1) * 4);
     w.r_gap_cap = (uint32_t)(n / 1024 + 2);
     GT_AL(r_gaps, (1 + 2 * (size_t)w.r_gap_cap) * 8);

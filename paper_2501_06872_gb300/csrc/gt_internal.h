@@ -76,6 +76,8 @@ struct DevWork {
   uint32_t r_dcap = 8;                        // widest digit of a pass (4..8)
   uint32_t *r_a_key = nullptr, *r_a_u = nullptr, *r_a_w = nullptr;  // [m] ping buffer
   uint32_t *r_b_key = nullptr;                // [m] keys of the pong buffer (u/w live in the outputs)
+  uint32_t *r_b_sv = nullptr;                 // weighted: [2m] interleaved (source, value) pairs of the pong
+                                              // buffer's middle passes (the last pass writes the outputs)
   uint32_t *r_long = nullptr;                 // rows longer than the window expansion handles
   unsigned long long *r_gaps = nullptr;       // [1 + 2 * r_gap_cap]: count, then (lo << 32 | hi, value) ranges
   uint32_t r_gap_cap = 0;                     // long col_ptr ranges listed per call

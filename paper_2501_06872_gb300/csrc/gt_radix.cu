@@ -818,14 +818,15 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   const uint32_t items = w.r_items;
   // buffers: A = (a_key, a_u, a_w); B = (b_key, row_idx, vals_out).  Pass p
   // writes B when (passes - p) is even, so the last pass writes the outputs.
-  // Weighted bulk passes keep A's (source, value) pairs interleaved in the
-  // a_u block (2m words): one 8-byte store per edge instead of two 4-byte
-  // ones, and one bulk copy per tile for the pair.
+  // Weighted bulk passes keep (source, value) pairs interleaved, in the a_u
+  // block (2 round_up(m, 4) words) and in r_b_sv, except in the last pass's
+  // outputs: one 8-byte store per edge instead of two 4-byte ones, and one
+  // bulk copy per tile for the pair.
   uint32_t *b_u = pb.row_idx, *b_w = (uint32_t *)pb.vals_out;
   // bulk-staged downsweep: every array a pass reads must be 16-byte aligned
   auto al16 = [](const void *p) { return p == nullptr || (((uintptr_t)p) & 15u) == 0; };
   const bool bulk = w.r_bulk && al16(pb.col_idx) && al16(pb.vals) && al16(b_u) && al16(b_w) && al16(w.r_a_key) &&
-                    al16(w.r_a_u) && al16(w.r_a_w) && al16(w.r_b_key);
+                    al16(w.r_a_u) && al16(w.r_a_w) && al16(w.r_b_key) && al16(w.r_b_sv);
   const uint32_t tile = bulk ? kBTile : kRThreads * items;
   const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
   const uint32_t G = bulk ? (uint32_t)w.num_sms * kBCtasPerSm : w.rG;
@@ -853,8 +854,14 @@ cudaError_t run_radix(const DevWork &w, const Problem &pb, cudaStream_t s, uint3
   bool in_sv = false;
   for (uint32_t p = 1; p <= passes; ++p) {
     const bool toB = ((passes - p) % 2) == 0;
-    const bool out_sv = sv && !toB;
+    // interleaved pairs everywhere but the last pass's outputs (B's middle
+    // passes use their own pair buffer)
+    const bool out_sv = sv && p < passes && (!toB || w.r_b_sv);
     uint32_t *ok = toB ? w.r_b_key : w.r_a_key, *ou = toB ? b_u : w.r_a_u, *ow = toB ? b_w : w.r_a_w;
+    if (out_sv && toB) {
+      ou = w.r_b_sv;
+      ow = nullptr;
+    }
     RadixArgs ra{pb.row_ptr, pb.col_idx, pb.vals, n, m, in_key, in_u, in_w, ok, ou, ow,
                  (p - 1) * dbits, dbits, ntiles, tpc, tile, w.r_table, w.r_offsets, w.status, BatchView{}, sub};
     if (p == 1) k_radix_up<true, kPlain><<<G * sub, kRThreads, 0, s>>>(ra);
