@@ -507,17 +507,23 @@ def partition_bits_for(n_cols):
     return min(8, max(1, kb - 20))
 
 
-def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, steal=False, partition_bits=0):
+def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, steal=False, partition_bits=0,
+            hdv_k=512, unsorted=False):
     """PoTra's own method (Algorithm 2, k = 512 HDVs, with the LDV list sort)
     on the same resident graph: per-step device time, per-step stage times,
     and whether its output equals the default method's bytes.  steal: the
     two-phase Step 3 of Sec. V-F.  partition_bits: the partitioned
-    (two-level) form, bucketed by that many top destination bits first."""
+    (two-level) form, bucketed by that many top destination bits first.
+    hdv_k = 0: Atomic GT (Algorithm 1).  unsorted: the paper's output as
+    Sec. V times it (no LDV sort); col_ptr must still equal the default
+    method's."""
     import torch
     from paper_2501_06872_gb300 import binding
     cfg = binding.default_config(n_cols, m)
-    cfg.method, cfg.hdv_k, cfg.table_log2 = 0, 512, 10
+    cfg.method, cfg.hdv_k, cfg.table_log2 = 0, hdv_k, (10 if hdv_k else 0)
     cfg.flags |= binding.FLAG_PARTITION_TIMES  # Step 3's per-warp busy times (Sec. V-F imbalance)
+    if unsorted:
+        cfg.flags |= binding.FLAG_UNSORTED
     if steal:
         cfg.flags |= binding.FLAG_STEAL_TAILS
     if partition_bits:
@@ -546,7 +552,8 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, stea
         pt = np.array(plan.partition_times())
     finally:
         plan.close()
-    same = bool(torch.equal(cp, ref_out[0]) and torch.equal(ri, ref_out[1]) and
+    same_cp = bool(torch.equal(cp, ref_out[0]))
+    same = bool(same_cp and torch.equal(ri, ref_out[1]) and
                 (vo is None or torch.equal(vo.view(torch.int32), ref_out[2].view(torch.int32))))
     del cp, ri, vo
     torch.cuda.empty_cache()
@@ -556,7 +563,8 @@ def hlh_leg(n, n_cols, m, weighted, rp, ci, vv, ref_out, steps=3, warmup=1, stea
                                            "sort_ms")},
             "scatter_launch_ms": t["dominant_ms"], "hdv_selected": st["hdv_selected"],
             "step3_imbalance": step3_imbalance(pt),
-            "coverage": st["hdv_edges"] / max(1, m), "identical_output": same,
+            "coverage": st["hdv_edges"] / max(1, m), "identical_output": same, "col_ptr_identical": same_cp,
+            "unsorted": unsorted,
             "gpu_launches": int(st["kernel_launches"]) * steps}
 
 
@@ -693,6 +701,10 @@ def main():
         hlh["two_phase_step3"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo), steal=True)
         hlh["partitioned"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo),
                                      partition_bits=partition_bits_for(n_cols))
+        # the paper's own comparison (Sec. V-B, no LDV sort): Atomic GT against the locality-optimised form
+        hlh["unsorted_atomic_gt"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo), hdv_k=0, unsorted=True)
+        hlh["unsorted_partitioned"] = hlh_leg(n, n_cols, m, weighted, rp, ci, vv, (cp, ri, vo), unsorted=True,
+                                              partition_bits=partition_bits_for(n_cols))
 
     e2e = None
     if not args.no_e2e and rank == 0:
