@@ -788,6 +788,9 @@ struct ScatterArgs {
   // bucketed by destination, so there are no rows to search); split-row tags
   // carry the edge's position e in the bucketed list
   const uint32_t *src = nullptr;
+  // unsorted weighted output: every entry (HDV ones too) goes to ldv64 as one
+  // 8-byte store; k_unpack then streams them to row_idx / vals_out
+  int pack_all = 0;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -905,7 +908,7 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
           wbits = a.src ? (uint32_t)e : (uint32_t)(e - (my_u == row_first ? rs_first : rs_last));
         }
       }
-      if (VALS && ldv && a.ldv64) {  // sorted output: LDV entries wait in the scratch for the list sort
+      if (VALS && a.ldv64 && (ldv || a.pack_all)) {  // LDV entries wait in the scratch for the list sort
         a.ldv64[slot] = ((unsigned long long)wbits << 32) | uu;
       } else {
         a.row_idx[slot] = uu;
@@ -1024,6 +1027,18 @@ __global__ void __launch_bounds__(1024) k_scatter(ScatterArgs a) {
   if (a.ptime) {
     __syncwarp();
     if (lane == 0) a.ptime[2 * (size_t)p + 1] = global_ns();
+  }
+}
+
+// Unsorted weighted output: the packed entries (value bits << 32 | source)
+// the scatter left at their final slots, streamed to row_idx and vals_out.
+__global__ void k_unpack(const unsigned long long *__restrict__ packed, uint64_t m, uint32_t *row_idx,
+                         float *vals_out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const unsigned long long e = __ldcs(packed + i);
+    __stcs(row_idx + i, (uint32_t)e);
+    __stcs(vals_out + i, __uint_as_float((uint32_t)(e >> 32)));
   }
 }
 
@@ -1217,8 +1232,10 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   if (w.steal && (err = cudaMemsetAsync(w.steal_next, 0, 4, s)) != cudaSuccess) return err;
   ScatterArgs sa{pb.row_ptr, e_dst, e_val,  w.n, w.n_rows, w.m,       ranges,   w.hkeys,
                  w.hvals,    w.tlog2,    w.kmax,   w.meta,      w.hdv_cnt, w.hdv_start, w.cursor,
-                 pb.col_ptr, pb.row_idx, pb.vals_out, unsorted ? nullptr : (unsigned long long *)w.scratch,
-                 w.status, flag_mode, w.stage_edges, w.ptime, w.steal, w.P, w.steal_next, e_src};
+                 pb.col_ptr, pb.row_idx, pb.vals_out,
+                 (unsorted && !pb.vals) ? nullptr : (unsigned long long *)w.scratch,
+                 w.status, flag_mode, w.stage_edges, w.ptime, w.steal, w.P, w.steal_next, e_src,
+                 (unsorted && pb.vals) ? 1 : 0};
   const bool vals = pb.vals != nullptr;
 #define GT_SC(H, V, ST) k_scatter<H, V, ST><<<w.G, threads, w.smem_scatter, s>>>(sa)
   if (hdv) {
@@ -1243,10 +1260,16 @@ cudaError_t run_transpose(const DevWork &w, const gt_config &cfg, const Problem 
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   mark(4);
 
-  // LDV sort (it re-reads row_ptr, col_idx and vals for split rows)
+  // LDV sort (it re-reads row_ptr, col_idx and vals for split rows); unsorted
+  // weighted output: the packed entries to the outputs
   if (!unsorted) {
     err = launch_sort(w, cfg, pb, s);
     nl += 4;
+  } else if (pb.vals && w.m) {
+    const uint32_t gu = (uint32_t)min64((w.m + 255) / 256, (uint64_t)w.num_sms * 16);
+    k_unpack<<<gu, 256, 0, s>>>((const unsigned long long *)w.scratch, w.m, pb.row_idx, pb.vals_out);
+    err = cudaGetLastError();
+    nl += 1;
   }
   if (err == cudaSuccess && pb.inputs_read) err = cudaEventRecord(pb.inputs_read, s);
   mark(5);
