@@ -485,9 +485,17 @@ __global__ void __launch_bounds__(kCtaThreads) k_sort_cta(SortArgs a) {
 struct Buf {
   uint32_t *u;
   uint32_t *w;                 // null for unweighted
-  unsigned long long *packed;  // non-null: AoS source (first pass only)
+  unsigned long long *packed;  // non-null: AoS entries (value bits << 32 | source)
   __device__ uint32_t getu(uint32_t i) const { return packed ? (uint32_t)packed[i] : u[i]; }
   __device__ uint32_t getw(uint32_t i) const { return packed ? (uint32_t)(packed[i] >> 32) : (w ? w[i] : 0u); }
+  __device__ void put(uint32_t i, uint32_t uu, uint32_t ww) const {
+    if (packed) {
+      packed[i] = ((unsigned long long)ww << 32) | uu;
+    } else {
+      u[i] = uu;
+      if (w) w[i] = ww;
+    }
+  }
 };
 
 // Sorts a[0, len) (u32 positions of one split-row run; all distinct) with the
@@ -708,8 +716,7 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
       __syncwarp();
       if (act) {
         const uint32_t pos = base + rank;
-        dst.u[pos] = u;
-        if (VALS) dst.w[pos] = wv;
+        dst.put(pos, u, VALS ? wv : 0u);
         if (more) {
           uint32_t q = chunk > 1u ? __umulhi(pos, cmag) : pos;
           if (q * chunk > pos) --q;
@@ -724,7 +731,7 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
     src = dst;
     dst = (dst.u == x.u) ? y : x;
   }
-  // src holds the sorted list (SoA)
+  // src holds the sorted list (SoA, or AoS in the scratch)
   if (VALS && a.flag_mode && sh.tagged) {
     const Buf other = (src.u == x.u) ? y : x;
     for (uint32_t base = 0; base < L; base += blockDim.x) {
@@ -732,24 +739,24 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
       __syncthreads();
       const uint32_t i = base + threadIdx.x;
       if (i < L) {
-        const uint32_t u = src.u[i];
-        if ((u & kSplitFlag) && (i == 0 || src.u[i - 1] != u)) {
+        const uint32_t u = src.getu(i);
+        if ((u & kSplitFlag) && (i == 0 || src.getu(i - 1) != u)) {
           uint32_t lo = i, hi = L;  // end of the run: first index past i with another source
           while (hi - lo > 1) {
             const uint32_t mid = lo + (hi - lo) / 2;
-            if (src.u[mid] == u) lo = mid;
+            if (src.getu(mid) == u) lo = mid;
             else hi = mid;
           }
           const uint32_t j = hi;
-          if (j - i <= 64) {
+          if (j - i <= 64) {  // by position (the entries of the run share their source)
             for (uint32_t xi = i + 1; xi < j; ++xi) {
-              const uint32_t tpos = src.w[xi];
+              const uint32_t tpos = src.getw(xi);
               uint32_t yi = xi;
-              while (yi > i && src.w[yi - 1] > tpos) {
-                src.w[yi] = src.w[yi - 1];
+              while (yi > i && src.getw(yi - 1) > tpos) {
+                src.put(yi, u, src.getw(yi - 1));
                 --yi;
               }
-              src.w[yi] = tpos;
+              src.put(yi, u, tpos);
             }
           } else {
             const uint32_t q = atomicAdd(&sh.nlong, 1u);
@@ -760,14 +767,26 @@ __device__ void sort_list(const SortArgs &a, uint64_t s0, uint32_t L, Buf src, c
       }
       __syncthreads();
       const uint32_t nl = sh.nlong;
-      for (uint32_t q = 0; q < nl; ++q) cta_sort_run(src.w + sh.long_i[q], other.w + sh.long_i[q], sh.long_n[q], words);
+      for (uint32_t q = 0; q < nl; ++q) {
+        const uint32_t i0 = sh.long_i[q], n0 = sh.long_n[q];
+        if (src.packed) {  // AoS: the run's positions through the other buffer's SoA view, then back
+          const uint32_t ur = src.getu(i0);
+          for (uint32_t k = threadIdx.x; k < n0; k += blockDim.x) other.w[i0 + k] = src.getw(i0 + k);
+          __syncthreads();
+          cta_sort_run(other.w + i0, other.u + i0, n0, words);
+          for (uint32_t k = threadIdx.x; k < n0; k += blockDim.x) src.put(i0 + k, ur, other.w[i0 + k]);
+          __syncthreads();
+        } else {  // SoA; the other buffer (SoA or the AoS scratch) is free as temporary space
+          cta_sort_run(src.w + i0, other.w ? other.w + i0 : (uint32_t *)other.packed + i0, n0, words);
+        }
+      }
       __syncthreads();
     }
   }
   for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-    uint32_t u = src.u[i];
+    uint32_t u = src.getu(i);
     if (VALS) {
-      uint32_t wb = src.w[i];
+      uint32_t wb = src.getw(i);
       if (a.flag_mode && (u & kSplitFlag)) {
         u &= ~kSplitFlag;
         wb = tagged_value(a, u, wb);
@@ -800,9 +819,8 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_radix(SortArgs a) {
     const uint64_t s0 = a.col_ptr[v];
     const uint32_t L = (uint32_t)(a.col_ptr[v + 1] - s0);
     const Buf out{a.row_idx + s0, VALS ? (uint32_t *)(a.vals_out + s0) : nullptr, nullptr};
-    if (VALS) {
-      uint32_t *base32 = (uint32_t *)(a.ldv64 + s0);  // the list's 8L scratch bytes as u[L], w[L]
-      sort_list<VALS>(a, s0, L, Buf{nullptr, nullptr, a.ldv64 + s0}, out, Buf{base32, base32 + L, nullptr},
+    if (VALS) {  // the list's 8L scratch bytes hold its entries packed, as the scatter left them
+      sort_list<VALS>(a, s0, L, Buf{nullptr, nullptr, a.ldv64 + s0}, out, Buf{nullptr, nullptr, a.ldv64 + s0},
                       (uint32_t *)smem, sh);
     } else {
       sort_list<VALS>(a, s0, L, out, Buf{a.scr32 + s0, nullptr, nullptr}, out, (uint32_t *)smem, sh);

@@ -513,3 +513,25 @@ def test_hdv_insertion_points_over_many_partitions(steal):
     plan.close()
     assert P > 32768
     assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
+
+
+def test_long_tagged_runs_in_lists_sorted_by_three_radix_passes():
+    """More than 2^16 rows, so the longest lists take three radix passes on the
+    source and end in the caller's arrays rather than in the scratch: a hub row
+    split over many partitions sends 80,000 parallel edges into one list (a
+    tagged run far longer than 64) and 5,000 into another."""
+    rng = np.random.default_rng(47)
+    n = 70000
+    rows = [np.concatenate([np.full(80000, 11), np.full(5000, 13), rng.integers(0, n, 20000)])]
+    rows += [rng.integers(0, n, rng.integers(0, 6)) for _ in range(n - 1)]
+    for r in rows[1:3000]:
+        if len(r):
+            r[0] = 11  # more sources into list 11, around the tagged run
+    rp = np.zeros(n + 1, np.uint64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate(rows).astype(np.uint32)
+    vv = rng.standard_normal(len(ci)).astype(np.float32)
+    exp = oracle.transpose(rp, ci, vv)
+    for cfg in [config(hdv_k=0, warp_edges=2048), config(hdv_k=4, warp_edges=1024),
+                config(hdv_k=0, warp_edges=2048, partition_bits=6)]:
+        assert_same(gpu_transpose(rp, ci, vv, cfg), exp)
