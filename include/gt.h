@@ -107,12 +107,14 @@ typedef struct gt_config {
 
 #define GT_FLAG_AGGREGATE 1u  /* aggregate LDV atomics across a warp (__match_any_sync) */
 #define GT_FLAG_NO_GRAPH 2u   /* batches: launch kernels directly, no CUDA graph        */
-/* GT_METHOD_HLH only: skip the LDV list sort; the scatter writes LDV entries
- * straight to the outputs, so the lists of low-degree destinations come out in
- * arbitrary order (each holds the right multiset of (source, value) pairs;
- * HDV lists stay in edge order).  This is the output of PoTra and Atomic GT as
- * the paper times them (Sec. V excludes the sort).  The radix method ignores
- * it: its lists are always sorted. */
+/* GT_METHOD_HLH only: skip the LDV list sort; the lists of low-degree
+ * destinations come out in arbitrary order (each holds the right multiset of
+ * (source, value) pairs; HDV lists stay in edge order).  Unweighted entries
+ * are written straight to row_idx; weighted ones go to the plan's scratch as
+ * one 8-byte store each and a streaming pass copies them to row_idx and
+ * vals_out.  This is the output of PoTra and Atomic GT as the paper times
+ * them (Sec. V excludes the sort).  The radix method ignores it: its lists are
+ * always sorted. */
 #define GT_FLAG_UNSORTED 4u
 /* GT_METHOD_HLH: record the start and end (global timer) of every warp
  * partition in Step 3, read with gt_plan_partition_times (Sec. V-F measures
